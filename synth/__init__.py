@@ -1,0 +1,115 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This module draws random numbers and lays them out; it holds none of the
+solver's arithmetic (no Shapley operator, no policy iteration, no multigrid).
+Both sides of every parity test take their inputs from here, or, for the
+Isaacs per-state noise that the C-ABI can also generate from a seed, each side
+implements the same counter-based generator (SplitMix64) from its published
+definition and the tests check that the two agree bit for bit.
+
+SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014): the i-th output (i = 0, 1, ...) of the stream with
+seed s is mix(s + (i + 1) * 0x9E3779B97F4A7C15 mod 2^64), where mix is the
+variant-13 finaliser of MurmurHash3 with shifts (30, 27, 31).  A double in
+[0, 1) takes the top 53 bits: (z >> 11) * 2^-53.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+_TWO_M53 = float(2.0 ** -53)
+
+
+def splitmix64(seed: int, counters: np.ndarray) -> np.ndarray:
+    """Outputs number ``counters`` (0-based, uint64 array) of the stream ``seed``."""
+    c = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (c + np.uint64(1)) * GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, counters: np.ndarray) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of each SplitMix64 output."""
+    z = splitmix64(seed, counters)
+    return (z >> np.uint64(11)).astype(np.float64) * _TWO_M53
+
+
+def isaacs_noise(side: int, seed: int) -> np.ndarray:
+    """Per-state reward noise xi(x) ~ U(-0.05, 0.05) of the Isaacs workload.
+
+    One draw per interior grid point, in row-major state order
+    x = i2 * side + i1 (i1 along the first coordinate), drawn from the stream
+    ``seed``: xi = 0.1 * u - 0.05 with u the x-th uniform.  Returned as a
+    float64 array of length side*side.
+    """
+    n = side * side
+    u = uniform01(seed, np.arange(n, dtype=np.uint64))
+    return u * 0.1 - 0.05
+
+
+DRAWS_PER_ROW = 17  # 8 successor draws, 8 exponential draws, 1 reward draw
+
+
+def random_game(n: int, seed: int, m1: int = 4, m2: int = 4, k: int = 8,
+                mu: float = 0.99):
+    """A random finite discounted game in the C-ABI's CSR layout.
+
+    Rows are indexed (x * m1 + a) * m2 + b.  Each row has ``k`` distinct
+    successors drawn uniformly from {0..n-1} (the state itself allowed),
+    with Dirichlet(1) probabilities (normalised Exp(1) draws, the last drawn
+    entry set to one minus the others) and a reward U(-1, 1).  Within a row
+    the successors are stored in increasing column order.
+
+    Row rho uses counters rho*17 .. rho*17+16 of the stream ``seed``: draws
+    0..k-1 pick the successors (sampling without replacement by rank
+    adjustment), draws 8..8+k-1 the exponentials, draw 16 the reward.
+
+    Returns (row_ptr int64[R+1], col int32[R*k], prob float64[R*k],
+    reward float64[R], mu) with R = n*m1*m2.
+    """
+    if not (1 <= k <= 8) or k > n:
+        raise ValueError("need 1 <= k <= min(8, n)")
+    R = n * m1 * m2
+    base = np.arange(R, dtype=np.uint64) * np.uint64(DRAWS_PER_ROW)
+    picks = np.empty((R, k), dtype=np.int64)
+    for t in range(k):
+        u = uniform01(seed, base + np.uint64(t))
+        idx = np.minimum((u * (n - t)).astype(np.int64), n - t - 1)
+        if t:
+            prev = np.sort(picks[:, :t], axis=1)
+            for s in range(t):          # shift past each earlier pick, ascending
+                idx = idx + (idx >= prev[:, s])
+        picks[:, t] = idx
+    e = np.empty((R, k), dtype=np.float64)
+    for t in range(k):
+        u = uniform01(seed, base + np.uint64(8 + t))
+        e[:, t] = -np.log1p(-u)
+    tot = e.sum(axis=1, keepdims=True)
+    p = e / tot
+    if k > 1:
+        p[:, k - 1] = np.maximum(1.0 - p[:, : k - 1].sum(axis=1), 0.0)
+    else:
+        p[:, 0] = 1.0
+    reward = uniform01(seed, base + np.uint64(16)) * 2.0 - 1.0
+    order = np.argsort(picks, axis=1, kind="stable")
+    col = np.take_along_axis(picks, order, axis=1).astype(np.int32)
+    prob = np.take_along_axis(p, order, axis=1)
+    row_ptr = np.arange(R + 1, dtype=np.int64) * k
+    return row_ptr, col.reshape(-1), prob.reshape(-1), reward, float(mu)
+
+
+def batch_game_sizes(count: int, seed: int, nmin: int = 256, nmax: int = 8192) -> np.ndarray:
+    """Sizes n_i ~ U{nmin..nmax} of a batch of random games (stream ``seed``)."""
+    u = uniform01(seed, np.arange(count, dtype=np.uint64))
+    return nmin + np.minimum((u * (nmax - nmin + 1)).astype(np.int64), nmax - nmin)
+
+
+def batch_game_seed(seed: int, i: int) -> int:
+    """Stream of game i of a batch: SplitMix64 seeded with seed XOR i."""
+    return (seed ^ i) & 0xFFFFFFFFFFFFFFFF

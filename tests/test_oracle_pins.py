@@ -1,0 +1,335 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: brute-force
+enumeration of all pure stationary policy pairs (Sec. 2 theorem: the value is
+attained by pure Markovian stationary strategies), closed forms, the
+contraction and monotonicity of the Shapley operator (Sec. 2), the monotone
+value sequences of policy iteration (Sec. 4.1-4.2), the a-posteriori bound that
+follows from the mu-contraction, O(h) convergence of the Isaacs scheme
+(Sec. 3.3) to a manufactured solution, and hand-worked interpolation examples
+for FAMGpi (Sec. 5.2).
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.game import game_from_csr, shapley_q, _keep_current
+from oracle.isaacs import (isaacs_game, isaacs_geometry, stencil_probabilities,
+                           default_alpha0, discount)
+from oracle.fmg import interp_value, interp_policy, famg_pi, injected_noise
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+def tiny_dense_game(seed, n, m1, m2, substochastic=True):
+    """Dense p[x, a, b, y] (rows sum to <= 1) and r[x, a, b] for brute force."""
+    rng = np.random.default_rng(seed)
+    p = rng.random((n, m1, m2, n)) * (rng.random((n, m1, m2, n)) < 0.7)
+    p[..., 0] += 1e-3                                  # no empty rows
+    p /= p.sum(axis=-1, keepdims=True)
+    if substochastic:
+        p *= rng.uniform(0.6, 1.0, size=(n, m1, m2, 1)) ** (rng.random((n, m1, m2, 1)) < 0.3)
+    r = rng.uniform(-1, 1, size=(n, m1, m2))
+    return p, r
+
+
+def dense_to_game(p, r, mu):
+    n, m1, m2, _ = p.shape
+    rows = p.reshape(n * m1 * m2, n)
+    row_ptr = [0]
+    col, prob = [], []
+    for row in rows:
+        nz = np.nonzero(row)[0]
+        col.extend(nz.tolist())
+        prob.extend(row[nz].tolist())
+        row_ptr.append(len(col))
+    return game_from_csr(n, m1, m2, np.array(row_ptr), np.array(col, np.int32),
+                         np.array(prob), r.reshape(-1), mu)
+
+
+def value_of(p, r, mu, alpha, bsel):
+    """v^{alpha beta} = (I - mu M)^-1 r^{alpha beta} with M from dense p."""
+    n = p.shape[0]
+    xs = np.arange(n)
+    M = p[xs, alpha, bsel, :]
+    return np.linalg.solve(np.eye(n) - mu * M, r[xs, alpha, bsel])
+
+
+def brute_force(p, r, mu):
+    """v* = max_alpha min_beta v^{alpha beta}, componentwise, by enumeration.
+
+    v^{alpha beta} depends on beta only through beta(x, alpha(x)), so MIN's
+    choices are enumerated as one action per state.  Returns v* and, per
+    alpha, MIN's componentwise-optimal value V^alpha.
+    """
+    n, m1, m2, _ = p.shape
+    V = {}
+    for alpha in itertools.product(range(m1), repeat=n):
+        vals = np.array([value_of(p, r, mu, np.array(alpha), np.array(b))
+                         for b in itertools.product(range(m2), repeat=n)])
+        Va = vals.min(axis=0)
+        # MDP theory: one stationary beta attains the componentwise minimum.
+        assert np.any(np.all(np.abs(vals - Va) <= 1e-12, axis=1))
+        V[alpha] = Va
+    allV = np.array(list(V.values()))
+    vstar = allV.max(axis=0)
+    assert np.any(np.all(np.abs(allV - vstar) <= 1e-12, axis=1))
+    return vstar, V
+
+
+def dense_F(p, r, mu, v):
+    q = mu * np.einsum("xaby,y->xab", p, v) + r
+    return q.min(axis=2).max(axis=1)
+
+
+# ----------------------------------------------------------------- brute force
+@pytest.mark.parametrize("mu", [0.5, 0.9, 0.99])
+@pytest.mark.parametrize("n", [2, 3, 4])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_pi_matches_brute_force(n, mu, seed):
+    p, r = tiny_dense_game(1000 * n + seed, n, 2, 2)
+    vstar, V = brute_force(p, r, mu)
+    game = dense_to_game(p, r, mu)
+    res = oracle.policy_iteration(game)
+    assert res.converged
+    assert np.max(np.abs(res.v - vstar)) <= 1e-13 * max(1.0, np.max(np.abs(vstar))) * 10
+    # the Shapley equation holds at the brute-force value
+    assert np.max(np.abs(dense_F(p, r, mu, vstar) - vstar)) <= 1e-12
+    # the returned policies are optimal: alpha attains v*, beta is MIN's best reply
+    a = res.alpha.astype(int)
+    assert np.allclose(V[tuple(a.tolist())], vstar, atol=1e-12)
+    b = res.beta[np.arange(n), a].astype(int)
+    assert np.allclose(value_of(p, r, mu, a, b), vstar, atol=1e-12)
+
+
+@pytest.mark.parametrize("m1,m2", [(1, 3), (3, 1), (2, 3)])
+def test_pi_matches_brute_force_uneven_actions(m1, m2):
+    p, r = tiny_dense_game(77 + m1 * 10 + m2, 3, m1, m2)
+    vstar, _ = brute_force(p, r, 0.9)
+    res = oracle.policy_iteration(dense_to_game(p, r, 0.9))
+    assert np.max(np.abs(res.v - vstar)) <= 1e-12
+
+
+def test_single_action_closed_form():
+    """m1 = m2 = 1: the game is a Markov chain, v = (I - mu P)^-1 r."""
+    rng = np.random.default_rng(5)
+    n = 40
+    p, r = tiny_dense_game(5, n, 1, 1)
+    mu = 0.95
+    v = np.linalg.solve(np.eye(n) - mu * p[:, 0, 0, :], r[:, 0, 0])
+    res = oracle.policy_iteration(dense_to_game(p, r, mu))
+    assert res.outer == 1 and res.systems == 1
+    assert np.max(np.abs(res.v - v)) <= 1e-12
+    del rng
+
+
+# ----------------------------------------------------------------- operator properties
+def _random_game(n=60, seed=3, mu=0.9, k=6):
+    rp, col, prob, rew, _ = synth.random_game(n, seed, k=k, mu=mu)
+    return game_from_csr(n, 4, 4, rp, col, prob, rew, mu), rew
+
+
+def _F(game, v):
+    return shapley_q(game, v).min(axis=2).max(axis=1)
+
+
+def test_shapley_monotone_contracting_homogeneous():
+    game, _ = _random_game()
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        v = rng.normal(size=game.n)
+        w = v + np.abs(rng.normal(size=game.n))          # w >= v
+        assert np.all(_F(game, v) <= _F(game, w) + 1e-15)
+        u = rng.normal(size=game.n) * 3
+        lhs = np.max(np.abs(_F(game, v) - _F(game, u)))
+        assert lhs <= game.mu * np.max(np.abs(v - u)) + 1e-13
+        c = rng.normal()
+        # rows are stochastic: F(v + c 1) = F(v) + mu c
+        assert np.max(np.abs(_F(game, v + c) - _F(game, v) - game.mu * c)) <= 1e-13
+
+
+@pytest.mark.parametrize("which", ["random", "isaacs", "obstacle"])
+def test_contraction_bound_and_fixed_point(which):
+    if which == "random":
+        game, rew = _random_game(mu=0.97)
+    else:
+        game = isaacs_game(15, 1 if which == "obstacle" else 0, seed=4)
+        rew = game.rew
+    a0 = default_alpha0(15, 1) if which == "obstacle" else None
+    res = oracle.policy_iteration(game, alpha0=a0)
+    assert res.converged
+    assert np.max(np.abs(res.v)) <= np.max(np.abs(rew)) / (1 - game.mu) + 1e-12
+    assert np.max(np.abs(_F(game, res.v) - res.v)) <= 1e-13
+
+
+@pytest.mark.parametrize("which", ["random", "isaacs", "obstacle"])
+def test_pi_value_sequences_monotone_and_aposteriori(which):
+    """Outer values non-decreasing, inner non-increasing (Sec. 4.2); and
+    |v - v*| <= |F(v) - v| / (1 - mu) for every intermediate iterate."""
+    if which == "random":
+        game, _ = _random_game(n=80, seed=11, mu=0.9)
+        a0 = None
+    else:
+        var = 1 if which == "obstacle" else 0
+        game = isaacs_game(15, var, seed=6)
+        a0 = default_alpha0(15, var)
+    res = oracle.policy_iteration(game, alpha0=a0, record=True)
+    assert res.converged
+    vstar = res.v
+    tol = 1e-12
+    for k in range(1, len(res.outer_values)):
+        assert np.all(res.outer_values[k] >= res.outer_values[k - 1] - tol)
+    for inner in res.inner_values:
+        for j in range(1, len(inner)):
+            assert np.all(inner[j] <= inner[j - 1] + tol)
+    for v in res.outer_values:
+        bound = np.max(np.abs(_F(game, v) - v)) / (1 - game.mu)
+        assert np.max(np.abs(v - vstar)) <= bound + tol
+
+
+def test_pi_terminates_and_records_counts():
+    game, _ = _random_game(n=100, seed=9, mu=0.99)
+    res = oracle.policy_iteration(game)
+    assert res.converged and 1 <= res.outer <= 50 and res.systems >= res.outer
+
+
+# ----------------------------------------------------------------- Isaacs scheme
+def test_isaacs_stencil_structure():
+    side = 9
+    game = isaacs_game(side, 1, seed=1)
+    h = 1.0 / (side + 1)
+    c0 = 2 + h
+    # a = +x1 (0), b = -x1 (1): drift (1, 0): upwind weight on +x1
+    p = stencil_probabilities(h, 0, 1)
+    assert p == pytest.approx(((0.5 + h) / c0, 0.5 / c0, 0.5 / c0, 0.5 / c0, 0.0), abs=0)
+    # a = +x2 (2), b = +x1 (0): drift (-1/2, 1/2)
+    p = stencil_probabilities(h, 2, 0)
+    assert p == pytest.approx((0.5 / c0, (0.5 + h / 2) / c0, (0.5 + h / 2) / c0, 0.5 / c0, 0.0))
+    # a == b: zero drift, the spare h/c0 is a self-transition
+    p = stencil_probabilities(h, 3, 3)
+    assert p == pytest.approx((0.5 / c0,) * 4 + (h / c0,))
+    rows = game.prob[:, :4, :, :].sum(axis=-1)
+    interior = np.zeros((side, side), bool)
+    interior[1:-1, 1:-1] = True
+    interior = interior.reshape(-1)
+    assert np.allclose(rows[interior], 1.0, atol=1e-15)
+    assert np.all(rows[~interior] < 1.0 - 0.2)          # boundary rows lose mass
+    assert np.all(game.prob >= 0)
+    # stop rows: no successors, reward psi
+    _, x1, x2 = isaacs_geometry(side)
+    assert np.all(game.succ[:, 4] == -1)
+    assert np.allclose(game.rew[:, 4, 0], 0.2 - (x1 - 0.5) ** 2 - (x2 - 0.5) ** 2)
+    mu, omm = discount(side)
+    assert game.mu == mu and abs((1 - mu) - omm) < 1e-15
+
+
+def test_isaacs_manufactured_solution_converges_O_h():
+    """The scheme (decent)-(centre) is monotone and consistent: O(h) error."""
+    errs = []
+    for side in (15, 31, 63, 127):
+        game = isaacs_game(side, 0, reward="manufactured")
+        res = oracle.policy_iteration(game)
+        _, x1, x2 = isaacs_geometry(side)
+        u = np.sin(np.pi * x1) * np.sin(np.pi * x2)
+        errs.append(np.max(np.abs(res.v - u)))
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert errs[-1] < 0.02
+    assert all(1.6 < q < 2.6 for q in ratios), (errs, ratios)
+
+
+# ----------------------------------------------------------------- tie rule
+def test_keep_current_rule():
+    vals = np.array([[1.0, 1.0 + 5e-14, 0.5], [1.0, 2.0, 2.0], [3.0, 1.0, 1.0]])
+    cur = np.array([0, 0, 1], np.uint8)
+    amax, _ = _keep_current(vals, cur, 1e-13, True)
+    assert amax.tolist() == [0, 1, 0]      # within tau: keep; else lowest optimum
+    amin, _ = _keep_current(vals, cur, 1e-13, False)
+    assert amin.tolist() == [2, 0, 1]
+
+
+# ----------------------------------------------------------------- FAMGpi pieces
+def _golden_rows(name):
+    rows = [ln for ln in open(os.path.join(GOLDEN, name)) if ln.strip() and not ln.startswith("#")]
+    return np.array([[float(t) for t in ln.split()] for ln in rows])
+
+
+def test_interp_value_hand_example():
+    out = interp_value(np.array([1.0]), 1).reshape(3, 3)
+    assert np.array_equal(out, _golden_rows("fmg_interp_1to3.txt"))
+
+
+def test_interp_value_copy_and_second_order():
+    errs = []
+    for side_c in (7, 15, 31, 63):
+        side_f = 2 * side_c + 1
+        _, x1c, x2c = isaacs_geometry(side_c)
+        _, x1f, x2f = isaacs_geometry(side_f)
+        f = lambda a, b: np.sin(np.pi * a) * np.sin(2 * np.pi * b) * np.exp(a)
+        out = interp_value(f(x1c, x2c), side_c)
+        grid = out.reshape(side_f, side_f)
+        assert np.array_equal(grid[1::2, 1::2].reshape(-1), f(x1c, x2c))
+        errs.append(np.max(np.abs(out - f(x1f, x2f))))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(3.3 < q < 4.7 for q in ratios), ratios
+
+
+def test_interp_policy_hand_example():
+    coarse = np.arange(9, dtype=np.uint8)      # 3x3 coarse grid, action = linear index
+    out = interp_policy(coarse, 3).reshape(7, 7)
+    # coarse points copied
+    assert np.array_equal(out[1::2, 1::2].reshape(-1), coarse)
+    # worked from the lowest interior member of N(x) (1-based fine (p, q) -> out[q-1, p-1]):
+    assert out[0, 0] == 0        # (1,1): N = {(0,0),(1,0),(0,1),(1,1)} -> coarse (1,1)
+    assert out[0, 2] == 0        # (3,1): interior members (1,1), (2,1) -> index 0
+    assert out[2, 3] == 1        # (4,3): members (2,1), (2,2) -> index 1
+    assert out[6, 6] == 8        # (7,7): only (3,3) is interior
+    assert out[5, 6] == 8        # (7,6): members (3,3) and boundary (4,3)
+    beta = np.stack([coarse, coarse + 10], axis=1)
+    assert np.array_equal(interp_policy(beta, 3)[:, 1], out.reshape(-1) + 10)
+
+
+def test_famg_matches_flat_value():
+    """FAMGpi and flat PI reach the same (unique) value, plain and obstacle."""
+    for variant in (0, 1):
+        xi = synth.isaacs_noise(31, 2)
+        res, levels = famg_pi(31, 3, variant, xi, c=0.1, eps=0.0)
+        flat = oracle.policy_iteration(isaacs_game(31, variant, xi=xi),
+                                       alpha0=default_alpha0(31, variant))
+        assert np.max(np.abs(res.v - flat.v)) <= 1e-13
+        assert len(levels) == 4
+
+
+def test_injected_noise_positions():
+    xi = np.arange(15 * 15, dtype=float)
+    out = injected_noise(xi, 15, 7).reshape(7, 7)
+    assert out[0, 0] == xi[1 * 15 + 1] and out[6, 6] == xi[13 * 15 + 13]
+
+
+# ----------------------------------------------------------------- generators
+def test_splitmix64_published_outputs():
+    with open(os.path.join(GOLDEN, "splitmix64_seed1234567.txt")) as fh:
+        want = [int(ln) for ln in fh if ln.strip() and not ln.startswith("#")]
+    got = synth.splitmix64(1234567, np.arange(5, dtype=np.uint64))
+    assert [int(z) for z in got] == want
+
+
+def test_random_game_structure():
+    n = 300
+    rp, col, prob, rew, mu = synth.random_game(n, 17)
+    R = n * 16
+    assert rp[-1] == R * 8 and mu == 0.99
+    c = col.reshape(R, 8)
+    assert np.all(np.diff(c, axis=1) > 0)            # distinct, ascending
+    assert c.min() >= 0 and c.max() < n
+    assert np.allclose(prob.reshape(R, 8).sum(axis=1), 1.0, atol=1e-15)
+    assert np.all(prob >= 0) and np.all(np.abs(rew) < 1)
+    rp2, col2, prob2, rew2, _ = synth.random_game(n, 17)
+    assert np.array_equal(col, col2) and np.array_equal(prob, prob2)
+    # roughly uniform successor marginal
+    counts = np.bincount(col, minlength=n)
+    assert counts.min() > 0.6 * counts.mean() and counts.max() < 1.4 * counts.mean()
