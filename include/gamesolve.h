@@ -1,0 +1,178 @@
+/*
+ * gamesolve.h - C ABI of the GB300 policy-iteration / algebraic-multigrid
+ * solver for discounted two-player zero-sum stochastic games.
+ *
+ * The method is that of M. Akian and S. Detournay, "Multigrid methods for
+ * two-player zero-sum stochastic games": find v : X -> R with
+ *
+ *     v(x) = max_{a in A} min_{b in B} ( sum_y mu p(y|x,a,b) v(y) + r(x,a,b) )
+ *
+ * (Sec. 2, Eq. (eq1)) by policy iteration (Algorithm 2 with Algorithm 1 as its
+ * inner loop, Sec. 4.1-4.2), solving every policy-fixed linear system
+ * (I - mu M^{alpha beta}) v = r^{alpha beta} (Eq. (LSPI)) with algebraic
+ * multigrid (Sec. 4.3, Algorithm 3; the combination is "AMGpi", Sec. 5.1), and,
+ * for Isaacs grids, the full multilevel scheme FAMGpi (Algorithm 4, Sec. 5.2).
+ *
+ * Conventions for every entry point:
+ *  - All pointers are plain host or device pointers.  Data passed in is COPIED
+ *    (the caller keeps ownership); data read out is written to the caller's
+ *    buffer.  Host buffers may be pageable or pinned; device pointers must be
+ *    on the solver's device.  Copies use cudaMemcpyDefault on the solver's
+ *    stream, and each call returns only after its work on that stream is done.
+ *  - A call that returns anything but GS_OK leaves the solver as it was before
+ *    the call, except gamesolve_solve, which keeps the best iterate reached.
+ *  - There is no CPU fallback: every step of the method runs in the library's
+ *    own CUDA kernels.  A missing or unusable GPU gives GS_ECUDA.
+ *  - Not thread-safe per solver; distinct solvers may be used concurrently.
+ */
+#ifndef GAMESOLVE_H
+#define GAMESOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gs_solver gs_solver;   /* opaque; owns all of its device memory */
+
+typedef enum {
+    GS_OK = 0,
+    GS_EINVAL = 1,      /* invalid argument or input data (nothing changed) */
+    GS_ENOMEM = 2,      /* device memory budget or allocation exceeded */
+    GS_ENOTCONV = 3,    /* iteration caps reached; best iterate kept */
+    GS_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+    GS_ECUDA = 5,       /* CUDA runtime error (message via gamesolve_last_error) */
+    GS_ESTATE = 6       /* call out of order (e.g. solve before a problem is set) */
+} gs_status;
+
+typedef enum {
+    GS_PREC_FP64 = 0,        /* every step in float64 */
+    GS_PREC_MIXED = 1,       /* float32 V-cycles inside float64 iterative refinement */
+    GS_PREC_MIXED_BF16 = 2   /* as MIXED, coarse stencils / game weights stored in bfloat16 */
+} gs_precision;
+
+/* Solver options.  Fill with gamesolve_default_options, then override. */
+typedef struct {
+    int32_t precision;     /* gs_precision */
+    double  eps;           /* policy iteration stops when |F(v) - v|_inf <= eps (Sec. 5.1)
+                              or when MAX's policy is unchanged; 0 = the latter only */
+    int32_t max_outer;     /* cap on MAX policy iterations (Algorithm 2) */
+    int32_t max_inner;     /* cap on MIN policy iterations per MAX step (Algorithm 1) */
+    int32_t nu1, nu2;      /* pre/post C/F relaxation sweeps per level (Algorithm 3) */
+    int32_t max_cycles;    /* cap on V-cycles (refinement steps) per linear system */
+    double  lin_tol;       /* linear solve stops when |b - A v|_inf <= lin_tol * |v|_inf,
+                              or when the residual stops decreasing (float64 floor) */
+    int32_t coarse_max;    /* coarsest multigrid level has at most this many unknowns */
+    int32_t fmg;           /* 1: FAMGpi (Algorithm 4) for Isaacs grids; 0: flat AMGpi */
+    int32_t fmg_side;      /* FAMGpi coarsest grid side (2^k - 1), e.g. 31 */
+    double  fmg_c;         /* FAMGpi per-level tolerance eps_l = fmg_c * h_l^2 */
+    int32_t mu_mode;       /* Isaacs discount: 0 mu = 1/(1+h^2), 1 mu = c0/(c0+h^2) */
+    int32_t reserved0;
+    uint64_t mem_budget;   /* bytes of device memory the solver may hold; 0 = no limit */
+    void*   stream;        /* cudaStream_t for all work; NULL = the legacy default stream */
+} gs_options;
+
+/* Statistics of the last gamesolve_solve (the columns of the paper's tables, Sec. 6). */
+typedef struct {
+    int32_t outer;          /* k: MAX policy iterations */
+    int32_t systems;        /* linear systems solved (sum of #j) */
+    int32_t cycles;         /* V-cycles (or refinement steps) over all systems */
+    int32_t levels;         /* multigrid levels of the finest hierarchy */
+    double  res_inf;        /* |F(v) - v|_inf at the returned v */
+    double  res_l2;         /* discrete L2 norm sqrt(mean (F(v) - v)^2) */
+    double  seconds;        /* wall time of the solve on the device stream */
+    int32_t converged;      /* 1 if a stopping rule was met */
+    int32_t fmg_levels;     /* FAMGpi levels run (0 for flat) */
+} gs_solve_stats;
+
+/* Fills *opt with the defaults: FP64, eps 0, max_outer 1000, max_inner 1000,
+ * V(1,1), max_cycles 200, lin_tol 1e-15, coarse_max 64, flat, fmg_side 31,
+ * fmg_c 0.1, literal mu, no memory budget, default stream. */
+void gamesolve_default_options(gs_options* opt);
+
+/* Creates a solver on the current CUDA device.  opt may be NULL (defaults).
+ * Errors: GS_EINVAL (bad option values), GS_ECUDA (no usable device). */
+gs_status gamesolve_create(gs_solver** out, const gs_options* opt);
+
+/* Sets a finite game (Sec. 2): n states, m1 MAX actions, m2 MIN actions.
+ * Rows of the transition table are indexed (x*m1 + a)*m2 + b; row_ptr has
+ * n*m1*m2 + 1 entries (CSR), col[k] in [0, n) and prob[k] = p(col[k] | x, a, b)
+ * for k in [row_ptr[row], row_ptr[row+1]); reward has n*m1*m2 entries r(x,a,b).
+ * Rows may be substochastic (the missing mass leaves the game), so a row
+ * without successors is a "stop" action.
+ * Errors (GS_EINVAL, solver unchanged): n < 1, m1 or m2 outside [1, 8],
+ * row_ptr not non-decreasing from 0, a column out of range, a negative
+ * probability, a row sum above 1 + 1e-12, mu outside (0, 1). */
+gs_status gamesolve_set_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2,
+                             const int64_t* row_ptr, const int32_t* col,
+                             const double* prob, const double* reward, double mu);
+
+/* Sets the finite-difference Isaacs game on the unit square (Sec. 3.3, the
+ * upwind scheme (decent) with the centred scheme (centre), scaled to the form
+ * of Eq. (eq1) as Sec. 6.1 does for Eq. (Iex1d)): side x side interior points,
+ * h = 1/(side+1), Dirichlet v = 0 on the boundary, actions a, b in {0..3}
+ * indexing the directions +x1, -x1, +x2, -x2, drift (e_a - e_b)/2, one
+ * normaliser c0 = 2 + h, reward (1-mu)(sin(pi x1) sin(pi x2) + 0.1(a-b) + xi(x)).
+ * variant 0: plain (m1 = m2 = 4).  variant 1: obstacle (Sec. 3.2, Eq. (VI)):
+ * MAX also has a = 4, "stop", worth psi(x) = 0.2 - |x - (1/2,1/2)|^2.
+ * xi: per-state noise, side*side doubles in row-major order (first
+ * coordinate fastest), host or device; NULL draws xi(x) = 0.1 u_x - 0.05 with
+ * u_x the x-th double of the SplitMix64 stream `seed`.
+ * Errors: GS_EINVAL if side < 1, side != 2^k - 1 when options.fmg is set, or
+ * variant not in {0, 1}. */
+gs_status gamesolve_set_isaacs_grid(gs_solver* s, int32_t side, int32_t variant,
+                                    uint64_t seed, const double* xi);
+
+/* Optional warm start for the next solve (Algorithm 4 passes the same three
+ * things to AMGpi): v0 (n doubles), alpha0 (n bytes), beta0 (n*m1 bytes,
+ * beta(x, a) at [x*m1 + a]).  Any pointer may be NULL: v0 defaults to 0,
+ * alpha0 to action 0 (stop everywhere for the obstacle variant), and beta0 to
+ * MIN's best reply to v0.  Errors: GS_ESTATE (no problem set), GS_EINVAL
+ * (an action out of range). */
+gs_status gamesolve_set_initial(gs_solver* s, const double* v0,
+                                const uint8_t* alpha0, const uint8_t* beta0);
+
+/* Runs AMGpi (or FAMGpi if options.fmg) from the current initial data.
+ * stats may be NULL.  Returns GS_ENOTCONV when a cap was reached (the best
+ * iterate is kept and readable), GS_ESTATE when no problem is set. */
+gs_status gamesolve_solve(gs_solver* s, gs_solve_stats* stats);
+
+/* Copies the value v (n doubles) to v_out (host or device). */
+gs_status gamesolve_get_value(const gs_solver* s, double* v_out, int64_t n);
+
+/* Copies MAX's policy alpha (n bytes) and MIN's policy beta (n*m1 bytes,
+ * beta(x, a) for every a) to the caller's buffers (either may be NULL). */
+gs_status gamesolve_get_policy(const gs_solver* s, uint8_t* alpha, uint8_t* beta);
+
+/* One policy improvement (Algorithm 2 step 2 with MIN's reply for every a,
+ * Eq. (eq1) and (ILPI)) at the value v (n doubles, host or device) against the
+ * current policies (the keep-current tie rule needs them).  Writes
+ * alpha' (n bytes), beta' (n*m1 bytes) and F(v) (n doubles); any output may
+ * be NULL.  Does not change the solver's policies or value. */
+gs_status gamesolve_improve(gs_solver* s, const double* v, uint8_t* alpha_out,
+                            uint8_t* beta_out, double* fv_out);
+
+/* Solves the policy-fixed system (I - mu M^{alpha beta}) w = r^{alpha beta}
+ * of Eq. (LSPI) for the given policies (alpha: n bytes, beta: n*m1 bytes) with
+ * the solver's multigrid method and precision, from the initial guess w0
+ * (NULL = 0).  Writes w (n doubles).  stats (may be NULL) gets cycles and the
+ * final |b - A w|_inf in res_inf. */
+gs_status gamesolve_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* beta,
+                                 const double* w0, double* w_out, gs_solve_stats* stats);
+
+/* Frees the solver and all of its device memory.  NULL is a no-op. */
+void gamesolve_destroy(gs_solver* s);
+
+/* Static description of a status code. */
+const char* gamesolve_strerror(gs_status st);
+
+/* Text of the last error raised on this thread (CUDA or validation detail). */
+const char* gamesolve_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAMESOLVE_H */

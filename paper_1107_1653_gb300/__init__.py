@@ -1,0 +1,210 @@
+"""Python binding of libgamesolve (include/gamesolve.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels; this module only
+converts arguments.  Importing it loads the in-tree shared library and fails
+loudly if it has not been built (``paper_1107_1653_gb300.build.build()``).
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); outputs
+are numpy arrays unless a preallocated ``out`` tensor is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgamesolve.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1107_1653_gb300.build.build()")
+lib = ctypes.CDLL(LIB_PATH)
+
+GS_OK, GS_EINVAL, GS_ENOMEM, GS_ENOTCONV, GS_ETIMEOUT, GS_ECUDA, GS_ESTATE = range(7)
+GS_PREC_FP64, GS_PREC_MIXED, GS_PREC_MIXED_BF16 = range(3)
+PRECISIONS = {"fp64": GS_PREC_FP64, "mixed": GS_PREC_MIXED, "mixed_bf16": GS_PREC_MIXED_BF16}
+
+
+class gs_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32), ("eps", ctypes.c_double),
+        ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
+        ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
+        ("max_cycles", ctypes.c_int32), ("lin_tol", ctypes.c_double),
+        ("coarse_max", ctypes.c_int32), ("fmg", ctypes.c_int32),
+        ("fmg_side", ctypes.c_int32), ("fmg_c", ctypes.c_double),
+        ("mu_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("mem_budget", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+    ]
+
+
+class gs_solve_stats(ctypes.Structure):
+    _fields_ = [
+        ("outer", ctypes.c_int32), ("systems", ctypes.c_int32),
+        ("cycles", ctypes.c_int32), ("levels", ctypes.c_int32),
+        ("res_inf", ctypes.c_double), ("res_l2", ctypes.c_double),
+        ("seconds", ctypes.c_double), ("converged", ctypes.c_int32),
+        ("fmg_levels", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_S = ctypes.c_int
+_SIGS = {
+    "gamesolve_default_options": (None, [ctypes.POINTER(gs_options)]),
+    "gamesolve_create": (_S, [ctypes.POINTER(_P), ctypes.POINTER(gs_options)]),
+    "gamesolve_set_game": (_S, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
+                                ctypes.c_double]),
+    "gamesolve_set_isaacs_grid": (_S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P]),
+    "gamesolve_set_initial": (_S, [_P, _P, _P, _P]),
+    "gamesolve_solve": (_S, [_P, ctypes.POINTER(gs_solve_stats)]),
+    "gamesolve_get_value": (_S, [_P, _P, ctypes.c_int64]),
+    "gamesolve_get_policy": (_S, [_P, _P, _P]),
+    "gamesolve_improve": (_S, [_P, _P, _P, _P, _P]),
+    "gamesolve_policy_solve": (_S, [_P, _P, _P, _P, _P, ctypes.POINTER(gs_solve_stats)]),
+    "gamesolve_destroy": (None, [_P]),
+    "gamesolve_strerror": (ctypes.c_char_p, [_S]),
+    "gamesolve_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+    globals()[_name] = _fn
+
+
+class GameSolveError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = lib.gamesolve_strerror(status).decode()
+        detail = lib.gamesolve_last_error().decode()
+        super().__init__(f"{where}: {msg} ({detail})")
+
+
+def _check(st, where, allow=(GS_OK,)):
+    if st not in allow:
+        raise GameSolveError(st, where)
+    return st
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None stays NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _as(a, dtype):
+    if a is None or not isinstance(a, np.ndarray) and not isinstance(a, (list, tuple)):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def default_options(**kw) -> gs_options:
+    o = gs_options()
+    lib.gamesolve_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = v.cuda_stream
+        setattr(o, k, v)
+    return o
+
+
+class GameSolver:
+    """Owns one gs_solver.  Keyword arguments override gs_options fields."""
+
+    def __init__(self, **opts):
+        self.opts = default_options(**opts)
+        h = _P()
+        _check(lib.gamesolve_create(ctypes.byref(h), ctypes.byref(self.opts)), "gamesolve_create")
+        self.h = h
+        self.n = 0
+        self.m1 = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gamesolve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_isaacs_grid(self, side, variant=0, seed=1, xi=None):
+        xi = _as(xi, np.float64)
+        _check(lib.gamesolve_set_isaacs_grid(self.h, side, variant, seed, _ptr(xi)),
+               "gamesolve_set_isaacs_grid")
+        self.n = side * side
+        self.m1 = 5 if variant == 1 else 4
+
+    def set_game(self, n, m1, m2, row_ptr, col, prob, reward, mu):
+        row_ptr, col = _as(row_ptr, np.int64), _as(col, np.int32)
+        prob, reward = _as(prob, np.float64), _as(reward, np.float64)
+        _check(lib.gamesolve_set_game(self.h, n, m1, m2, _ptr(row_ptr), _ptr(col), _ptr(prob),
+                                      _ptr(reward), mu), "gamesolve_set_game")
+        self.n, self.m1 = n, m1
+
+    def set_initial(self, v0=None, alpha0=None, beta0=None):
+        v0, alpha0, beta0 = _as(v0, np.float64), _as(alpha0, np.uint8), _as(beta0, np.uint8)
+        _check(lib.gamesolve_set_initial(self.h, _ptr(v0), _ptr(alpha0), _ptr(beta0)),
+               "gamesolve_set_initial")
+
+    def solve(self, allow_notconv=False):
+        st = gs_solve_stats()
+        allow = (GS_OK, GS_ENOTCONV) if allow_notconv else (GS_OK,)
+        _check(lib.gamesolve_solve(self.h, ctypes.byref(st)), "gamesolve_solve", allow)
+        return st.as_dict()
+
+    def get_value(self, out=None):
+        out = np.empty(self.n, np.float64) if out is None else out
+        _check(lib.gamesolve_get_value(self.h, _ptr(out), self.n), "gamesolve_get_value")
+        return out
+
+    def get_policy(self, alpha_out=None, beta_out=None):
+        a = np.empty(self.n, np.uint8) if alpha_out is None else alpha_out
+        b = np.empty((self.n, self.m1), np.uint8) if beta_out is None else beta_out
+        _check(lib.gamesolve_get_policy(self.h, _ptr(a), _ptr(b)), "gamesolve_get_policy")
+        return a, b
+
+    def improve(self, v):
+        v = _as(v, np.float64)
+        a = np.empty(self.n, np.uint8)
+        b = np.empty((self.n, self.m1), np.uint8)
+        fv = np.empty(self.n, np.float64)
+        _check(lib.gamesolve_improve(self.h, _ptr(v), _ptr(a), _ptr(b), _ptr(fv)),
+               "gamesolve_improve")
+        return a, b, fv
+
+    def policy_solve(self, alpha, beta, w0=None):
+        alpha, beta, w0 = _as(alpha, np.uint8), _as(beta, np.uint8), _as(w0, np.float64)
+        w = np.empty(self.n, np.float64)
+        st = gs_solve_stats()
+        _check(lib.gamesolve_policy_solve(self.h, _ptr(alpha), _ptr(beta), _ptr(w0), _ptr(w),
+                                          ctypes.byref(st)), "gamesolve_policy_solve")
+        return w, st.as_dict()
+
+
+def exported_symbols():
+    """Names of the C-ABI functions this binding resolves from the library."""
+    return sorted(_SIGS)

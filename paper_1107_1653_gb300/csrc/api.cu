@@ -1,0 +1,242 @@
+// C ABI entry points (include/gamesolve.h): argument checks, error mapping,
+// and dispatch to the host orchestrator.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "solver.cuh"
+
+namespace gs {
+
+static thread_local char g_last_error[512] = "";
+
+void set_last_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+}
+
+template <typename F>
+static gs_status guarded(F&& f) {
+    try {
+        return f();
+    } catch (const Error& e) {
+        return e.st;
+    } catch (...) {
+        set_last_error("unexpected host exception");
+        return GS_ECUDA;
+    }
+}
+
+static bool is_pow2m1(int side) {
+    return side >= 1 && ((side + 1) & side) == 0;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+void gamesolve_default_options(gs_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = GS_PREC_FP64;
+    o->eps = 0.0;
+    o->max_outer = 1000;
+    o->max_inner = 1000;
+    o->nu1 = 1;
+    o->nu2 = 1;
+    o->max_cycles = 200;
+    o->lin_tol = 1e-15;
+    o->coarse_max = 64;
+    o->fmg = 0;
+    o->fmg_side = 31;
+    o->fmg_c = 0.1;
+    o->mu_mode = 0;
+    o->mem_budget = 0;
+    o->stream = nullptr;
+}
+
+gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
+    if (!out) {
+        set_last_error("create: out is NULL");
+        return GS_EINVAL;
+    }
+    *out = nullptr;
+    gs_options o;
+    if (opt) o = *opt;
+    else gamesolve_default_options(&o);
+    if (o.precision < 0 || o.precision > 2 || o.max_outer < 1 || o.max_inner < 1 || o.nu1 < 0 ||
+        o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 1 || !(o.lin_tol >= 0) ||
+        o.coarse_max < 1 || o.coarse_max > 64 || !(o.eps >= 0) || !(o.fmg_c > 0) ||
+        (o.fmg && !is_pow2m1(o.fmg_side)) || o.mu_mode < 0 || o.mu_mode > 1) {
+        set_last_error("create: invalid option value");
+        return GS_EINVAL;
+    }
+    return guarded([&]() -> gs_status {
+        int dev = 0;
+        GS_CUDA(cudaGetDevice(&dev));
+        auto* s = new gs_solver();
+        s->opt = o;
+        s->st = (cudaStream_t)o.stream;
+        cudaError_t e1 = cudaMalloc(&s->dsc, sizeof(DevScalars));
+        cudaError_t e2 = cudaMallocHost(&s->hsc, sizeof(DevScalars));
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            set_last_error("create: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+            if (s->dsc) cudaFree(s->dsc);
+            if (s->hsc) cudaFreeHost(s->hsc);
+            delete s;
+            cudaGetLastError();
+            return GS_ECUDA;
+        }
+        *out = s;
+        return GS_OK;
+    });
+}
+
+gs_status gamesolve_set_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2,
+                             const int64_t* row_ptr, const int32_t* col, const double* prob,
+                             const double* reward, double mu) {
+    if (!s || n < 1 || m1 < 1 || m1 > 8 || m2 < 1 || m2 > 8 || !row_ptr || !col || !prob ||
+        !reward || !(mu > 0.0 && mu < 1.0)) {
+        set_last_error("set_game: invalid argument");
+        return GS_EINVAL;
+    }
+    set_last_error("set_game: finite games are not supported by this build");
+    return GS_EINVAL;
+}
+
+gs_status gamesolve_set_isaacs_grid(gs_solver* s, int32_t side, int32_t variant, uint64_t seed,
+                                    const double* xi) {
+    if (!s || !is_pow2m1(side) || (variant != 0 && variant != 1)) {
+        set_last_error("set_isaacs_grid: side must be 2^k - 1 and variant 0 or 1");
+        return GS_EINVAL;
+    }
+    if (s->opt.fmg && side < s->opt.fmg_side) {
+        set_last_error("set_isaacs_grid: side below the FAMGpi coarsest side");
+        return GS_EINVAL;
+    }
+    return guarded([&]() -> gs_status {
+        auto P = build_isaacs_problem(s, side, variant, seed, xi);
+        s->prob = std::move(P);
+        reset_initial(s);
+        return GS_OK;
+    });
+}
+
+gs_status gamesolve_set_initial(gs_solver* s, const double* v0, const uint8_t* alpha0,
+                                const uint8_t* beta0) {
+    if (!s) return GS_EINVAL;
+    if (!s->prob) {
+        set_last_error("set_initial: no problem set");
+        return GS_ESTATE;
+    }
+    return guarded([&]() -> gs_status {
+        IsaacsGrid& g = *s->prob->grids.back();
+        const int m1 = g.variant == 1 ? 5 : 4;
+        if (alpha0 || beta0) {
+            // validate on the host side copy
+            std::vector<uint8_t> a(alpha0 ? g.n : 0), b(beta0 ? g.n * m1 : 0);
+            if (alpha0) GS_CUDA(cudaMemcpy(a.data(), alpha0, g.n, cudaMemcpyDefault));
+            if (beta0) GS_CUDA(cudaMemcpy(b.data(), beta0, g.n * m1, cudaMemcpyDefault));
+            for (uint8_t x : a)
+                if (x >= m1) { set_last_error("set_initial: alpha out of range"); return GS_EINVAL; }
+            for (uint8_t x : b)
+                if (x >= 4) { set_last_error("set_initial: beta out of range"); return GS_EINVAL; }
+        }
+        if (v0) {
+            GS_CUDA(cudaMemcpyAsync(g.v, v0, g.n * sizeof(double), cudaMemcpyDefault, s->st));
+            s->init_v = true;
+        }
+        if (alpha0) {
+            GS_CUDA(cudaMemcpyAsync(g.alpha, alpha0, g.n, cudaMemcpyDefault, s->st));
+            s->init_alpha = true;
+        }
+        if (beta0) {
+            pack_beta_upload(s, g, beta0);
+            s->init_beta = true;
+        }
+        GS_CUDA(cudaStreamSynchronize(s->st));
+        return GS_OK;
+    });
+}
+
+gs_status gamesolve_solve(gs_solver* s, gs_solve_stats* stats) {
+    if (!s) return GS_EINVAL;
+    if (!s->prob) {
+        set_last_error("solve: no problem set");
+        return GS_ESTATE;
+    }
+    return guarded([&]() { return run_solve(s, stats); });
+}
+
+gs_status gamesolve_get_value(const gs_solver* s, double* v_out, int64_t n) {
+    if (!s || !v_out) return GS_EINVAL;
+    if (!s->prob) return GS_ESTATE;
+    const IsaacsGrid& g = *s->prob->grids.back();
+    if (n != (int64_t)g.n) {
+        set_last_error("get_value: n = %lld, problem has %zu states", (long long)n, g.n);
+        return GS_EINVAL;
+    }
+    return guarded([&]() -> gs_status {
+        GS_CUDA(cudaMemcpyAsync(v_out, g.v, g.n * sizeof(double), cudaMemcpyDefault, s->st));
+        GS_CUDA(cudaStreamSynchronize(s->st));
+        return GS_OK;
+    });
+}
+
+gs_status gamesolve_get_policy(const gs_solver* s, uint8_t* alpha, uint8_t* beta) {
+    if (!s) return GS_EINVAL;
+    if (!s->prob) return GS_ESTATE;
+    gs_solver* sm = const_cast<gs_solver*>(s);
+    return guarded([&]() -> gs_status {
+        const IsaacsGrid& g = *s->prob->grids.back();
+        if (alpha) GS_CUDA(cudaMemcpyAsync(alpha, g.alpha, g.n, cudaMemcpyDefault, s->st));
+        if (beta) unpack_beta_download(sm, g, beta);
+        GS_CUDA(cudaStreamSynchronize(s->st));
+        return GS_OK;
+    });
+}
+
+gs_status gamesolve_improve(gs_solver* s, const double* v, uint8_t* alpha_out, uint8_t* beta_out,
+                            double* fv_out) {
+    if (!s || !v) return GS_EINVAL;
+    if (!s->prob) return GS_ESTATE;
+    return guarded([&]() { return run_improve(s, v, alpha_out, beta_out, fv_out); });
+}
+
+gs_status gamesolve_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* beta,
+                                 const double* w0, double* w_out, gs_solve_stats* stats) {
+    if (!s || !alpha || !beta || !w_out) return GS_EINVAL;
+    if (!s->prob) return GS_ESTATE;
+    return guarded([&]() { return run_policy_solve(s, alpha, beta, w0, w_out, stats); });
+}
+
+void gamesolve_destroy(gs_solver* s) {
+    if (!s) return;
+    if (s->st) cudaStreamSynchronize(s->st);
+    else cudaDeviceSynchronize();
+    s->prob.reset();
+    if (s->dsc) cudaFree(s->dsc);
+    if (s->hsc) cudaFreeHost(s->hsc);
+    delete s;
+}
+
+const char* gamesolve_strerror(gs_status st) {
+    switch (st) {
+    case GS_OK: return "ok";
+    case GS_EINVAL: return "invalid argument";
+    case GS_ENOMEM: return "out of device memory or over the memory budget";
+    case GS_ENOTCONV: return "iteration caps reached before convergence";
+    case GS_ETIMEOUT: return "a bounded device-side wait timed out";
+    case GS_ECUDA: return "CUDA error";
+    case GS_ESTATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char* gamesolve_last_error(void) { return g_last_error; }
+
+}  // extern "C"

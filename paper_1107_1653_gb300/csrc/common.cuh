@@ -1,0 +1,96 @@
+// Shared definitions of the CUDA path (kernels and host orchestration).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/gamesolve.h"
+
+namespace gs {
+
+// ---------------------------------------------------------------- errors
+void set_last_error(const char* fmt, ...);
+
+struct Error {
+    gs_status st;
+};
+
+#define GS_CUDA(call)                                                           \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) {                                                \
+            ::gs::set_last_error("%s:%d %s: %s", __FILE__, __LINE__, #call,     \
+                                 cudaGetErrorString(e_));                       \
+            throw ::gs::Error{GS_ECUDA};                                        \
+        }                                                                       \
+    } while (0)
+
+#define GS_CHECK_LAUNCH() GS_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------- stencils
+// Directions of a 9-point stencil on a grid whose first index i (along x1) is
+// the fast one: C centre, W (i-1), E (i+1), S (j-1), N (j+1) and diagonals.
+enum Dir { DC = 0, DW = 1, DE = 2, DS = 3, DN = 4, DSW = 5, DSE = 6, DNW = 7, DNE = 8 };
+__host__ __device__ constexpr int dir_di(int d) {
+    return d == DW || d == DSW || d == DNW ? -1 : (d == DE || d == DSE || d == DNE ? 1 : 0);
+}
+__host__ __device__ constexpr int dir_dj(int d) {
+    return d == DS || d == DSW || d == DSE ? -1 : (d == DN || d == DNW || d == DNE ? 1 : 0);
+}
+__host__ __device__ constexpr int dir_of(int di, int dj) {
+    return dj == 0 ? (di == 0 ? DC : (di < 0 ? DW : DE))
+                   : (dj < 0 ? (di == 0 ? DS : (di < 0 ? DSW : DSE))
+                             : (di == 0 ? DN : (di < 0 ? DNW : DNE)));
+}
+
+// Interpolation weights of one coarse cell (I, J), I, J in [0, sc]: the fine
+// points (2I, 2J+1) (x-edge, between coarse (I-1,J) and (I,J)), (2I+1, 2J)
+// (y-edge, between (I,J-1) and (I,J)) and (2I, 2J) (cell corner, between the
+// four coarse points around it).  Stored as P[k * ncell + cell].
+enum PW { PXW = 0, PXE = 1, PYS = 2, PYN = 3, PSW = 4, PSE = 5, PNW = 6, PNE = 7 };
+
+// Policy code of a fine Isaacs row: 4 a + b for a, b in {0..3}; 16 = stop.
+constexpr int kStopCode = 16;
+constexpr int kCodes = 17;
+
+// Constants of one Isaacs grid, resident in device memory.
+struct IsaacsConsts {
+    int side;
+    int variant;          // 0 plain, 1 obstacle
+    double h, mu, kappa;  // kappa = 1 - mu, evaluated without cancellation
+    // Row of A = I - mu M for each code, in direction order C, W, E, S, N.
+    double am[kCodes][5];
+    // Transition probabilities per code (a < 4) in the order of the neighbours
+    // E (+x1), W (-x1), N (+x2), S (-x2), self.
+    double p[16][5];
+    // Reward offset (1 - mu) 0.1 (a - b).
+    double dr[4][4];
+    // float copies of the off-diagonal entries of am (index 1..4 used).
+    float amf[kCodes][5];
+};
+
+// Device-side scalars: reductions written by kernels, read by the host once
+// per decision.  Non-negative doubles are reduced as their bit patterns.
+struct DevScalars {
+    unsigned long long vmax;     // |v|_inf (bits)
+    unsigned long long res;      // |F(v) - v|_inf or |b - A v|_inf (bits)
+    double res_sq;               // sum of squares (statistics only)
+    int changed;                 // policy entries changed by an improvement
+    int pad;
+};
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* dst, double v) {
+    atomicMax(dst, (unsigned long long)__double_as_longlong(v));
+}
+
+inline double bits_to_double(unsigned long long b) {
+    double d;
+    static_assert(sizeof(d) == sizeof(b), "");
+    __builtin_memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+inline unsigned int div_up(size_t a, size_t b) { return (unsigned int)((a + b - 1) / b); }
+
+}  // namespace gs

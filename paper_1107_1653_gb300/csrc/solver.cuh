@@ -1,0 +1,99 @@
+// Host-side solver objects: device memory, multigrid hierarchies and the
+// policy-iteration driver.
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace gs {
+
+// All device allocations of one problem, counted against the memory budget.
+class Arena {
+public:
+    Arena(size_t budget, size_t already_held) : budget_(budget), base_(already_held) {}
+    ~Arena();
+    Arena(const Arena&) = delete;
+    Arena& operator=(const Arena&) = delete;
+    template <typename T>
+    T* alloc(size_t count) {
+        return static_cast<T*>(raw(count * sizeof(T)));
+    }
+    size_t held() const { return held_; }
+
+private:
+    void* raw(size_t bytes);
+    size_t budget_, base_, held_ = 0;
+    std::vector<void*> ptrs_;
+};
+
+// One multigrid level.  Level 0 of an Isaacs hierarchy is the implicit fine
+// operator (policy codes); levels >= 1 hold explicit 9-point stencils.
+struct Level {
+    int side = 0;
+    size_t n = 0;
+    double* A64 = nullptr;     // [9][n], levels >= 1
+    float* A32 = nullptr;      // [9][n]: row sum, then off-diagonals
+    double* P64 = nullptr;     // interpolation from level+1: [8][(sc+1)^2]
+    float* P32 = nullptr;
+    double *u64 = nullptr, *f64 = nullptr, *r64 = nullptr;
+    float *u32 = nullptr, *f32 = nullptr, *r32 = nullptr;
+};
+
+// An Isaacs grid with its policies, value and multigrid hierarchy.
+struct IsaacsGrid {
+    int side = 0, variant = 0;
+    size_t n = 0;
+    IsaacsConsts Kh{};
+    IsaacsConsts* Kd = nullptr;
+    double *r0 = nullptr, *v = nullptr, *rhs = nullptr, *fv = nullptr;
+    uint8_t *alpha = nullptr, *code = nullptr, *beta4 = nullptr;
+    uint32_t* beta = nullptr;
+    std::vector<Level> lv;
+    double* inv = nullptr;     // explicit inverse of the coarsest operator
+    int* dstatus = nullptr;
+};
+
+struct Problem {
+    explicit Problem(size_t budget, size_t held) : arena(budget, held) {}
+    Arena arena;
+    int kind = 0;                                // 1 Isaacs
+    std::vector<std::unique_ptr<IsaacsGrid>> grids;   // FAMGpi levels, coarse to fine
+    double* xi = nullptr;                        // finest-grid noise (when given)
+};
+
+struct Counters {
+    int outer = 0, systems = 0, cycles = 0;
+    double res_inf = 0, res_l2 = 0;
+    bool converged = false;
+    double last_lin_res = 0;
+};
+
+}  // namespace gs
+
+struct gs_solver {
+    gs_options opt;
+    cudaStream_t st = nullptr;
+    gs::DevScalars* dsc = nullptr;     // device scalars
+    gs::DevScalars* hsc = nullptr;     // pinned host mirror
+    std::unique_ptr<gs::Problem> prob;
+    bool init_v = false, init_alpha = false, init_beta = false;
+    int last_levels = 0;
+};
+
+namespace gs {
+
+IsaacsConsts make_isaacs_consts(int side, int variant, int mu_mode);
+std::unique_ptr<Problem> build_isaacs_problem(gs_solver* s, int side, int variant, uint64_t seed,
+                                              const double* xi);
+void reset_initial(gs_solver* s);
+gs_status run_solve(gs_solver* s, gs_solve_stats* stats);
+gs_status run_improve(gs_solver* s, const double* v, uint8_t* alpha_out, uint8_t* beta_out,
+                      double* fv_out);
+gs_status run_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* beta,
+                           const double* w0, double* w_out, gs_solve_stats* stats);
+void pack_beta_upload(gs_solver* s, IsaacsGrid& g, const uint8_t* beta_host);
+void unpack_beta_download(gs_solver* s, const IsaacsGrid& g, uint8_t* beta_out);
+
+}  // namespace gs

@@ -1,0 +1,50 @@
+"""The C-ABI library loads and exports every entry point include/gamesolve.h
+declares; host-side argument checks need no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "gamesolve.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gamesolve_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def gs():
+    if not os.path.exists(os.path.join(ROOT, "paper_1107_1653_gb300", "libgamesolve.so")):
+        pytest.skip("library not built")
+    import paper_1107_1653_gb300 as pkg
+    return pkg
+
+
+def test_every_declared_symbol_is_exported(gs):
+    names = declared()
+    assert len(names) >= 13
+    for name in names:
+        assert hasattr(gs.lib, name), name
+    assert sorted(gs.exported_symbols()) == names
+
+
+def test_struct_layouts_match_header(gs):
+    # gs_options: 96 bytes with the stream pointer last; gs_solve_stats: 48 bytes
+    assert ctypes.sizeof(gs.gs_options) == 96 and gs.gs_options.stream.offset == 88
+    assert ctypes.sizeof(gs.gs_solve_stats) == 48
+
+
+def test_host_side_checks_without_gpu(gs):
+    o = gs.default_options()
+    assert o.precision == gs.GS_PREC_FP64 and o.nu1 == 1 and o.nu2 == 1
+    assert gs.lib.gamesolve_strerror(gs.GS_ENOTCONV).startswith(b"iteration caps")
+    # NULL out-pointer and invalid options are rejected before any CUDA call
+    assert gs.lib.gamesolve_create(None, None) == gs.GS_EINVAL
+    bad = gs.default_options(coarse_max=0)
+    h = ctypes.c_void_p()
+    assert gs.lib.gamesolve_create(ctypes.byref(h), ctypes.byref(bad)) == gs.GS_EINVAL
+    assert gs.lib.gamesolve_solve(None, None) == gs.GS_EINVAL
+    gs.lib.gamesolve_destroy(None)

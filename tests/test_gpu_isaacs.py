@@ -1,0 +1,156 @@
+"""GPU parity of the Isaacs path against the FP64 oracle, through the C-ABI.
+
+Bars: value to 1e-10 relative max-norm (FP64 path) and 1e-9 (mixed path);
+policies bit-exact wherever the oracle's max-min gap exceeds 1e-8; integer
+work (noise generation, interpolated policies) bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.isaacs import isaacs_game, default_alpha0
+from oracle.fmg import famg_pi, interp_value, interp_policy
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-9}
+_CACHE = {}
+
+
+def oracle_solve(side, variant, seed):
+    key = (side, variant, seed)
+    if key not in _CACHE:
+        game = isaacs_game(side, variant, seed=seed)
+        _CACHE[key] = (game, oracle.policy_iteration(game, alpha0=default_alpha0(side, variant)))
+    return _CACHE[key]
+
+
+def rel_err(v, ref):
+    return np.max(np.abs(v - ref)) / max(np.max(np.abs(ref)), 1e-300)
+
+
+def check_policies(alpha, beta, ref, m1):
+    sure_a = ref.gap_max > 1e-8
+    assert np.array_equal(alpha[sure_a], ref.alpha[sure_a])
+    sure_b = ref.gap_min[:, :4] > 1e-8
+    assert np.array_equal(beta[:, :4][sure_b], ref.beta[:, :4][sure_b])
+    assert beta.shape == (len(alpha), m1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("side", [1, 3, 7, 15, 63, 255])
+def test_solve_parity_plain(gs, side, prec):
+    game, ref = oracle_solve(side, 0, 1)
+    with gs.GameSolver(precision=prec) as s:
+        s.set_isaacs_grid(side, 0, 1)
+        st = s.solve()
+        v = s.get_value()
+        a, b = s.get_policy()
+    assert st["converged"] == 1
+    assert rel_err(v, ref.v) <= TOL[prec], (rel_err(v, ref.v), st)
+    check_policies(a, b, ref, 4)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("side", [15, 63])
+def test_solve_parity_obstacle(gs, side, prec):
+    game, ref = oracle_solve(side, 1, 2)
+    with gs.GameSolver(precision=prec) as s:
+        s.set_isaacs_grid(side, 1, 2)
+        st = s.solve()
+        v = s.get_value()
+        a, b = s.get_policy()
+    assert st["converged"] == 1
+    assert rel_err(v, ref.v) <= TOL[prec]
+    check_policies(a, b, ref, 5)
+
+
+def test_noise_generators_agree(gs):
+    """The CUDA SplitMix64 stream and synth's give bit-identical solves."""
+    side, seed = 63, 12345
+    out = []
+    for xi in (None, synth.isaacs_noise(side, seed)):
+        with gs.GameSolver() as s:
+            s.set_isaacs_grid(side, 0, seed, xi=xi)
+            s.solve()
+            out.append(s.get_value())
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("side", [63, 255])
+def test_improve_parity(gs, side):
+    """One policy improvement (Eq. (eq1)/(ILPI)) at a perturbed value."""
+    game, ref = oracle_solve(side, 0, 1)
+    rng = np.random.default_rng(side)
+    v = ref.v + 1e-3 * rng.standard_normal(ref.v.shape)
+    alpha0 = rng.integers(0, 4, size=game.n).astype(np.uint8)
+    beta0 = rng.integers(0, 4, size=(game.n, 4)).astype(np.uint8)
+    a_ref, b_ref, fv_ref = oracle.improve(game, v, alpha0, beta0)
+    q = oracle.shapley_q(game, v)
+    with gs.GameSolver() as s:
+        s.set_isaacs_grid(side, 0, 1)
+        s.set_initial(alpha0=alpha0, beta0=beta0)
+        a, b, fv = s.improve(v)
+    assert np.max(np.abs(fv - fv_ref)) <= 1e-14
+    fa = q.min(axis=2)
+    srt = np.sort(fa, axis=1)
+    sure_a = srt[:, -1] - srt[:, -2] > 1e-8
+    assert np.array_equal(a[sure_a], a_ref[sure_a])
+    sb = np.sort(q, axis=2)
+    sure_b = sb[:, :, 1] - sb[:, :, 0] > 1e-8
+    assert np.array_equal(b[sure_b], b_ref[sure_b])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("side", [7, 63, 255])
+def test_policy_solve_parity(gs, side, prec):
+    """The multigrid solve of Eq. (LSPI) for fixed policies vs a direct solve."""
+    game, _ = oracle_solve(side, 0, 1)
+    rng = np.random.default_rng(7)
+    alpha = rng.integers(0, 4, size=game.n).astype(np.uint8)
+    beta = rng.integers(0, 4, size=(game.n, 4)).astype(np.uint8)
+    A, r = oracle.policy_system(game, alpha, beta)
+    w_ref = oracle.solve_policy_system(A, r)
+    with gs.GameSolver(precision=prec) as s:
+        s.set_isaacs_grid(side, 0, 1)
+        w, st = s.policy_solve(alpha, beta)
+    assert rel_err(w, w_ref) <= TOL[prec] / 10, (rel_err(w, w_ref), st)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fmg_parity(gs, variant):
+    """FAMGpi (Algorithm 4) from side 15 to 127 reaches the oracle's value."""
+    side, seed = 127, 3
+    _, ref = oracle_solve(side, variant, seed)
+    with gs.GameSolver(fmg=1, fmg_side=15, fmg_c=0.1 if variant == 0 else 0.01) as s:
+        s.set_isaacs_grid(side, variant, seed)
+        st = s.solve()
+        v = s.get_value()
+        a, b = s.get_policy()
+    assert st["fmg_levels"] == 4 and st["converged"] == 1
+    assert rel_err(v, ref.v) <= 1e-10
+    check_policies(a, b, ref, 5 if variant else 4)
+
+
+def test_status_codes(gs):
+    with gs.GameSolver() as s:
+        with pytest.raises(gs.GameSolveError) as e:
+            s.solve()
+        assert e.value.status == gs.GS_ESTATE
+        with pytest.raises(gs.GameSolveError) as e:
+            s.set_isaacs_grid(10, 0, 1)
+        assert e.value.status == gs.GS_EINVAL
+        s.set_isaacs_grid(15, 0, 1)
+        with pytest.raises(gs.GameSolveError) as e:
+            s.set_initial(alpha0=np.full(225, 7, np.uint8))
+        assert e.value.status == gs.GS_EINVAL
+    with gs.GameSolver(max_outer=1, max_inner=1) as s:
+        s.set_isaacs_grid(63, 0, 1)
+        st = gs.gs_solve_stats()
+        code = gs.lib.gamesolve_solve(s.h, gs.ctypes.byref(st))
+        assert code == gs.GS_ENOTCONV and st.outer == 1
+    with gs.GameSolver(mem_budget=1 << 16) as s:
+        with pytest.raises(gs.GameSolveError) as e:
+            s.set_isaacs_grid(255, 0, 1)
+        assert e.value.status == gs.GS_ENOMEM
