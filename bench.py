@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""Isaacs solves/s at 1023^2 on one GB300 (mixed float32/float64 vs float64).
+
+One step = one full AMGpi solve (policy iteration with multigrid linear
+solves) of the 1023 x 1023 finite-difference Isaacs game, plain variant,
+started from scratch (v = 0, default policies), run until MAX's policy is
+stable, with every linear system solved to the float64 residual floor.
+The reward noise is generated on the device from the seed, so the inputs are
+resident when the timed region starts.  Between timed steps a 256 MiB buffer
+is written to flush the L2 (the solve's working set, ~60 MB, fits in L2).
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Isaacs solves/s at 1023^2 (FP32+refine vs FP64), HBM GB/s, p50/p99 latency"
+SIDE = 1023
+SEED = 2
+
+# Algorithmic bytes per launch of each traced kernel class, per fine state
+# (what the method must move; see the design notes, section "Kernels").
+BYTES_PER_STATE = {
+    # one colour of the red-black C/F relaxation over half the points:
+    # code (1 B) + f + u written for n/2 points, the other colour's u read once
+    ("fine_relax", "mixed"): 0.5 * (1 + 4 + 4) + 0.5 * 4,
+    ("fine_relax", "fp64"): 0.5 * (1 + 8 + 8) + 0.5 * 8,
+    # float64 refinement residual: code, f, v read; r written (float32 / float64)
+    ("refine", "mixed"): 1 + 8 + 8 + 4,
+    ("refine", "fp64"): 1 + 8 + 8 + 8,
+    # in-cycle fine residual: code, f, u read; r written
+    ("fine_residual", "mixed"): 1 + 4 + 4 + 4,
+    ("fine_residual", "fp64"): 1 + 8 + 8 + 8,
+}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.fh = tempfile.TemporaryFile(mode="w+")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.fh.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.fh.read())) if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(systems_per_solve: int, outer_per_solve: int):
+    """Seconds of one oracle policy evaluation + improvement at 1023^2.
+
+    The sample is one sparse-LU solve of the policy-fixed system (Eq. (LSPI))
+    and one full improvement sweep; a whole oracle solve performs
+    `systems_per_solve` of the former and about as many improvements.
+    """
+    import numpy as np
+    import oracle
+    from oracle.isaacs import isaacs_game
+    game = isaacs_game(SIDE, 0, seed=SEED)
+    n = game.n
+    alpha = np.zeros(n, np.uint8)
+    beta = np.zeros((n, 4), np.uint8)
+    t0 = time.perf_counter()
+    A, r = oracle.policy_system(game, alpha, beta)
+    w = oracle.solve_policy_system(A, r, "lu")
+    t1 = time.perf_counter()
+    oracle.improve(game, w, alpha, beta)
+    t2 = time.perf_counter()
+    t_solve = systems_per_solve * (t1 - t0) + (systems_per_solve + outer_per_solve) * (t2 - t1)
+    return t_solve, t1 - t0, t2 - t1
+
+
+# Policy iterations the FP64 oracle needs for this workload (1023^2, seed 2),
+# counted by a full oracle run (tests/golden/oracle_counts_1023.txt).
+def oracle_counts():
+    path = os.path.join(ROOT, "tests", "golden", "oracle_counts_1023.txt")
+    d = {}
+    with open(path) as fh:
+        for ln in fh:
+            if ln.strip() and not ln.startswith("#"):
+                k, v = ln.split()
+                d[k] = int(v)
+    return d["systems"], d["outer"]
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    systems, outer = oracle_counts()
+    times = []
+    for k in range(args.warmup + args.steps):
+        t_solve, _, _ = oracle_sample(systems, outer)
+        if k >= args.warmup:
+            times.append(t_solve)
+    sec = statistics.mean(times)
+    value = 1.0 / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"isaacs_{SIDE}x{SIDE}_plain_amgpi", "side": SIDE, "seed": SEED,
+                   "variant": "plain", "solver": "oracle PI + SuperLU", "parallelism": "none"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: one sparse-LU policy evaluation + one improvement at "
+                                   f"{SIDE}^2, scaled by the oracle's {systems} systems / {outer} "
+                                   f"outer iterations per solve"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_1107_1653_gb300 as gs
+
+    stream = torch.cuda.current_stream()
+    n = SIDE * SIDE
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(precision, steps, warmup, trace=None):
+        s = gs.GameSolver(precision=precision, fmg=args.fmg, fmg_side=31, stream=stream)
+        s.set_isaacs_grid(SIDE, 0, SEED)
+        for _ in range(warmup):
+            s.solve()
+        if trace:
+            s.trace(trace)
+        launches0 = gs.lib.gamesolve_kernel_launches()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        per_step, stats = [], None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t_wall = time.perf_counter()
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            stats = s.solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per_step.append(e0.elapsed_time(e1))
+        t_wall = time.perf_counter() - t_wall
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        launches = gs.lib.gamesolve_kernel_launches() - launches0
+        tr = s.trace_read() if trace else (0.0, 0)
+        v = s.get_value()
+        s.close()
+        return per_step, stats, launches, tr, v, t_wall
+
+    clocks = ClockSampler(local)
+    prec = args.precision
+    per_step, stats, launches, (tr_ms, tr_n), v_main, t_wall = timed(
+        prec, args.steps, args.warmup, trace=args.trace_kernel)
+    clk = clocks.stop()
+    ms = statistics.mean(per_step)
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * 1000.0 / ms_max
+
+    # the other precision, for the FP32+refine vs FP64 comparison
+    other = "fp64" if prec != "fp64" else "mixed"
+    o_steps, o_stats, _, _, v_other, _ = timed(other, max(2, args.steps // 2), 1)
+    o_ms = statistics.mean(o_steps)
+    rel = float(np.max(np.abs(v_main - v_other)) / np.max(np.abs(v_other)))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": f"isaacs_{SIDE}x{SIDE}_plain_{'famgpi' if args.fmg else 'amgpi'}_{prec}",
+                   "side": SIDE, "states": n, "seed": SEED, "variant": "plain",
+                   "precision": prec, "fmg": bool(args.fmg),
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between steps (256 MiB write)",
+                   "outer": stats["outer"], "systems": stats["systems"], "cycles": stats["cycles"],
+                   "levels": stats["levels"], "res_inf": stats["res_inf"]},
+        "p50_ms": statistics.median(per_step),
+        "p99_ms": sorted(per_step)[min(len(per_step) - 1, int(0.99 * len(per_step)))],
+        "wall_s_timed_loop": t_wall,
+        "gpu_launches": int(launches),
+        "compare": {other: {"value": 1000.0 / o_ms, "ms_per_step": o_ms,
+                            "outer": o_stats["outer"], "systems": o_stats["systems"],
+                            "cycles": o_stats["cycles"]},
+                    "rel_diff_vs_" + other: rel},
+    }
+    if clk:
+        line["clocks"] = clk
+
+    # roofline of the traced kernel class
+    peak, peak_kind = load_peaks()
+    if tr_n:
+        bpl = BYTES_PER_STATE[(args.trace_kernel, "mixed" if prec != "fp64" else "fp64")] * n
+        avg_s = tr_ms * 1e-3 / tr_n
+        ach = bpl / avg_s / 1e9
+        line["roofline"] = {"kernel": args.trace_kernel, "bound": "hbm", "achieved": ach,
+                            "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                            "peak_source": peak_kind, "traffic": None,
+                            "launches": tr_n, "avg_us": avg_s * 1e6,
+                            "algorithmic_bytes_per_launch": bpl}
+
+    # end to end through the C-ABI with host buffers
+    if not args.no_e2e:
+        import synth
+        xi_h = torch.from_numpy(synth.isaacs_noise(SIDE, SEED)).pin_memory()
+        v_h = torch.empty(n, dtype=torch.float64).pin_memory()
+        a_h = torch.empty(n, dtype=torch.uint8).pin_memory()
+        b_h = torch.empty((n, 4), dtype=torch.uint8).pin_memory()
+        s = gs.GameSolver(precision=prec, fmg=args.fmg, fmg_side=31, stream=stream)
+        e2e = []
+        for k in range(1 + max(2, args.steps // 2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.set_isaacs_grid(SIDE, 0, SEED, xi=xi_h)
+            s.solve()
+            s.get_value(out=v_h)
+            s.get_policy(alpha_out=a_h, beta_out=b_h)
+            t1 = time.perf_counter()
+            if k:
+                e2e.append(t1 - t0)
+        s.close()
+        line["e2e"] = {"value": 1.0 / statistics.mean(e2e), "unit": "solves/s",
+                       "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n + n + 4 * n}
+
+    # CPU oracle baseline on a bounded sample (rank 0, one GPU only)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        systems, outer = oracle_counts()
+        t_solve, t_lu, t_imp = oracle_sample(systems, outer)
+        line["cpu_baseline"] = {
+            "value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"one sparse-LU policy evaluation ({t_lu:.1f} s) + one improvement "
+                      f"({t_imp:.1f} s) at {SIDE}^2, scaled by the oracle's {systems} systems / "
+                      f"{outer} outer iterations per solve"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_bf16"])
+    ap.add_argument("--fmg", type=int, default=0)
+    ap.add_argument("--trace-kernel", default="fine_relax",
+                    choices=sorted(k for k, _ in BYTES_PER_STATE))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -120,8 +120,9 @@ gs_status gamesolve_set_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2,
  * xi: per-state noise, side*side doubles in row-major order (first
  * coordinate fastest), host or device; NULL draws xi(x) = 0.1 u_x - 0.05 with
  * u_x the x-th double of the SplitMix64 stream `seed`.
- * Errors: GS_EINVAL if side < 1, side != 2^k - 1 when options.fmg is set, or
- * variant not in {0, 1}. */
+ * The multigrid hierarchy coarsens by 2 per level, so side must be 2^k - 1.
+ * Errors: GS_EINVAL if side is not 2^k - 1 (k >= 1), side is below
+ * options.fmg_side when options.fmg is set, or variant is not 0 or 1. */
 gs_status gamesolve_set_isaacs_grid(gs_solver* s, int32_t side, int32_t variant,
                                     uint64_t seed, const double* xi);
 
@@ -161,6 +162,30 @@ gs_status gamesolve_improve(gs_solver* s, const double* v, uint8_t* alpha_out,
  * final |b - A w|_inf in res_inf. */
 gs_status gamesolve_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* beta,
                                  const double* w0, double* w_out, gs_solve_stats* stats);
+
+/* Kernel classes that gamesolve_trace can time (diagnostics). */
+typedef enum {
+    GS_K_NONE = 0,
+    GS_K_IMPROVE = 1,        /* policy improvement fused with assembly, fine level */
+    GS_K_FINE_RELAX = 2,     /* one colour of the fine-level C/F relaxation */
+    GS_K_FINE_RESIDUAL = 3,  /* fine-level residual inside a V-cycle */
+    GS_K_SETUP = 4,          /* interpolation weights, Galerkin products, coarsest inverse */
+    GS_K_COARSE = 5,         /* everything a V-cycle does on levels >= 1 */
+    GS_K_TRANSFER = 6,       /* fine-level restriction and prolongation */
+    GS_K_REFINE = 7          /* float64 residual b - A v of the fine system (refinement / stopping test) */
+} gs_kernel_class;
+
+/* Selects one kernel class whose launches the following solves bracket with
+ * CUDA events on the solver's stream (GS_K_NONE: off) and clears the totals.
+ * Costs a few microseconds of host time per bracketed launch. */
+gs_status gamesolve_trace(gs_solver* s, int32_t kernel_class);
+
+/* Totals of the traced class since gamesolve_trace: summed device time in
+ * milliseconds and number of launches.  Either pointer may be NULL. */
+gs_status gamesolve_trace_read(gs_solver* s, double* total_ms, int64_t* launches);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t gamesolve_kernel_launches(void);
 
 /* Frees the solver and all of its device memory.  NULL is a no-op. */
 void gamesolve_destroy(gs_solver* s);

@@ -22,6 +22,8 @@ lib = ctypes.CDLL(LIB_PATH)
 
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_ENOTCONV, GS_ETIMEOUT, GS_ECUDA, GS_ESTATE = range(7)
 GS_PREC_FP64, GS_PREC_MIXED, GS_PREC_MIXED_BF16 = range(3)
+KERNEL_CLASSES = {"none": 0, "improve": 1, "fine_relax": 2, "fine_residual": 3, "setup": 4,
+                  "coarse": 5, "transfer": 6, "refine": 7}
 PRECISIONS = {"fp64": GS_PREC_FP64, "mixed": GS_PREC_MIXED, "mixed_bf16": GS_PREC_MIXED_BF16}
 
 
@@ -65,6 +67,9 @@ _SIGS = {
     "gamesolve_get_policy": (_S, [_P, _P, _P]),
     "gamesolve_improve": (_S, [_P, _P, _P, _P, _P]),
     "gamesolve_policy_solve": (_S, [_P, _P, _P, _P, _P, ctypes.POINTER(gs_solve_stats)]),
+    "gamesolve_trace": (_S, [_P, ctypes.c_int32]),
+    "gamesolve_trace_read": (_S, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+    "gamesolve_kernel_launches": (ctypes.c_uint64, []),
     "gamesolve_destroy": (None, [_P]),
     "gamesolve_strerror": (ctypes.c_char_p, [_S]),
     "gamesolve_last_error": (ctypes.c_char_p, []),
@@ -195,6 +200,17 @@ class GameSolver:
         _check(lib.gamesolve_improve(self.h, _ptr(v), _ptr(a), _ptr(b), _ptr(fv)),
                "gamesolve_improve")
         return a, b, fv
+
+    def trace(self, kernel_class):
+        cls = KERNEL_CLASSES[kernel_class] if isinstance(kernel_class, str) else kernel_class
+        _check(lib.gamesolve_trace(self.h, cls), "gamesolve_trace")
+
+    def trace_read(self):
+        ms = ctypes.c_double()
+        cnt = ctypes.c_int64()
+        _check(lib.gamesolve_trace_read(self.h, ctypes.byref(ms), ctypes.byref(cnt)),
+               "gamesolve_trace_read")
+        return ms.value, cnt.value
 
     def policy_solve(self, alpha, beta, w0=None):
         alpha, beta, w0 = _as(alpha, np.uint8), _as(beta, np.uint8), _as(w0, np.float64)

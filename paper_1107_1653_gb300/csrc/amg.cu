@@ -170,7 +170,7 @@ void launch_interp9(const double* A, int side, double* P, float* P32, cudaStream
     Src9 src{A, side, (size_t)side * side};
     k_interp_edges<<<div_up(ncell, kBlock), kBlock, 0, st>>>(src, sc, P, P32);
     k_interp_corners<<<div_up(ncell, kBlock), kBlock, 0, st>>>(src, sc, P, P32);
-    GS_CHECK_LAUNCH();
+    GS_CHECK_LAUNCH_N(2);
 }
 
 void launch_rap9(const double* A, int side, const double* P, double* Ac, cudaStream_t st) {

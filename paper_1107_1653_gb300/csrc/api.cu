@@ -214,8 +214,29 @@ gs_status gamesolve_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8
     return guarded([&]() { return run_policy_solve(s, alpha, beta, w0, w_out, stats); });
 }
 
+gs_status gamesolve_trace(gs_solver* s, int32_t kernel_class) {
+    if (!s || kernel_class < GS_K_NONE || kernel_class > GS_K_REFINE) return GS_EINVAL;
+    return guarded([&]() -> gs_status {
+        trace_reset(s, kernel_class);
+        return GS_OK;
+    });
+}
+
+gs_status gamesolve_trace_read(gs_solver* s, double* total_ms, int64_t* launches) {
+    if (!s) return GS_EINVAL;
+    return guarded([&]() -> gs_status {
+        trace_harvest(s);
+        if (total_ms) *total_ms = s->trace.ms;
+        if (launches) *launches = s->trace.launches;
+        return GS_OK;
+    });
+}
+
+uint64_t gamesolve_kernel_launches(void) { return launch_count(); }
+
 void gamesolve_destroy(gs_solver* s) {
     if (!s) return;
+    for (cudaEvent_t e : s->trace.ev) cudaEventDestroy(e);
     if (s->st) cudaStreamSynchronize(s->st);
     else cudaDeviceSynchronize();
     s->prob.reset();

@@ -26,7 +26,14 @@ struct Error {
         }                                                                       \
     } while (0)
 
-#define GS_CHECK_LAUNCH() GS_CUDA(cudaGetLastError())
+// Counts kernels launched by the library (process-wide) for launch accounting.
+void note_launches(int k);
+#define GS_CHECK_LAUNCH_N(k)          \
+    do {                              \
+        ::gs::note_launches(k);       \
+        GS_CUDA(cudaGetLastError());  \
+    } while (0)
+#define GS_CHECK_LAUNCH() GS_CHECK_LAUNCH_N(1)
 
 // ---------------------------------------------------------------- stencils
 // Directions of a 9-point stencil on a grid whose first index i (along x1) is

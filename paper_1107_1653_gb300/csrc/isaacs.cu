@@ -444,7 +444,7 @@ void launch_l0_interp(const IsaacsConsts* K, int side, const uint8_t* code, doub
     Src5 src{K, code, side};
     k_interp_edges<<<div_up(ncell, kBlock), kBlock, 0, st>>>(src, sc, P, P32);
     k_interp_corners<<<div_up(ncell, kBlock), kBlock, 0, st>>>(src, sc, P, P32);
-    GS_CHECK_LAUNCH();
+    GS_CHECK_LAUNCH_N(2);
 }
 
 void launch_l0_rap(const IsaacsConsts* K, int side, const uint8_t* code, const double* P,

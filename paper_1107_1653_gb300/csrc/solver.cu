@@ -2,6 +2,7 @@
 // multilevel scheme FAMGpi (Algorithm 4, Sec. 5.2): host orchestration of the
 // kernels on the solver's stream.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -31,6 +32,60 @@ void* Arena::raw(size_t bytes) {
     ptrs_.push_back(p);
     held_ += bytes;
     return p;
+}
+
+// ------------------------------------------------------------------ tracing
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(); }
+
+namespace {
+
+// Brackets the launches issued in its scope with events when `cls` is traced.
+class KScope {
+public:
+    KScope(gs_solver* s, int cls) : s_(s), on_(s->trace.cls == cls && cls != 0) {
+        if (on_) record();
+    }
+    ~KScope() {
+        if (on_) {
+            record();
+            ++s_->trace.launches;
+        }
+    }
+
+private:
+    void record() {
+        Tracer& t = s_->trace;
+        if (t.used == t.ev.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { on_ = false; return; }
+            t.ev.push_back(e);
+        }
+        cudaEventRecord(t.ev[t.used++], s_->st);
+    }
+    gs_solver* s_;
+    bool on_;
+};
+
+}  // namespace
+
+void trace_harvest(gs_solver* s) {
+    Tracer& t = s->trace;
+    if (!t.used) return;
+    GS_CUDA(cudaStreamSynchronize(s->st));
+    for (size_t k = 0; k + 1 < t.used; k += 2) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, t.ev[k], t.ev[k + 1]) == cudaSuccess) t.ms += ms;
+    }
+    t.used = 0;
+}
+
+void trace_reset(gs_solver* s, int cls) {
+    trace_harvest(s);
+    s->trace.cls = cls;
+    s->trace.ms = 0;
+    s->trace.launches = 0;
 }
 
 namespace {
@@ -229,6 +284,7 @@ namespace {
 void setup_hierarchy(gs_solver* s, IsaacsGrid& g, bool need32) {
     cudaStream_t st = s->st;
     const int L = (int)g.lv.size() - 1;
+    KScope ks(s, GS_K_SETUP);
     if (L == 0) {
         launch_l0_coarse_invert(g.Kd, g.side, g.code, g.inv, g.dstatus, st);
         return;
@@ -267,6 +323,7 @@ void smooth(gs_solver* s, IsaacsGrid& g, int l, bool from_zero) {
     const Level& L = g.lv[l];
     if (l == 0) {
         for (int c = 0; c < 2; ++c) {
+            KScope ks(s, GS_K_FINE_RELAX);
             if constexpr (sizeof(T) == 8)
                 launch_l0_smooth64(g.Kd, L.side, g.code, V.f, V.u, c, s->st);
             else
@@ -274,8 +331,10 @@ void smooth(gs_solver* s, IsaacsGrid& g, int l, bool from_zero) {
         }
     } else {
         const void* A = sizeof(T) == 8 ? (const void*)L.A64 : (const void*)L.A32;
-        for (int ph = 0; ph < 4; ++ph)
+        for (int ph = 0; ph < 4; ++ph) {
+            KScope ks(s, GS_K_COARSE);
             launch_smooth9<T>(A, L.side, V.f, V.u, ph, from_zero && ph == 0, s->st);
+        }
     }
 }
 
@@ -287,32 +346,46 @@ void vcycle(gs_solver* s, IsaacsGrid& g, int l, bool u_is_zero) {
     const int L = (int)g.lv.size() - 1;
     Vec<T> V = level_vec<T>(g, l);
     const Level& Lv = g.lv[l];
+    const int tcls = l == 0 ? GS_K_TRANSFER : GS_K_COARSE;
     if (l == L) {
+        KScope ks(s, GS_K_COARSE);
         launch_coarse_apply<T>(g.inv, (int)Lv.n, V.f, V.u, s->st);
         return;
     }
     for (int k = 0; k < s->opt.nu1; ++k) smooth<T>(s, g, l, u_is_zero && k == 0);
-    if constexpr (sizeof(T) == 8) {
-        if (l == 0) launch_l0_residual64(g.Kd, Lv.side, g.code, V.f, V.u, V.r, nullptr, s->st);
-        else launch_residual9<double>(Lv.A64, Lv.side, V.f, V.u, V.r, s->st);
-    } else {
-        if (l == 0) launch_l0_residual32(g.Kd, Lv.side, g.code, V.f, V.u, V.r, s->st);
-        else launch_residual9<float>(Lv.A32, Lv.side, V.f, V.u, V.r, s->st);
+    {
+        KScope ks(s, l == 0 ? GS_K_FINE_RESIDUAL : GS_K_COARSE);
+        if constexpr (sizeof(T) == 8) {
+            if (l == 0) launch_l0_residual64(g.Kd, Lv.side, g.code, V.f, V.u, V.r, nullptr, s->st);
+            else launch_residual9<double>(Lv.A64, Lv.side, V.f, V.u, V.r, s->st);
+        } else {
+            if (l == 0) launch_l0_residual32(g.Kd, Lv.side, g.code, V.f, V.u, V.r, s->st);
+            else launch_residual9<float>(Lv.A32, Lv.side, V.f, V.u, V.r, s->st);
+        }
     }
     Vec<T> C = level_vec<T>(g, l + 1);
-    launch_restrict<T>(V.r, Lv.P64, Lv.P32, Lv.side, C.f, s->st);
+    {
+        KScope ks(s, tcls);
+        launch_restrict<T>(V.r, Lv.P64, Lv.P32, Lv.side, C.f, s->st);
+    }
     GS_CUDA(cudaMemsetAsync(C.u, 0, sizeof(T) * g.lv[l + 1].n, s->st));
     vcycle<T>(s, g, l + 1, true);
-    launch_prolong<T>(C.u, Lv.P64, Lv.P32, Lv.side, V.u, s->st);
+    {
+        KScope ks(s, tcls);
+        launch_prolong<T>(C.u, Lv.P64, Lv.P32, Lv.side, V.u, s->st);
+    }
     for (int k = 0; k < s->opt.nu2; ++k) smooth<T>(s, g, l, false);
 }
 
 double fine_residual(gs_solver* s, IsaacsGrid& g, float* r32) {
     clear_scalars(s);
-    if (r32)
-        launch_l0_residual64_to32(g.Kd, g.side, g.code, g.rhs, g.v, r32, &s->dsc->res, s->st);
-    else
-        launch_l0_residual64(g.Kd, g.side, g.code, g.rhs, g.v, g.lv[0].r64, &s->dsc->res, s->st);
+    {
+        KScope ks(s, GS_K_REFINE);
+        if (r32)
+            launch_l0_residual64_to32(g.Kd, g.side, g.code, g.rhs, g.v, r32, &s->dsc->res, s->st);
+        else
+            launch_l0_residual64(g.Kd, g.side, g.code, g.rhs, g.v, g.lv[0].r64, &s->dsc->res, s->st);
+    }
     launch_absmax(g.v, g.n, &s->dsc->vmax, s->st);
     const DevScalars& h = read_scalars(s);
     return bits_to_double(h.res);
@@ -362,6 +435,7 @@ bool amgpi(gs_solver* s, IsaacsGrid& g, double eps, bool beta_given, Counters& c
     cudaStream_t st = s->st;
     if (!beta_given) {
         vmax_to_device(s, g);
+        KScope ks(s, GS_K_IMPROVE);
         launch_isaacs_improve(IMP_REPLY, g.Kd, g.side, g.variant, g.v, g.r0, g.alpha, g.beta,
                               g.code, g.rhs, nullptr, s->dsc, st);
     } else {
@@ -374,14 +448,18 @@ bool amgpi(gs_solver* s, IsaacsGrid& g, double eps, bool beta_given, Counters& c
             linear_solve(s, g, cnt);
             ++cnt.systems;
             vmax_to_device(s, g);
+            KScope ks(s, GS_K_IMPROVE);
             launch_isaacs_improve(IMP_INNER, g.Kd, g.side, g.variant, g.v, g.r0, g.alpha, g.beta,
                                   g.code, g.rhs, nullptr, s->dsc, st);
             if (read_scalars(s).changed == 0) break;
         }
         ++outer;
         vmax_to_device(s, g);
-        launch_isaacs_improve(IMP_OUTER, g.Kd, g.side, g.variant, g.v, g.r0, g.alpha, g.beta,
-                              g.code, g.rhs, g.fv, s->dsc, st);
+        {
+            KScope ks(s, GS_K_IMPROVE);
+            launch_isaacs_improve(IMP_OUTER, g.Kd, g.side, g.variant, g.v, g.r0, g.alpha, g.beta,
+                                  g.code, g.rhs, g.fv, s->dsc, st);
+        }
         const DevScalars& h = read_scalars(s);
         cnt.res_inf = bits_to_double(h.res);
         cnt.res_l2 = std::sqrt(h.res_sq / (double)g.n);
@@ -456,6 +534,7 @@ gs_status run_solve(gs_solver* s, gs_solve_stats* stats) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     s->last_levels = (int)fine.lv.size();
+    trace_harvest(s);
     reset_initial(s);
     if (stats) {
         stats->outer = cnt.outer;
@@ -522,6 +601,7 @@ gs_status run_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* be
     GS_CUDA(cudaMemsetAsync(bad, 0, 2 * sizeof(int), s->st));
     k_check_actions<<<div_up(g.n, 256), 256, 0, s->st>>>(a, g.n, m1, bad);
     k_check_actions<<<div_up(g.n * m1, 256), 256, 0, s->st>>>(bst, g.n * m1, 4, bad + 1);
+    GS_CHECK_LAUNCH_N(2);
     int hbad[2];
     GS_CUDA(cudaMemcpyAsync(hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, s->st));
     sync(s);

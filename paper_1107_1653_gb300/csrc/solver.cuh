@@ -72,8 +72,20 @@ struct Counters {
 
 }  // namespace gs
 
+namespace gs {
+// CUDA-event brackets around the launches of one kernel class.
+struct Tracer {
+    int cls = 0;
+    std::vector<cudaEvent_t> ev;   // pairs: start, stop
+    size_t used = 0;               // events recorded since the last harvest
+    double ms = 0.0;
+    long long launches = 0;
+};
+}  // namespace gs
+
 struct gs_solver {
     gs_options opt;
+    gs::Tracer trace;
     cudaStream_t st = nullptr;
     gs::DevScalars* dsc = nullptr;     // device scalars
     gs::DevScalars* hsc = nullptr;     // pinned host mirror
@@ -93,6 +105,9 @@ gs_status run_improve(gs_solver* s, const double* v, uint8_t* alpha_out, uint8_t
                       double* fv_out);
 gs_status run_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* beta,
                            const double* w0, double* w_out, gs_solve_stats* stats);
+void trace_harvest(gs_solver* s);
+unsigned long long launch_count();
+void trace_reset(gs_solver* s, int cls);
 void pack_beta_upload(gs_solver* s, IsaacsGrid& g, const uint8_t* beta_host);
 void unpack_beta_download(gs_solver* s, const IsaacsGrid& g, uint8_t* beta_out);
 
