@@ -69,9 +69,17 @@ typedef struct {
     int32_t fmg_side;      /* FAMGpi coarsest grid side (2^k - 1), e.g. 31 */
     double  fmg_c;         /* FAMGpi per-level tolerance eps_l = fmg_c * h_l^2 */
     int32_t mu_mode;       /* Isaacs discount: 0 mu = 1/(1+h^2), 1 mu = c0/(c0+h^2) */
-    int32_t reserved0;
+    int32_t tail_side;     /* levels of side <= tail_side are relaxed by one thread block,
+                              without grid-wide barriers (0 = default, 31) */
     uint64_t mem_budget;   /* bytes of device memory the solver may hold; 0 = no limit */
     void*   stream;        /* cudaStream_t for all work; NULL = the legacy default stream */
+    double  pi_rtol;       /* policy evaluations inside the inner loop stop once the residual
+                              drops by this factor; before any stopping decision the system is
+                              re-solved to the float64 floor and the policies re-checked
+                              (0 = every system to the floor) */
+    double  setup_reuse;   /* keep the previous Galerkin hierarchy when at most this fraction
+                              of the rows of the policy-fixed system changed (0 = always
+                              rebuild); the float64 residual test keeps the solution exact */
 } gs_options;
 
 /* Statistics of the last gamesolve_solve (the columns of the paper's tables, Sec. 6). */
@@ -88,8 +96,9 @@ typedef struct {
 } gs_solve_stats;
 
 /* Fills *opt with the defaults: FP64, eps 0, max_outer 1000, max_inner 1000,
- * V(1,1), max_cycles 200, lin_tol 1e-15, coarse_max 64, flat, fmg_side 31,
- * fmg_c 0.1, literal mu, no memory budget, default stream. */
+ * V(1,1), max_cycles 200, lin_tol 1e-15, coarse_max 9, flat, fmg_side 31,
+ * fmg_c 0.1, literal mu, tail_side 31, no memory budget, default stream,
+ * pi_rtol 1e-3, setup_reuse 1e-3. */
 void gamesolve_default_options(gs_options* opt);
 
 /* Creates a solver on the current CUDA device.  opt may be NULL (defaults).
@@ -166,13 +175,9 @@ gs_status gamesolve_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8
 /* Kernel classes that gamesolve_trace can time (diagnostics). */
 typedef enum {
     GS_K_NONE = 0,
-    GS_K_IMPROVE = 1,        /* policy improvement fused with assembly, fine level */
-    GS_K_FINE_RELAX = 2,     /* one colour of the fine-level C/F relaxation */
-    GS_K_FINE_RESIDUAL = 3,  /* fine-level residual inside a V-cycle */
-    GS_K_SETUP = 4,          /* interpolation weights, Galerkin products, coarsest inverse */
-    GS_K_COARSE = 5,         /* everything a V-cycle does on levels >= 1 */
-    GS_K_TRANSFER = 6,       /* fine-level restriction and prolongation */
-    GS_K_REFINE = 7          /* float64 residual b - A v of the fine system (refinement / stopping test) */
+    GS_K_IMPROVE = 1,        /* policy improvement fused with the assembly (one launch) */
+    GS_K_MG_SOLVE = 2        /* multigrid solve of one policy-fixed system (one launch:
+                                Galerkin set-up, V-cycles and the float64 stopping test) */
 } gs_kernel_class;
 
 /* Selects one kernel class whose launches the following solves bracket with

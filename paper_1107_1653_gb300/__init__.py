@@ -22,8 +22,7 @@ lib = ctypes.CDLL(LIB_PATH)
 
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_ENOTCONV, GS_ETIMEOUT, GS_ECUDA, GS_ESTATE = range(7)
 GS_PREC_FP64, GS_PREC_MIXED, GS_PREC_MIXED_BF16 = range(3)
-KERNEL_CLASSES = {"none": 0, "improve": 1, "fine_relax": 2, "fine_residual": 3, "setup": 4,
-                  "coarse": 5, "transfer": 6, "refine": 7}
+KERNEL_CLASSES = {"none": 0, "improve": 1, "mg_solve": 2}
 PRECISIONS = {"fp64": GS_PREC_FP64, "mixed": GS_PREC_MIXED, "mixed_bf16": GS_PREC_MIXED_BF16}
 
 
@@ -35,8 +34,9 @@ class gs_options(ctypes.Structure):
         ("max_cycles", ctypes.c_int32), ("lin_tol", ctypes.c_double),
         ("coarse_max", ctypes.c_int32), ("fmg", ctypes.c_int32),
         ("fmg_side", ctypes.c_int32), ("fmg_c", ctypes.c_double),
-        ("mu_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("mu_mode", ctypes.c_int32), ("tail_side", ctypes.c_int32),
         ("mem_budget", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+        ("pi_rtol", ctypes.c_double), ("setup_reuse", ctypes.c_double),
     ]
 
 

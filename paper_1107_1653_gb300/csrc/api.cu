@@ -50,13 +50,16 @@ void gamesolve_default_options(gs_options* o) {
     o->nu2 = 1;
     o->max_cycles = 200;
     o->lin_tol = 1e-15;
-    o->coarse_max = 64;
+    o->coarse_max = 9;
+    o->tail_side = 31;
     o->fmg = 0;
     o->fmg_side = 31;
     o->fmg_c = 0.1;
     o->mu_mode = 0;
     o->mem_budget = 0;
     o->stream = nullptr;
+    o->pi_rtol = 1e-3;
+    o->setup_reuse = 1e-3;
 }
 
 gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
@@ -70,8 +73,9 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
     else gamesolve_default_options(&o);
     if (o.precision < 0 || o.precision > 2 || o.max_outer < 1 || o.max_inner < 1 || o.nu1 < 0 ||
         o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 1 || !(o.lin_tol >= 0) ||
-        o.coarse_max < 1 || o.coarse_max > 64 || !(o.eps >= 0) || !(o.fmg_c > 0) ||
-        (o.fmg && !is_pow2m1(o.fmg_side)) || o.mu_mode < 0 || o.mu_mode > 1) {
+        o.coarse_max < 1 || o.coarse_max > 64 || o.tail_side < 0 || !(o.eps >= 0) || !(o.fmg_c > 0) ||
+        (o.fmg && !is_pow2m1(o.fmg_side)) || o.mu_mode < 0 || o.mu_mode > 1 ||
+        !(o.pi_rtol >= 0.0 && o.pi_rtol < 1.0) || !(o.setup_reuse >= 0.0 && o.setup_reuse <= 1.0)) {
         set_last_error("create: invalid option value");
         return GS_EINVAL;
     }
@@ -83,10 +87,15 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
         s->st = (cudaStream_t)o.stream;
         cudaError_t e1 = cudaMalloc(&s->dsc, sizeof(DevScalars));
         cudaError_t e2 = cudaMallocHost(&s->hsc, sizeof(DevScalars));
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
-            set_last_error("create: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+        cudaError_t e3 = cudaMalloc(&s->mgd, sizeof(MGState));
+        cudaError_t e4 = cudaMallocHost(&s->mgh, sizeof(MGState));
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
+            cudaError_t e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4;
+            set_last_error("create: %s", cudaGetErrorString(e));
             if (s->dsc) cudaFree(s->dsc);
             if (s->hsc) cudaFreeHost(s->hsc);
+            if (s->mgd) cudaFree(s->mgd);
+            if (s->mgh) cudaFreeHost(s->mgh);
             delete s;
             cudaGetLastError();
             return GS_ECUDA;
@@ -215,7 +224,7 @@ gs_status gamesolve_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8
 }
 
 gs_status gamesolve_trace(gs_solver* s, int32_t kernel_class) {
-    if (!s || kernel_class < GS_K_NONE || kernel_class > GS_K_REFINE) return GS_EINVAL;
+    if (!s || kernel_class < GS_K_NONE || kernel_class > GS_K_MG_SOLVE) return GS_EINVAL;
     return guarded([&]() -> gs_status {
         trace_reset(s, kernel_class);
         return GS_OK;
@@ -242,6 +251,8 @@ void gamesolve_destroy(gs_solver* s) {
     s->prob.reset();
     if (s->dsc) cudaFree(s->dsc);
     if (s->hsc) cudaFreeHost(s->hsc);
+    if (s->mgd) cudaFree(s->mgd);
+    if (s->mgh) cudaFreeHost(s->mgh);
     delete s;
 }
 

@@ -75,6 +75,7 @@ struct IsaacsConsts {
     double dr[4][4];
     // float copies of the off-diagonal entries of am (index 1..4 used).
     float amf[kCodes][5];
+    float kappa_f;        // kappa rounded to float
 };
 
 // Device-side scalars: reductions written by kernels, read by the host once
@@ -84,7 +85,7 @@ struct DevScalars {
     unsigned long long res;      // |F(v) - v|_inf or |b - A v|_inf (bits)
     double res_sq;               // sum of squares (statistics only)
     int changed;                 // policy entries changed by an improvement
-    int pad;
+    int code_changed;            // rows of the policy-fixed system that changed
 };
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* dst, double v) {

@@ -1,8 +1,7 @@
 // Fine-level kernels of the finite-difference Isaacs game (Sec. 3.3, Sec. 6.1):
 // reward set-up, policy improvement (Eq. (eq1)/(ILPI)) fused with the
-// policy-fixed assembly (Eq. (LSPI)), the implicit 5-point operator's
-// relaxation/residual, its interpolation and Galerkin product, and the FAMGpi
-// interpolations (Sec. 5.2).
+// policy-fixed assembly (Eq. (LSPI)), and the
+// FAMGpi interpolations (Sec. 5.2).
 #include "kernels.cuh"
 #include "stencil.cuh"
 
@@ -96,7 +95,7 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
     const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = x < n;
     double res = 0.0;
-    int changed = 0;
+    int changed = 0, code_changed = 0;
     if (active) {
         const int i = (int)(x % side), j = (int)(x / side);
         const double tau = 1e-13 * fmax(1.0, __longlong_as_double((long long)sc->vmax));
@@ -145,24 +144,30 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
         }
         beta[x] = bnew;
         // policy-fixed assembly for (alpha, beta(., alpha))
+        const int old_code = code[x];
+        int new_code;
         if (anew == 4) {
-            code[x] = kStopCode;
+            new_code = kStopCode;
             rhs[x] = obstacle_psi(i, j, K->h);
         } else {
             const int b = (bnew >> (8 * anew)) & 0xff;
-            code[x] = (uint8_t)(4 * anew + b);
+            new_code = 4 * anew + b;
             rhs[x] = rx + K->dr[anew][b];
         }
+        code[x] = (uint8_t)new_code;
+        code_changed = new_code != old_code;
     }
     const double wres = warp_max(res);
     const double wsq = warp_sum(res * res);
     const int wch = warp_isum(changed);
+    const int wcc = warp_isum(code_changed);
     if ((threadIdx.x & 31) == 0) {
         if (MODE == IMP_OUTER) {
             atomic_max_nonneg(&sc->res, wres);
             atomicAdd(&sc->res_sq, wsq);
         }
         if (wch) atomicAdd(&sc->changed, wch);
+        if (wcc) atomicAdd(&sc->code_changed, wcc);
     }
 }
 
@@ -193,126 +198,6 @@ __global__ void k_absmax(const double* __restrict__ v, size_t n, unsigned long l
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
 }
 
-// Fine-level neighbour access with Dirichlet zero outside the grid.
-template <typename T>
-struct Fine5 {
-    T c, w, e, s, nn;
-};
-template <typename T>
-__device__ __forceinline__ Fine5<T> load5(const T* __restrict__ u, size_t x, int i, int j, int side) {
-    Fine5<T> q;
-    q.c = u[x];
-    q.w = i > 0 ? u[x - 1] : T(0);
-    q.e = i + 1 < side ? u[x + 1] : T(0);
-    q.s = j > 0 ? u[x - side] : T(0);
-    q.nn = j + 1 < side ? u[x + side] : T(0);
-    return q;
-}
-
-// float64 residual r = f - A u of the implicit 5-point operator; |r|_inf.
-template <bool TO32>
-__global__ void k_l0_residual64(const IsaacsConsts* __restrict__ K, int side,
-                                const uint8_t* __restrict__ code, const double* __restrict__ f,
-                                const double* __restrict__ u, void* __restrict__ r,
-                                unsigned long long* rmax) {
-    const size_t n = (size_t)side * side;
-    const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double rx = 0.0;
-    if (x < n) {
-        const int i = (int)(x % side), j = (int)(x / side);
-        const double* am = K->am[code[x]];
-        const Fine5<double> q = load5(u, x, i, j, side);
-        const double Au = am[0] * q.c + am[1] * q.w + am[2] * q.e + am[3] * q.s + am[4] * q.nn;
-        rx = f[x] - Au;
-        if (TO32) ((float*)r)[x] = (float)rx;
-        else ((double*)r)[x] = rx;
-    }
-    if (rmax) {
-        const double m = warp_max(fabs(rx));
-        if ((threadIdx.x & 31) == 0) atomic_max_nonneg(rmax, m);
-    }
-}
-
-// Red-black ordering of the 5-point operator: colour 0 = points with i + j
-// even = the C points (odd, odd) and the cell corners (even, even), which are
-// uncoupled; colour 1 = the edge F points.  Relaxing colour 0 then colour 1
-// is the C/F relaxation (C points first, then F points).
-__device__ __forceinline__ bool colour_point(int side, int color, size_t t, int* i, int* j) {
-    const int hs = (side + 1) / 2;
-    *j = (int)(t / hs);
-    *i = ((*j + color) & 1) + 2 * (int)(t % hs);
-    return *j < side && *i < side;
-}
-
-__global__ void k_l0_smooth64(const IsaacsConsts* __restrict__ K, int side,
-                              const uint8_t* __restrict__ code, const double* __restrict__ f,
-                              double* __restrict__ u, int color) {
-    int i, j;
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (!colour_point(side, color, t, &i, &j)) return;
-    const size_t x = (size_t)j * side + i;
-    const double* am = K->am[code[x]];
-    double s = f[x];
-    if (i > 0) s -= am[1] * u[x - 1];
-    if (i + 1 < side) s -= am[2] * u[x + 1];
-    if (j > 0) s -= am[3] * u[x - side];
-    if (j + 1 < side) s -= am[4] * u[x + side];
-    u[x] = s / am[0];
-}
-
-// Row sum of the fine row (the leakage 1 - mu sum_y p), float64.
-__device__ __forceinline__ double l0_rowsum(const IsaacsConsts* K, int c, int i, int j, int side) {
-    if (c == kStopCode) return 1.0;
-    const double* am = K->am[c];
-    double s = K->kappa;
-    if (i == 0) s -= am[1];
-    if (i + 1 == side) s -= am[2];
-    if (j == 0) s -= am[3];
-    if (j + 1 == side) s -= am[4];
-    return s;
-}
-
-__global__ void k_l0_smooth32(const IsaacsConsts* __restrict__ K, int side,
-                              const uint8_t* __restrict__ code, const float* __restrict__ f,
-                              float* __restrict__ u, int color, bool zero_init) {
-    int i, j;
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (!colour_point(side, color, t, &i, &j)) return;
-    const size_t x = (size_t)j * side + i;
-    const int c = code[x];
-    const float* am = K->amf[c];
-    const float s_row = (float)l0_rowsum(K, c, i, j, side);
-    float diag = s_row, acc = f[x];
-    if (i > 0) { diag -= am[1]; if (!zero_init) acc -= am[1] * u[x - 1]; }
-    if (i + 1 < side) { diag -= am[2]; if (!zero_init) acc -= am[2] * u[x + 1]; }
-    if (j > 0) { diag -= am[3]; if (!zero_init) acc -= am[3] * u[x - side]; }
-    if (j + 1 < side) { diag -= am[4]; if (!zero_init) acc -= am[4] * u[x + side]; }
-    u[x] = acc / diag;
-}
-
-__global__ void k_l0_residual32(const IsaacsConsts* __restrict__ K, int side,
-                                const uint8_t* __restrict__ code, const float* __restrict__ f,
-                                const float* __restrict__ u, float* __restrict__ r) {
-    const size_t n = (size_t)side * side;
-    const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= n) return;
-    const int i = (int)(x % side), j = (int)(x / side);
-    const int c = code[x];
-    const float* am = K->amf[c];
-    const Fine5<float> q = load5(u, x, i, j, side);
-    // leakage form: (A u)_x = s_x u_x + sum_d a_d (u_d - u_x) over interior d
-    float Au = (float)l0_rowsum(K, c, i, j, side) * q.c;
-    if (i > 0) Au += am[1] * (q.w - q.c);
-    if (i + 1 < side) Au += am[2] * (q.e - q.c);
-    if (j > 0) Au += am[3] * (q.s - q.c);
-    if (j + 1 < side) Au += am[4] * (q.nn - q.c);
-    r[x] = f[x] - Au;
-}
-
-__global__ void k_axpy32(double* __restrict__ v, const float* __restrict__ e, size_t n) {
-    const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < n) v[x] += (double)e[x];
-}
 
 // FAMGpi interpolation from side sc to sf = 2 sc + 1 (1-based fine (p, q),
 // coarse (P, Q) at fine (2P, 2Q); P or Q in {0, sc+1} is the boundary).
@@ -401,78 +286,14 @@ void launch_absmax(const double* v, size_t n, unsigned long long* out, cudaStrea
     GS_CHECK_LAUNCH();
 }
 
-void launch_l0_residual64(const IsaacsConsts* K, int side, const uint8_t* code, const double* f,
-                          const double* u, double* r, unsigned long long* rmax, cudaStream_t st) {
-    const size_t n = (size_t)side * side;
-    k_l0_residual64<false><<<div_up(n, kBlock), kBlock, 0, st>>>(K, side, code, f, u, r, rmax);
-    GS_CHECK_LAUNCH();
-}
 
-void launch_l0_residual64_to32(const IsaacsConsts* K, int side, const uint8_t* code,
-                               const double* f, const double* u, float* r32,
-                               unsigned long long* rmax, cudaStream_t st) {
-    const size_t n = (size_t)side * side;
-    k_l0_residual64<true><<<div_up(n, kBlock), kBlock, 0, st>>>(K, side, code, f, u, r32, rmax);
-    GS_CHECK_LAUNCH();
-}
 
-void launch_l0_smooth64(const IsaacsConsts* K, int side, const uint8_t* code, const double* f,
-                        double* u, int color, cudaStream_t st) {
-    const size_t cnt = (size_t)side * ((side + 1) / 2);
-    k_l0_smooth64<<<div_up(cnt, kBlock), kBlock, 0, st>>>(K, side, code, f, u, color);
-    GS_CHECK_LAUNCH();
-}
 
-void launch_l0_smooth32(const IsaacsConsts* K, int side, const uint8_t* code, const float* f,
-                        float* u, int color, bool zero_init, cudaStream_t st) {
-    const size_t cnt = (size_t)side * ((side + 1) / 2);
-    k_l0_smooth32<<<div_up(cnt, kBlock), kBlock, 0, st>>>(K, side, code, f, u, color, zero_init);
-    GS_CHECK_LAUNCH();
-}
 
-void launch_l0_residual32(const IsaacsConsts* K, int side, const uint8_t* code, const float* f,
-                          const float* u, float* r, cudaStream_t st) {
-    const size_t n = (size_t)side * side;
-    k_l0_residual32<<<div_up(n, kBlock), kBlock, 0, st>>>(K, side, code, f, u, r);
-    GS_CHECK_LAUNCH();
-}
 
-void launch_l0_interp(const IsaacsConsts* K, int side, const uint8_t* code, double* P, float* P32,
-                      cudaStream_t st) {
-    const int sc = (side - 1) / 2;
-    const size_t ncell = (size_t)(sc + 1) * (sc + 1);
-    Src5 src{K, code, side};
-    k_interp_edges<<<div_up(ncell, kBlock), kBlock, 0, st>>>(src, sc, P, P32);
-    k_interp_corners<<<div_up(ncell, kBlock), kBlock, 0, st>>>(src, sc, P, P32);
-    GS_CHECK_LAUNCH_N(2);
-}
 
-void launch_l0_rap(const IsaacsConsts* K, int side, const uint8_t* code, const double* P,
-                   double* Ac, cudaStream_t st) {
-    const int sc = (side - 1) / 2;
-    Src5 src{K, code, side};
-    k_rap<<<div_up((size_t)sc * sc, kBlock), kBlock, 0, st>>>(src, sc, P, Ac);
-    GS_CHECK_LAUNCH();
-}
 
-void launch_l0_coarse_invert(const IsaacsConsts* K, int side, const uint8_t* code, double* inv,
-                             int* status, cudaStream_t st) {
-    const int n = side * side;
-    static bool attr = false;
-    if (!attr) {
-        GS_CUDA(cudaFuncSetAttribute(k_coarse_invert<Src5>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 128 * 8));
-        attr = true;
-    }
-    Src5 src{K, code, side};
-    k_coarse_invert<<<1, 256, (size_t)n * 2 * n * sizeof(double), st>>>(src, side, inv, status);
-    GS_CHECK_LAUNCH();
-}
 
-void launch_axpy32(double* v, const float* e, size_t n, cudaStream_t st) {
-    k_axpy32<<<div_up(n, kBlock), kBlock, 0, st>>>(v, e, n);
-    GS_CHECK_LAUNCH();
-}
 
 void launch_fmg_interp(int sc, const double* v_c, const uint8_t* alpha_c, const uint32_t* beta_c,
                        const uint8_t* beta4_c, double* v_f, uint8_t* alpha_f, uint32_t* beta_f,

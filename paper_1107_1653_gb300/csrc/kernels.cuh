@@ -38,54 +38,9 @@ void launch_isaacs_assemble(const IsaacsConsts* K, int side, const uint8_t* alph
 // |v|_inf into sc->vmax (sc->vmax must be cleared first).
 void launch_absmax(const double* v, size_t n, unsigned long long* out, cudaStream_t st);
 
-// Fine-level (implicit 5-point stencil) operators.
-void launch_l0_residual64(const IsaacsConsts* K, int side, const uint8_t* code,
-                          const double* f, const double* u, double* r,
-                          unsigned long long* rmax, cudaStream_t st);
-// Refinement residual: float64 r = f - A u, written rounded to float.
-void launch_l0_residual64_to32(const IsaacsConsts* K, int side, const uint8_t* code,
-                               const double* f, const double* u, float* r32,
-                               unsigned long long* rmax, cudaStream_t st);
-void launch_l0_smooth64(const IsaacsConsts* K, int side, const uint8_t* code,
-                        const double* f, double* u, int color, cudaStream_t st);
-void launch_l0_smooth32(const IsaacsConsts* K, int side, const uint8_t* code,
-                        const float* f, float* u, int color, bool zero_init, cudaStream_t st);
-void launch_l0_residual32(const IsaacsConsts* K, int side, const uint8_t* code,
-                          const float* f, const float* u, float* r, cudaStream_t st);
-void launch_l0_interp(const IsaacsConsts* K, int side, const uint8_t* code, double* P,
-                      float* P32, cudaStream_t st);
-void launch_l0_rap(const IsaacsConsts* K, int side, const uint8_t* code, const double* P,
-                   double* Ac, cudaStream_t st);
-void launch_l0_coarse_invert(const IsaacsConsts* K, int side, const uint8_t* code,
-                             double* inv, int* status, cudaStream_t st);
-
-// v += e
-void launch_axpy32(double* v, const float* e, size_t n, cudaStream_t st);
-
 // FAMGpi interpolations (Sec. 5.2) from a coarse grid of side sc to 2 sc + 1.
 void launch_fmg_interp(int sc, const double* v_c, const uint8_t* alpha_c,
                        const uint32_t* beta_c, const uint8_t* beta4_c, double* v_f,
                        uint8_t* alpha_f, uint32_t* beta_f, uint8_t* beta4_f, cudaStream_t st);
-
-// ------------------------------------------------------------ 9-point levels
-void launch_interp9(const double* A, int side, double* P, float* P32, cudaStream_t st);
-void launch_rap9(const double* A, int side, const double* P, double* Ac, cudaStream_t st);
-void launch_coarse_invert9(const double* A, int side, double* inv, int* status,
-                           cudaStream_t st);
-void launch_stencil_to32(const double* A, size_t n, float* A32, cudaStream_t st);
-
-template <typename T>
-void launch_smooth9(const void* A, int side, const T* f, T* u, int phase, bool zero_init,
-                    cudaStream_t st);
-template <typename T>
-void launch_residual9(const void* A, int side, const T* f, const T* u, T* r, cudaStream_t st);
-template <typename T>
-void launch_restrict(const T* r, const double* P64, const float* P32, int side_f, T* fc,
-                     cudaStream_t st);
-template <typename T>
-void launch_prolong(const T* uc, const double* P64, const float* P32, int side_f, T* uf,
-                    cudaStream_t st);
-template <typename T>
-void launch_coarse_apply(const double* inv, int n, const T* f, T* u, cudaStream_t st);
 
 }  // namespace gs

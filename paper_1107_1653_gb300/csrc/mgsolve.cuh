@@ -1,0 +1,73 @@
+// Persistent multigrid solve of one policy-fixed system (Eq. (LSPI)): the
+// arguments the host passes to the single cooperative kernel that runs the
+// Galerkin set-up, the V-cycles (Algorithm 3) and the float64 stopping test.
+#pragma once
+
+#include "common.cuh"
+
+namespace gs {
+
+constexpr int kMaxLevels = 14;
+constexpr int kMGThreads = 256;
+// Largest shared-memory footprint of the tail levels staged by block 0.
+constexpr int kTailSmemMax = 100 * 1024;
+
+// Plain data (no initialisers): copies live in shared memory.
+struct LevelArgs {
+    int side;            // grid side of the level
+    int sc;              // side of the next coarser level, (side - 1) / 2
+    size_t n;
+    void* u;             // V-cycle unknown (float32 in the mixed path, else float64)
+    void* f;             // V-cycle right-hand side
+    const void* A;       // V-cycle operator, levels >= 1 (float32 leakage or float64)
+    const void* P;       // V-cycle interpolation weights from level + 1
+    double* A64;         // Galerkin operator, levels >= 1 (written by the set-up)
+    float* A32;          // its float32 leakage copy (mixed path)
+    double* P64;         // interpolation weights (written by the set-up)
+    float* P32;
+};
+
+// Bounded grid barrier state; `error` is set when a wait gives up.
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+    int error;
+    int pad;
+};
+
+struct SolveOut {
+    unsigned long long rmax[2];   // |b - A v|_inf per residual evaluation (bits), ping-pong
+    unsigned long long vmax[2];   // |v|_inf (bits)
+    int cycles;
+    int reason;                   // 1 tolerance or float64 floor, 2 relative drop, 3 cycle cap
+    double res;                   // final |b - A v|_inf
+};
+
+struct SolveArgs {
+    const IsaacsConsts* K;
+    const uint8_t* code;
+    double* v;
+    const double* rhs;
+    int nlev;        // levels; nlev - 1 is the coarsest (explicit inverse)
+    int tail;        // levels >= tail are relaxed by thread block 0 alone
+    int smem_from;   // levels >= smem_from (>= max(tail, 1)) live in block 0's shared memory
+    int nu1, nu2, max_cycles;
+    int mixed;       // float32 V-cycles on the float64 residual (iterative refinement)
+    int do_setup;    // build interpolation, Galerkin operators and coarse inverse first
+    double lin_tol;
+    double rel_tol;  // also stop once the residual fell by this factor (0: floor only)
+    double* inv;     // inverse of the coarsest operator (n_L x n_L)
+    int* inv_status;
+    GridBarrier* bar;
+    SolveOut* out;
+    LevelArgs L[kMaxLevels];
+};
+
+// Launches the cooperative set-up (if a.do_setup) and solve on `st`
+// (asynchronous).  bar and out must be zeroed on the stream before the launch.
+void launch_mg_solve(const SolveArgs& a, cudaStream_t st);
+
+// Shared memory the tail levels >= a.smem_from need (elem = 4 or 8 bytes).
+size_t tail_smem_bytes(const SolveArgs& a, int elem);
+
+}  // namespace gs

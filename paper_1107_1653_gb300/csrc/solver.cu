@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "mgsolve.cuh"
 #include "solver.cuh"
 
 namespace gs {
@@ -170,6 +171,7 @@ IsaacsConsts make_isaacs_consts(int side, int variant, int mu_mode) {
     K.am[kStopCode][0] = 1.0;
     for (int c = 0; c < kCodes; ++c)
         for (int d = 0; d < 5; ++d) K.amf[c][d] = (float)K.am[c][d];
+    K.kappa_f = (float)K.kappa;
     return K;
 }
 
@@ -278,150 +280,93 @@ void unpack_beta_download(gs_solver* s, const IsaacsGrid& g, uint8_t* beta_out) 
 // ------------------------------------------------------------------ multigrid
 namespace {
 
-// Galerkin hierarchy for the current policy codes of grid g: interpolation
-// weights and A^{l+1} = P^T A^l P on every level, float32 copies for the mixed
-// path, and the explicit inverse of the coarsest operator (float64).
-void setup_hierarchy(gs_solver* s, IsaacsGrid& g, bool need32) {
-    cudaStream_t st = s->st;
-    const int L = (int)g.lv.size() - 1;
-    KScope ks(s, GS_K_SETUP);
-    if (L == 0) {
-        launch_l0_coarse_invert(g.Kd, g.side, g.code, g.inv, g.dstatus, st);
-        return;
-    }
-    launch_l0_interp(g.Kd, g.side, g.code, g.lv[0].P64, g.lv[0].P32, st);
-    launch_l0_rap(g.Kd, g.side, g.code, g.lv[0].P64, g.lv[1].A64, st);
-    for (int l = 1; l < L; ++l) {
-        launch_interp9(g.lv[l].A64, g.lv[l].side, g.lv[l].P64, g.lv[l].P32, st);
-        launch_rap9(g.lv[l].A64, g.lv[l].side, g.lv[l].P64, g.lv[l + 1].A64, st);
-    }
-    if (need32)
-        for (int l = 1; l <= L; ++l) launch_stencil_to32(g.lv[l].A64, g.lv[l].n, g.lv[l].A32, st);
-    launch_coarse_invert9(g.lv[L].A64, g.lv[L].side, g.inv, g.dstatus, st);
-}
-
-template <typename T>
-struct Vec {
-    T *u, *f, *r;
-};
-
-template <typename T>
-Vec<T> level_vec(IsaacsGrid& g, int l);
-template <>
-Vec<double> level_vec<double>(IsaacsGrid& g, int l) {
-    if (l == 0) return {g.v, g.rhs, g.lv[0].r64};
-    return {g.lv[l].u64, g.lv[l].f64, g.lv[l].r64};
-}
-template <>
-Vec<float> level_vec<float>(IsaacsGrid& g, int l) {
-    return {g.lv[l].u32, g.lv[l].f32, g.lv[l].r32};
-}
-
-template <typename T>
-void smooth(gs_solver* s, IsaacsGrid& g, int l, bool from_zero) {
-    Vec<T> V = level_vec<T>(g, l);
-    const Level& L = g.lv[l];
-    if (l == 0) {
-        for (int c = 0; c < 2; ++c) {
-            KScope ks(s, GS_K_FINE_RELAX);
-            if constexpr (sizeof(T) == 8)
-                launch_l0_smooth64(g.Kd, L.side, g.code, V.f, V.u, c, s->st);
-            else
-                launch_l0_smooth32(g.Kd, L.side, g.code, V.f, V.u, c, from_zero && c == 0, s->st);
-        }
-    } else {
-        const void* A = sizeof(T) == 8 ? (const void*)L.A64 : (const void*)L.A32;
-        for (int ph = 0; ph < 4; ++ph) {
-            KScope ks(s, GS_K_COARSE);
-            launch_smooth9<T>(A, L.side, V.f, V.u, ph, from_zero && ph == 0, s->st);
-        }
-    }
-}
-
-// Algorithm 3 with gamma = 1 (V-cycle): nu1 pre-relaxations, residual
-// restriction, recursive coarse correction from zero, prolongation and
-// correction, nu2 post-relaxations; exact solve on the coarsest level.
-template <typename T>
-void vcycle(gs_solver* s, IsaacsGrid& g, int l, bool u_is_zero) {
-    const int L = (int)g.lv.size() - 1;
-    Vec<T> V = level_vec<T>(g, l);
-    const Level& Lv = g.lv[l];
-    const int tcls = l == 0 ? GS_K_TRANSFER : GS_K_COARSE;
-    if (l == L) {
-        KScope ks(s, GS_K_COARSE);
-        launch_coarse_apply<T>(g.inv, (int)Lv.n, V.f, V.u, s->st);
-        return;
-    }
-    for (int k = 0; k < s->opt.nu1; ++k) smooth<T>(s, g, l, u_is_zero && k == 0);
-    {
-        KScope ks(s, l == 0 ? GS_K_FINE_RESIDUAL : GS_K_COARSE);
-        if constexpr (sizeof(T) == 8) {
-            if (l == 0) launch_l0_residual64(g.Kd, Lv.side, g.code, V.f, V.u, V.r, nullptr, s->st);
-            else launch_residual9<double>(Lv.A64, Lv.side, V.f, V.u, V.r, s->st);
-        } else {
-            if (l == 0) launch_l0_residual32(g.Kd, Lv.side, g.code, V.f, V.u, V.r, s->st);
-            else launch_residual9<float>(Lv.A32, Lv.side, V.f, V.u, V.r, s->st);
-        }
-    }
-    Vec<T> C = level_vec<T>(g, l + 1);
-    {
-        KScope ks(s, tcls);
-        launch_restrict<T>(V.r, Lv.P64, Lv.P32, Lv.side, C.f, s->st);
-    }
-    GS_CUDA(cudaMemsetAsync(C.u, 0, sizeof(T) * g.lv[l + 1].n, s->st));
-    vcycle<T>(s, g, l + 1, true);
-    {
-        KScope ks(s, tcls);
-        launch_prolong<T>(C.u, Lv.P64, Lv.P32, Lv.side, V.u, s->st);
-    }
-    for (int k = 0; k < s->opt.nu2; ++k) smooth<T>(s, g, l, false);
-}
-
-double fine_residual(gs_solver* s, IsaacsGrid& g, float* r32) {
-    clear_scalars(s);
-    {
-        KScope ks(s, GS_K_REFINE);
-        if (r32)
-            launch_l0_residual64_to32(g.Kd, g.side, g.code, g.rhs, g.v, r32, &s->dsc->res, s->st);
-        else
-            launch_l0_residual64(g.Kd, g.side, g.code, g.rhs, g.v, g.lv[0].r64, &s->dsc->res, s->st);
-    }
-    launch_absmax(g.v, g.n, &s->dsc->vmax, s->st);
-    const DevScalars& h = read_scalars(s);
-    return bits_to_double(h.res);
+// First level whose side is at most the single-block threshold (capped at the
+// coarsest): from there on one thread block relaxes, without grid barriers.
+int tail_level(const gs_solver* s, const IsaacsGrid& g) {
+    const int thr = s->opt.tail_side > 0 ? s->opt.tail_side : 31;
+    const int Lc = (int)g.lv.size() - 1;
+    for (int l = 0; l < Lc; ++l)
+        if (g.lv[l].side <= thr) return l;
+    return Lc;
 }
 
 // Solves (I - mu M) v = r for the assembled codes/rhs of g, warm-started from
-// g.v: float64 V-cycles, or (mixed) float32 V-cycles on the float64 residual
-// with float64 correction (iterative refinement).  Returns the cycles used.
-int linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt) {
+// g.v, in one cooperative launch: Galerkin set-up for the current policies,
+// then float64 V-cycles, or float32 V-cycles on the float64 residual with
+// float64 correction (iterative refinement), until the float64 stopping test.
+// rel_tol > 0 also stops once the residual fell by that factor (an inexact
+// policy evaluation); do_setup = false reuses the hierarchy of the previous
+// call (valid when the policy codes are unchanged).  Returns true when the
+// solve stopped at the float64 floor / tolerance rather than at rel_tol.
+bool linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bool do_setup) {
     const bool mixed = s->opt.precision != GS_PREC_FP64;
-    setup_hierarchy(s, g, mixed);
-    float* r32 = mixed ? g.lv[0].f32 : nullptr;
-    double res = fine_residual(s, g, r32);
-    double vmax = bits_to_double(s->hsc->vmax);
-    int cycles = 0, slow = 0;
-    double prev = res;
-    while (cycles < s->opt.max_cycles) {
-        const double tol = s->opt.lin_tol * std::max(vmax, 1e-300);
-        if (res <= tol || res == 0.0) break;
-        if (mixed) {
-            vcycle<float>(s, g, 0, true);
-            launch_axpy32(g.v, g.lv[0].u32, g.n, s->st);
+    SolveArgs a{};
+    a.K = g.Kd;
+    a.code = g.code;
+    a.v = g.v;
+    a.rhs = g.rhs;
+    a.nlev = (int)g.lv.size();
+    a.tail = tail_level(s, g);
+    a.nu1 = s->opt.nu1;
+    a.nu2 = s->opt.nu2;
+    a.max_cycles = s->opt.max_cycles;
+    a.mixed = mixed ? 1 : 0;
+    a.do_setup = do_setup ? 1 : 0;
+    a.lin_tol = s->opt.lin_tol;
+    a.rel_tol = rel_tol;
+    a.inv = g.inv;
+    a.inv_status = g.dstatus;
+    a.bar = &s->mgd->bar;
+    a.out = &s->mgd->out;
+    for (int l = 0; l < a.nlev; ++l) {
+        Level& Lv = g.lv[l];
+        LevelArgs& L = a.L[l];
+        L.side = Lv.side;
+        L.sc = (Lv.side - 1) / 2;
+        L.n = Lv.n;
+        if (l == 0) {
+            L.u = mixed ? (void*)Lv.u32 : (void*)g.v;
+            L.f = mixed ? (void*)Lv.f32 : (void*)g.rhs;
         } else {
-            vcycle<double>(s, g, 0, false);
+            L.u = mixed ? (void*)Lv.u32 : (void*)Lv.u64;
+            L.f = mixed ? (void*)Lv.f32 : (void*)Lv.f64;
+            L.A = mixed ? (const void*)Lv.A32 : (const void*)Lv.A64;
         }
-        ++cycles;
-        res = fine_residual(s, g, r32);
-        vmax = bits_to_double(s->hsc->vmax);
-        // float64 floor: the residual no longer decreases
-        slow = res > 0.5 * prev ? slow + 1 : 0;
-        if (slow >= 2 && res < 1e-12 * std::max(vmax, 1e-300)) break;
-        prev = std::min(prev, res);
+        L.P = mixed ? (const void*)Lv.P32 : (const void*)Lv.P64;
+        L.A64 = Lv.A64;
+        L.A32 = Lv.A32;
+        L.P64 = Lv.P64;
+        L.P32 = Lv.P32;
     }
-    cnt.cycles += cycles;
-    cnt.last_lin_res = res;
-    return cycles;
+    // levels from smem_from on are staged in block 0's shared memory, as many as fit
+    a.smem_from = std::max(a.tail, 1);
+    while (a.smem_from < a.nlev && tail_smem_bytes(a, mixed ? 4 : 8) > (size_t)kTailSmemMax)
+        ++a.smem_from;
+    GS_CUDA(cudaMemsetAsync(s->mgd, 0, sizeof(MGState), s->st));
+    {
+        KScope ks(s, GS_K_MG_SOLVE);
+        launch_mg_solve(a, s->st);
+    }
+    GS_CUDA(cudaMemcpyAsync(s->mgh, s->mgd, sizeof(MGState), cudaMemcpyDeviceToHost, s->st));
+    sync(s);
+    if (s->mgh->bar.error) {
+        set_last_error("multigrid solve: a grid barrier wait timed out");
+        throw Error{GS_ETIMEOUT};
+    }
+    if (do_setup) {
+        g.hier_valid = true;
+        g.stale_rows = 0;
+    }
+    cnt.cycles += s->mgh->out.cycles;
+    cnt.last_lin_res = s->mgh->out.res;
+    return s->mgh->out.reason != 2;
+}
+
+// The Galerkin hierarchy must be rebuilt unless it was built for (nearly)
+// the current policy codes.
+bool need_setup(const gs_solver* s, const IsaacsGrid& g) {
+    if (!g.hier_valid) return true;
+    return (double)g.stale_rows > s->opt.setup_reuse * (double)g.n;
 }
 
 void vmax_to_device(gs_solver* s, IsaacsGrid& g) {
@@ -433,6 +378,7 @@ void vmax_to_device(gs_solver* s, IsaacsGrid& g) {
 // solved by multigrid.  Starts from g.v, g.alpha and (if beta_given) g.beta.
 bool amgpi(gs_solver* s, IsaacsGrid& g, double eps, bool beta_given, Counters& cnt) {
     cudaStream_t st = s->st;
+    g.hier_valid = false;
     if (!beta_given) {
         vmax_to_device(s, g);
         KScope ks(s, GS_K_IMPROVE);
@@ -444,14 +390,26 @@ bool amgpi(gs_solver* s, IsaacsGrid& g, double eps, bool beta_given, Counters& c
     bool converged = false;
     int outer = 0;
     while (true) {
-        for (int j = 0; j < s->opt.max_inner; ++j) {
-            linear_solve(s, g, cnt);
-            ++cnt.systems;
+        auto inner_improve = [&]() {
             vmax_to_device(s, g);
             KScope ks(s, GS_K_IMPROVE);
             launch_isaacs_improve(IMP_INNER, g.Kd, g.side, g.variant, g.v, g.r0, g.alpha, g.beta,
                                   g.code, g.rhs, nullptr, s->dsc, st);
-            if (read_scalars(s).changed == 0) break;
+            const DevScalars& h = read_scalars(s);
+            g.stale_rows += h.code_changed;
+            return h.changed;
+        };
+        for (int j = 0; j < s->opt.max_inner; ++j) {
+            // Algorithm 1 step 1: evaluate MIN's policy (inexactly inside the loop)
+            const bool exact = linear_solve(s, g, cnt, s->opt.pi_rtol, need_setup(s, g));
+            ++cnt.systems;
+            if (inner_improve() != 0) continue;
+            if (!exact) {
+                // confirm on the float64-floor solution of the same system before stopping
+                linear_solve(s, g, cnt, 0.0, need_setup(s, g));
+                if (inner_improve() != 0) continue;
+            }
+            break;
         }
         ++outer;
         vmax_to_device(s, g);
@@ -461,6 +419,7 @@ bool amgpi(gs_solver* s, IsaacsGrid& g, double eps, bool beta_given, Counters& c
                                   g.code, g.rhs, g.fv, s->dsc, st);
         }
         const DevScalars& h = read_scalars(s);
+        g.stale_rows += h.code_changed;
         cnt.res_inf = bits_to_double(h.res);
         cnt.res_l2 = std::sqrt(h.res_sq / (double)g.n);
         if (cnt.res_inf <= eps || h.changed == 0) {
@@ -616,7 +575,8 @@ gs_status run_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* be
     else GS_CUDA(cudaMemsetAsync(g.v, 0, g.n * sizeof(double), s->st));
     launch_isaacs_assemble(g.Kd, g.side, g.alpha, g.beta, g.r0, g.code, g.rhs, s->st);
     Counters cnt;
-    linear_solve(s, g, cnt);
+    g.hier_valid = false;
+    linear_solve(s, g, cnt, 0.0, true);
     GS_CUDA(cudaMemcpyAsync(w_out, g.v, g.n * sizeof(double), cudaMemcpyDefault, s->st));
     sync(s);
     if (stats) {

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "mgsolve.cuh"
 
 namespace gs {
 
@@ -53,6 +54,8 @@ struct IsaacsGrid {
     std::vector<Level> lv;
     double* inv = nullptr;     // explicit inverse of the coarsest operator
     int* dstatus = nullptr;
+    bool hier_valid = false;   // hierarchy built for (nearly) the current codes
+    long long stale_rows = 0;  // rows whose code changed since the hierarchy was built
 };
 
 struct Problem {
@@ -73,6 +76,12 @@ struct Counters {
 }  // namespace gs
 
 namespace gs {
+// Device state of one multigrid solve launch (barrier and results).
+struct MGState {
+    GridBarrier bar;
+    SolveOut out;
+};
+
 // CUDA-event brackets around the launches of one kernel class.
 struct Tracer {
     int cls = 0;
@@ -89,6 +98,8 @@ struct gs_solver {
     cudaStream_t st = nullptr;
     gs::DevScalars* dsc = nullptr;     // device scalars
     gs::DevScalars* hsc = nullptr;     // pinned host mirror
+    gs::MGState* mgd = nullptr;        // multigrid launch state (device)
+    gs::MGState* mgh = nullptr;        // pinned host mirror
     std::unique_ptr<gs::Problem> prob;
     bool init_v = false, init_alpha = false, init_beta = false;
     int last_levels = 0;

@@ -1,21 +1,22 @@
-// Structured algebraic multigrid on 2^k - 1 grids: generic device code shared
-// by the fine Isaacs level (implicit 5-point rows from policy codes) and the
-// coarse levels (explicit 9-point rows).
+// Structured algebraic multigrid on 2^k - 1 grids: device code shared by the
+// fine Isaacs level (implicit 5-point rows from policy codes) and the coarse
+// levels (explicit 9-point rows).
 //
 // C/F splitting (Sec. 4.3): the coarse variables C of a level of side sf are
 // its points (2I+1, 2J+1), I, J in [0, sc), sc = (sf-1)/2; the others are F.
-// Interpolation P (Sec. 4.3, P^l_{l+1}) is operator dependent: an F point on
-// an x-edge interpolates from its two C neighbours with the row collapsed
-// along y, a y-edge point likewise, and a cell corner from the four diagonal C
-// points through its own row and the edge weights.  Restriction is P^T and
-// the coarse operator is the Galerkin product A^{l+1} = P^T A^l P.
+// Interpolation P^l_{l+1} is operator dependent: an F point on an x-edge
+// interpolates from its two C neighbours with its row collapsed along y, a
+// y-edge point likewise along x, and a cell corner from the four diagonal C
+// points through its own row and the edge weights.  Restriction is
+// R = P^T and the coarse operator is the Galerkin product A^{l+1} = R A^l P.
 #pragma once
 
 #include "common.cuh"
 
 namespace gs {
 
-// Explicit 9-point rows A[d * n + x].
+// ------------------------------------------------------------------ rows
+// Explicit 9-point rows A[d * n + x] (float64).
 struct Src9 {
     const double* A;
     int side;
@@ -23,18 +24,18 @@ struct Src9 {
     __device__ __forceinline__ void row(int i, int j, double a[9]) const {
         size_t x = (size_t)j * side + i;
 #pragma unroll
-        for (int d = 0; d < 9; ++d) a[d] = __ldg(A + d * n + x);
+        for (int d = 0; d < 9; ++d) a[d] = A[d * n + x];
     }
 };
 
 // Implicit 5-point rows of the fine Isaacs level: the row of A = I - mu M for
-// the policy code at the point, with couplings to boundary points dropped.
+// the policy code at the point, couplings to boundary points dropped.
 struct Src5 {
     const IsaacsConsts* K;
     const uint8_t* code;
     int side;
     __device__ __forceinline__ void row(int i, int j, double a[9]) const {
-        int c = __ldg(code + (size_t)j * side + i);
+        int c = code[(size_t)j * side + i];
         const double* am = K->am[c];
         a[DC] = am[0];
         a[DW] = i > 0 ? am[1] : 0.0;
@@ -45,27 +46,160 @@ struct Src5 {
     }
 };
 
-// Edge weights (F points on cell edges), one thread per cell (I, J) in [0, sc]^2.
+// Row sum of an implicit fine row (the leakage 1 - mu sum_y p(y)), float64.
+__device__ __forceinline__ double l0_rowsum(const IsaacsConsts* K, int c, int i, int j, int side) {
+    if (c == kStopCode) return 1.0;
+    const double* am = K->am[c];
+    double s = K->kappa;
+    if (i == 0) s -= am[1];
+    if (i + 1 == side) s -= am[2];
+    if (j == 0) s -= am[3];
+    if (j + 1 == side) s -= am[4];
+    return s;
+}
+
+// The same row sum in float32 for the float32 path: kappa plus the mass of
+// the couplings dropped at the boundary (all terms non-negative).
+__device__ __forceinline__ float l0_rowsum_f(const IsaacsConsts* K, int c, int i, int j, int side) {
+    if (c == kStopCode) return 1.0f;
+    const float* am = K->amf[c];
+    float s = K->kappa_f;
+    if (i == 0) s -= am[1];
+    if (i + 1 == side) s -= am[2];
+    if (j == 0) s -= am[3];
+    if (j + 1 == side) s -= am[4];
+    return s;
+}
+
+// ------------------------------------------------------------------ level operators
+// Residual f - A u at (i, j) and one Gauss-Seidel update of u at (i, j).
+// The float32 forms use the leakage representation: the row sum s is kept
+// separately and the diagonal is re-formed as s - sum(off-diagonals), so that
+// the small row sums carrying the discount survive the rounding.
+template <typename T>
+struct L0Op;
+
+template <>
+struct L0Op<double> {
+    const IsaacsConsts* K;
+    const uint8_t* code;
+    int side;
+    __device__ __forceinline__ double resid(const double* f, const double* u, int i, int j) const {
+        const size_t x = (size_t)j * side + i;
+        const double* am = K->am[code[x]];
+        double Au = am[0] * u[x];
+        if (i > 0) Au += am[1] * u[x - 1];
+        if (i + 1 < side) Au += am[2] * u[x + 1];
+        if (j > 0) Au += am[3] * u[x - side];
+        if (j + 1 < side) Au += am[4] * u[x + side];
+        return f[x] - Au;
+    }
+    // Gauss-Seidel value of u at (i, j) (neighbours from u; zero: u == 0).
+    __device__ __forceinline__ double relaxed(const double* f, const double* u, int i, int j,
+                                              bool zero) const {
+        const size_t x = (size_t)j * side + i;
+        const double* am = K->am[code[x]];
+        double s = f[x];
+        if (!zero) {
+            if (i > 0) s -= am[1] * u[x - 1];
+            if (i + 1 < side) s -= am[2] * u[x + 1];
+            if (j > 0) s -= am[3] * u[x - side];
+            if (j + 1 < side) s -= am[4] * u[x + side];
+        }
+        return s / am[0];
+    }
+};
+
+template <>
+struct L0Op<float> {
+    const IsaacsConsts* K;
+    const uint8_t* code;
+    int side;
+    __device__ __forceinline__ float resid(const float* f, const float* u, int i, int j) const {
+        const size_t x = (size_t)j * side + i;
+        const int c = code[x];
+        const float* am = K->amf[c];
+        const float ux = u[x];
+        float Au = l0_rowsum_f(K, c, i, j, side) * ux;
+        if (i > 0) Au += am[1] * (u[x - 1] - ux);
+        if (i + 1 < side) Au += am[2] * (u[x + 1] - ux);
+        if (j > 0) Au += am[3] * (u[x - side] - ux);
+        if (j + 1 < side) Au += am[4] * (u[x + side] - ux);
+        return f[x] - Au;
+    }
+    __device__ __forceinline__ float relaxed(const float* f, const float* u, int i, int j,
+                                             bool zero) const {
+        const size_t x = (size_t)j * side + i;
+        const int c = code[x];
+        const float* am = K->amf[c];
+        float diag = l0_rowsum_f(K, c, i, j, side), s = f[x];
+        if (i > 0) { diag -= am[1]; if (!zero) s -= am[1] * u[x - 1]; }
+        if (i + 1 < side) { diag -= am[2]; if (!zero) s -= am[2] * u[x + 1]; }
+        if (j > 0) { diag -= am[3]; if (!zero) s -= am[3] * u[x - side]; }
+        if (j + 1 < side) { diag -= am[4]; if (!zero) s -= am[4] * u[x + side]; }
+        return s / diag;
+    }
+};
+
+// 9-point levels: float64 rows hold the entries of A; float32 rows hold the
+// row sum in slot 0 and the off-diagonal entries in slots 1..8.
+template <typename T>
+struct L9Op {
+    const T* A;
+    size_t n;
+    int side;
+    __device__ __forceinline__ T resid(const T* f, const T* u, int i, int j) const {
+        const size_t x = (size_t)j * side + i;
+        const T ux = u[x];
+        T Au = A[x] * ux;
+#pragma unroll
+        for (int d = 1; d < 9; ++d) {
+            const int gi = i + dir_di(d), gj = j + dir_dj(d);
+            const bool in = gi >= 0 && gj >= 0 && gi < side && gj < side;
+            const T ud = in ? u[(size_t)gj * side + gi] : T(0);
+            if constexpr (sizeof(T) == 8) Au += A[d * n + x] * ud;
+            else Au += A[d * n + x] * (ud - ux);
+        }
+        return f[x] - Au;
+    }
+    __device__ __forceinline__ void relax(const T* f, T* u, int i, int j, bool zero) const {
+        const size_t x = (size_t)j * side + i;
+        T s = f[x];
+        T diag = A[x];
+#pragma unroll
+        for (int d = 1; d < 9; ++d) {
+            const T a = A[d * n + x];
+            if constexpr (sizeof(T) == 4) diag -= a;
+            if (zero) continue;
+            const int gi = i + dir_di(d), gj = j + dir_dj(d);
+            if (gi < 0 || gj < 0 || gi >= side || gj >= side) continue;
+            s -= a * u[(size_t)gj * side + gi];
+        }
+        u[x] = s / diag;
+    }
+};
+
+// ------------------------------------------------------------------ interpolation
+// Edge weights of cell t = (I, J), I, J in [0, sc].
 template <class Src>
-__global__ void k_interp_edges(Src src, int sc, double* __restrict__ P, float* __restrict__ P32) {
+__device__ __forceinline__ void interp_edges_item(const Src& src, int sc, size_t t, double* P,
+                                                  float* P32) {
     const int nc1 = sc + 1;
     const size_t ncell = (size_t)nc1 * nc1;
-    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncell) return;
-    int I = (int)(t % nc1), J = (int)(t / nc1);
+    const int I = (int)(t % nc1), J = (int)(t / nc1);
     double a[9];
     double wxW = 0, wxE = 0, wyS = 0, wyN = 0;
-    if (J < sc) {          // x-edge point (2I, 2J+1): collapse the row along y
+    if (J < sc) {          // x-edge point (2I, 2J+1): row collapsed along y
         src.row(2 * I, 2 * J + 1, a);
-        double dC = a[DC] + a[DS] + a[DN];
+        const double dC = a[DC] + a[DS] + a[DN];
         if (dC > 0) {
             wxW = -(a[DW] + a[DSW] + a[DNW]) / dC;
             wxE = -(a[DE] + a[DSE] + a[DNE]) / dC;
         }
     }
-    if (I < sc) {          // y-edge point (2I+1, 2J): collapse the row along x
+    if (I < sc) {          // y-edge point (2I+1, 2J): row collapsed along x
         src.row(2 * I + 1, 2 * J, a);
-        double dC = a[DC] + a[DW] + a[DE];
+        const double dC = a[DC] + a[DW] + a[DE];
         if (dC > 0) {
             wyS = -(a[DS] + a[DSW] + a[DSE]) / dC;
             wyN = -(a[DN] + a[DNW] + a[DNE]) / dC;
@@ -83,27 +217,26 @@ __global__ void k_interp_edges(Src src, int sc, double* __restrict__ P, float* _
     }
 }
 
-// Corner weights: the corner point (2I, 2J) solves its own row for the value
-// given the (already interpolated) values of its 8 neighbours.
+// Corner weights: the corner point (2I, 2J) solves its own row given the
+// interpolated values of its 8 neighbours (needs the edge weights).
 template <class Src>
-__global__ void k_interp_corners(Src src, int sc, double* __restrict__ P, float* __restrict__ P32) {
+__device__ __forceinline__ void interp_corners_item(const Src& src, int sc, size_t t, double* P,
+                                                    float* P32) {
     const int nc1 = sc + 1;
     const size_t ncell = (size_t)nc1 * nc1;
-    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncell) return;
-    int I = (int)(t % nc1), J = (int)(t / nc1);
+    const int I = (int)(t % nc1), J = (int)(t / nc1);
     double a[9];
     src.row(2 * I, 2 * J, a);
-    size_t cW = t - 1, cS = t - nc1;
+    const size_t cW = t - 1, cS = t - nc1;
     // west neighbour (2I-1, 2J): y-edge of cell (I-1, J); east (2I+1, 2J): of cell (I, J)
-    double yS_W = I >= 1 ? P[PYS * ncell + cW] : 0.0, yN_W = I >= 1 ? P[PYN * ncell + cW] : 0.0;
-    double yS_E = I < sc ? P[PYS * ncell + t] : 0.0, yN_E = I < sc ? P[PYN * ncell + t] : 0.0;
+    const double yS_W = I >= 1 ? P[PYS * ncell + cW] : 0.0, yN_W = I >= 1 ? P[PYN * ncell + cW] : 0.0;
+    const double yS_E = I < sc ? P[PYS * ncell + t] : 0.0, yN_E = I < sc ? P[PYN * ncell + t] : 0.0;
     // south neighbour (2I, 2J-1): x-edge of cell (I, J-1); north (2I, 2J+1): of cell (I, J)
-    double xW_S = J >= 1 ? P[PXW * ncell + cS] : 0.0, xE_S = J >= 1 ? P[PXE * ncell + cS] : 0.0;
-    double xW_N = J < sc ? P[PXW * ncell + t] : 0.0, xE_N = J < sc ? P[PXE * ncell + t] : 0.0;
+    const double xW_S = J >= 1 ? P[PXW * ncell + cS] : 0.0, xE_S = J >= 1 ? P[PXE * ncell + cS] : 0.0;
+    const double xW_N = J < sc ? P[PXW * ncell + t] : 0.0, xE_N = J < sc ? P[PXE * ncell + t] : 0.0;
     double wSW = 0, wSE = 0, wNW = 0, wNE = 0;
     if (a[DC] > 0) {
-        double inv = 1.0 / a[DC];
+        const double inv = 1.0 / a[DC];
         wSW = -(a[DSW] + a[DW] * yS_W + a[DS] * xW_S) * inv;
         wSE = -(a[DSE] + a[DE] * yS_E + a[DS] * xE_S) * inv;
         wNW = -(a[DNW] + a[DW] * yN_W + a[DN] * xW_N) * inv;
@@ -123,8 +256,8 @@ __global__ void k_interp_corners(Src src, int sc, double* __restrict__ P, float*
 
 // Coarse points from which the fine point (gi, gj) interpolates, with weights.
 template <typename W>
-__device__ __forceinline__ int interp_of(const W* __restrict__ P, int sc, int gi, int gj,
-                                         int cI[4], int cJ[4], W w[4]) {
+__device__ __forceinline__ int interp_of(const W* P, int sc, int gi, int gj, int cI[4], int cJ[4],
+                                         W w[4]) {
     const int nc1 = sc + 1;
     const size_t ncell = (size_t)nc1 * nc1;
     const int I = gi >> 1, J = gj >> 1;
@@ -151,11 +284,10 @@ __device__ __forceinline__ int interp_of(const W* __restrict__ P, int sc, int gi
     return 4;
 }
 
-// Weight of the fine point (2I+1+di, 2J+1+dj) towards the coarse point (I, J),
-// i.e. the restriction coefficient R = P^T.
+// Weight of the fine point (2I+1+di, 2J+1+dj) towards the coarse point (I, J):
+// the restriction coefficient R = P^T.
 template <typename W>
-__device__ __forceinline__ W restrict_weight(const W* __restrict__ P, int sc, int I, int J,
-                                             int di, int dj) {
+__device__ __forceinline__ W restrict_weight(const W* P, int sc, int I, int J, int di, int dj) {
     const int nc1 = sc + 1;
     const size_t ncell = (size_t)nc1 * nc1;
     if (di == 0 && dj == 0) return W(1);
@@ -169,51 +301,90 @@ __device__ __forceinline__ W restrict_weight(const W* __restrict__ P, int sc, in
                   : P[PSW * ncell + (size_t)(J + 1) * nc1 + I + 1];
 }
 
-// Galerkin coarse operator A_c = P^T A P (float64 accumulation), one thread per
-// coarse point; the result is a 9-point stencil on the coarse grid.
+// Adds v to the coarse stencil entry towards (I + tx, J + ty) if that point is
+// an unknown (coarse boundary points carry the Dirichlet value 0).
+__device__ __forceinline__ void rap_add(double acc[9], int I, int J, int sc, int tx, int ty, double v) {
+    if (I + tx >= 0 && I + tx < sc && J + ty >= 0 && J + ty < sc) acc[dir_of(tx, ty)] += v;
+}
+
+// Scatters RA = R(., i) A(i, g) along the interpolation row of the fine point g
+// at offset (qx, qy) in [-2, 2]^2 from the coarse point's fine position
+// (2I+1, 2J+1).  After unrolling, qx and qy are constants: the point's type
+// (C, x-edge, y-edge, corner), its cell and its coarse targets fold away and
+// acc stays in registers.
+__device__ __forceinline__ void rap_scatter(const double* P, int sc, int I, int J, int qx, int qy,
+                                            double RA, double acc[9]) {
+    const int nc1 = sc + 1;
+    const size_t ncell = (size_t)nc1 * nc1;
+    const bool xC = (qx & 1) == 0, yC = (qy & 1) == 0;
+    if (xC && yC) {
+        rap_add(acc, I, J, sc, qx / 2, qy / 2, RA);
+    } else if (!xC && yC) {                     // x-edge of cell (I + (1+qx)/2, J + qy/2)
+        const int tx = (1 + qx) / 2, ty = qy / 2;
+        const size_t c = (size_t)(J + ty) * nc1 + (I + tx);
+        rap_add(acc, I, J, sc, tx - 1, ty, RA * P[PXW * ncell + c]);
+        rap_add(acc, I, J, sc, tx, ty, RA * P[PXE * ncell + c]);
+    } else if (xC && !yC) {                     // y-edge of cell (I + qx/2, J + (1+qy)/2)
+        const int tx = qx / 2, ty = (1 + qy) / 2;
+        const size_t c = (size_t)(J + ty) * nc1 + (I + tx);
+        rap_add(acc, I, J, sc, tx, ty - 1, RA * P[PYS * ncell + c]);
+        rap_add(acc, I, J, sc, tx, ty, RA * P[PYN * ncell + c]);
+    } else {                                    // corner of cell (I + (1+qx)/2, J + (1+qy)/2)
+        const int tx = (1 + qx) / 2, ty = (1 + qy) / 2;
+        const size_t c = (size_t)(J + ty) * nc1 + (I + tx);
+        rap_add(acc, I, J, sc, tx - 1, ty - 1, RA * P[PSW * ncell + c]);
+        rap_add(acc, I, J, sc, tx, ty - 1, RA * P[PSE * ncell + c]);
+        rap_add(acc, I, J, sc, tx - 1, ty, RA * P[PNW * ncell + c]);
+        rap_add(acc, I, J, sc, tx, ty, RA * P[PNE * ncell + c]);
+    }
+}
+
+// Galerkin coarse row A_c(t, .) = (P^T A P)(t, .) for the coarse point t
+// (float64 accumulation); also its float32 leakage form when A32 is given.
 template <class Src>
-__global__ void k_rap(Src src, int sc, const double* __restrict__ P, double* __restrict__ Ac) {
+__device__ __forceinline__ void rap_item(const Src& src, int sc, size_t t, const double* P,
+                                         double* Ac, float* A32) {
     const size_t nc = (size_t)sc * sc;
-    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nc) return;
     const int I = (int)(t % sc), J = (int)(t / sc);
     const int sf = 2 * sc + 1;
     double acc[9];
 #pragma unroll
     for (int d = 0; d < 9; ++d) acc[d] = 0.0;
-    for (int dj = -1; dj <= 1; ++dj) {
-        for (int di = -1; di <= 1; ++di) {
-            const double R = restrict_weight(P, sc, I, J, di, dj);
-            if (R == 0.0) continue;
-            const int fi = 2 * I + 1 + di, fj = 2 * J + 1 + dj;
+#pragma unroll
+    for (int oy = -1; oy <= 1; ++oy) {
+#pragma unroll
+        for (int ox = -1; ox <= 1; ++ox) {
+            const double R = restrict_weight(P, sc, I, J, ox, oy);
             double a[9];
-            src.row(fi, fj, a);
+            src.row(2 * I + 1 + ox, 2 * J + 1 + oy, a);
 #pragma unroll
             for (int d = 0; d < 9; ++d) {
-                if (a[d] == 0.0) continue;
-                const int gi = fi + dir_di(d), gj = fj + dir_dj(d);
+                if (a[d] == 0.0) continue;   // folds away for the 5-point fine rows
+                const int qx = ox + dir_di(d), qy = oy + dir_dj(d);
+                const int gi = 2 * I + 1 + qx, gj = 2 * J + 1 + qy;
                 if (gi < 0 || gj < 0 || gi >= sf || gj >= sf) continue;
-                const double RA = R * a[d];
-                int cI[4], cJ[4];
-                double w[4];
-                const int m = interp_of(P, sc, gi, gj, cI, cJ, w);
-                for (int k = 0; k < m; ++k) {
-                    if (cI[k] < 0 || cJ[k] < 0 || cI[k] >= sc || cJ[k] >= sc) continue;
-                    acc[dir_of(cI[k] - I, cJ[k] - J)] += RA * w[k];
-                }
+                rap_scatter(P, sc, I, J, qx, qy, R * a[d], acc);
             }
         }
     }
+    double s = 0.0;
 #pragma unroll
-    for (int d = 0; d < 9; ++d) Ac[d * nc + t] = acc[d];
+    for (int d = 0; d < 9; ++d) {
+        Ac[d * nc + t] = acc[d];
+        s += acc[d];
+    }
+    if (A32) {
+        A32[t] = (float)s;
+#pragma unroll
+        for (int d = 1; d < 9; ++d) A32[d * nc + t] = (float)acc[d];
+    }
 }
 
 // Explicit inverse of the coarsest operator (n = side^2 <= 64) by Gauss-Jordan
-// elimination with partial pivoting, in one thread block.  status[0] is set to
-// 1 if a pivot vanished.
+// elimination with partial pivoting, by one thread block; M is n x 2n shared
+// memory.  *status is set to 1 if a pivot vanished.
 template <class Src>
-__global__ void k_coarse_invert(Src src, int side, double* __restrict__ inv, int* status) {
-    extern __shared__ double M[];   // n rows of 2n
+__device__ void coarse_invert_block(const Src& src, int side, double* M, double* inv, int* status) {
     const int n = side * side, w = 2 * n;
     for (int e = threadIdx.x; e < n * w; e += blockDim.x) M[e] = 0.0;
     __syncthreads();
@@ -235,20 +406,19 @@ __global__ void k_coarse_invert(Src src, int side, double* __restrict__ inv, int
             int best = k;
             double bv = fabs(M[k * w + k]);
             for (int r = k + 1; r < n; ++r) {
-                double v = fabs(M[r * w + k]);
+                const double v = fabs(M[r * w + k]);
                 if (v > bv) { bv = v; best = r; }
             }
             piv = best;
-            if (bv == 0.0) status[0] = 1;
+            if (bv == 0.0) *status = 1;
         }
         __syncthreads();
-        if (piv != k) {
+        if (piv != k)
             for (int c = threadIdx.x; c < w; c += blockDim.x) {
-                double tmp = M[k * w + c];
+                const double tmp = M[k * w + c];
                 M[k * w + c] = M[piv * w + c];
                 M[piv * w + c] = tmp;
             }
-        }
         __syncthreads();
         const double d = M[k * w + k];
         const double dinv = d != 0.0 ? 1.0 / d : 0.0;
@@ -266,6 +436,7 @@ __global__ void k_coarse_invert(Src src, int side, double* __restrict__ inv, int
         __syncthreads();
     }
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) inv[e] = M[(e / n) * w + n + (e % n)];
+    __syncthreads();
 }
 
 }  // namespace gs

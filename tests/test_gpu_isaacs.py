@@ -154,3 +154,21 @@ def test_status_codes(gs):
         with pytest.raises(gs.GameSolveError) as e:
             s.set_isaacs_grid(255, 0, 1)
         assert e.value.status == gs.GS_ENOMEM
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("tail_side", [1, 7, 15, 31, 63])
+def test_vcycle_count_size_independent(gs, prec, tail_side):
+    """AMG cycles per system stay bounded as the grid grows (the paper's tables
+    report 3-5 W-cycles per system at every size), whatever the split between
+    grid-wide and single-block levels."""
+    rng = np.random.default_rng(11)
+    for side in (63, 255, 1023):
+        n = side * side
+        alpha = rng.integers(0, 4, size=n).astype(np.uint8)
+        beta = rng.integers(0, 4, size=(n, 4)).astype(np.uint8)
+        with gs.GameSolver(precision=prec, tail_side=tail_side) as s:
+            s.set_isaacs_grid(side, 0, 1)
+            _, st = s.policy_solve(alpha, beta)
+        assert st["cycles"] <= 14, (side, st)
+        assert st["res_inf"] < 1e-14
