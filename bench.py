@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Isaacs solves/s at 1023^2 (FP32+refine vs FP64), HBM GB/s, p50/p99 latency"
-SIDE = 1023
+SIDE = 1023          # the metric's workload; --side changes it (e.g. 2047 for profiling)
 SEED = 2
 
 # Algorithmic bytes of the multigrid solve kernel (one launch per linear
@@ -51,10 +51,11 @@ def mg_bytes_per_state(prec: str):
     return {"check": check, "cycle": cycle, "setup": setup}
 
 
-def mg_bytes(n: int, prec: str, systems: int, cycles: int) -> float:
-    """Algorithmic bytes of `systems` solve launches running `cycles` V-cycles in all."""
+def mg_cycle_bytes(n: int, prec: str, launches: int, cycles: int) -> float:
+    """Algorithmic bytes of `launches` V-cycle launches running `cycles` cycles in all
+    (each launch evaluates the float64 residual once more than it has cycles)."""
     b = mg_bytes_per_state(prec)
-    return n * (systems * (b["setup"] + b["check"]) + cycles * (b["cycle"] + b["check"]))
+    return n * (launches * b["check"] + cycles * (b["cycle"] + b["check"]))
 
 
 def load_peaks():
@@ -177,6 +178,20 @@ def run_reference(args):
     return 0
 
 
+def run_profile(args):
+    """One solve of the workload and nothing else (a short command for ncu)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1107_1653_gb300 as gs
+    with gs.GameSolver(precision=args.precision, fmg=args.fmg, fmg_side=31,
+                       stream=torch.cuda.current_stream()) as s:
+        s.set_isaacs_grid(SIDE, 0, SEED)
+        st = s.solve()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": True, "side": SIDE, "precision": args.precision, **st}))
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -266,15 +281,15 @@ def run_ours(args):
     if clk:
         line["clocks"] = clk
 
-    # roofline of the dominant kernel: the multigrid solve launch (one per system)
+    # roofline of the dominant kernel: the V-cycle launch (one or two per system)
     peak, peak_kind = load_peaks()
     if tr_n:
         kind = "mixed" if prec != "fp64" else "fp64"
-        total = mg_bytes(n, kind, stats["systems"] * args.steps, stats["cycles"] * args.steps)
+        total = mg_cycle_bytes(n, kind, tr_n, stats["cycles"] * args.steps)
         bpl = total / tr_n
         avg_s = tr_ms * 1e-3 / tr_n
         ach = bpl / avg_s / 1e9
-        line["roofline"] = {"kernel": "k_mg_solve", "bound": "hbm", "achieved": ach,
+        line["roofline"] = {"kernel": "k_mg_cycles", "bound": "hbm", "achieved": ach,
                             "peak": peak, "unit": "GB/s", "frac": ach / peak,
                             "peak_source": peak_kind, "traffic": None,
                             "launches": tr_n, "avg_us": avg_s * 1e6,
@@ -330,10 +345,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_bf16"])
     ap.add_argument("--fmg", type=int, default=0)
-    ap.add_argument("--trace-kernel", default="mg_solve", choices=["mg_solve", "none"])
+    ap.add_argument("--trace-kernel", default="mg_cycles", choices=["mg_cycles", "none"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", type=int, default=SIDE)
+    ap.add_argument("--profile", action="store_true",
+                    help="run one solve only (for ncu); prints the solve statistics")
     args = ap.parse_args()
+    globals()["SIDE"] = args.side
+    if args.profile:
+        return run_profile(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -50,7 +50,7 @@ typedef enum {
 typedef enum {
     GS_PREC_FP64 = 0,        /* every step in float64 */
     GS_PREC_MIXED = 1,       /* float32 V-cycles inside float64 iterative refinement */
-    GS_PREC_MIXED_BF16 = 2   /* as MIXED, coarse stencils / game weights stored in bfloat16 */
+    GS_PREC_MIXED_BF16 = 2   /* reserved: bfloat16 weight storage (not built; rejected) */
 } gs_precision;
 
 /* Solver options.  Fill with gamesolve_default_options, then override. */
@@ -176,8 +176,8 @@ gs_status gamesolve_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8
 typedef enum {
     GS_K_NONE = 0,
     GS_K_IMPROVE = 1,        /* policy improvement fused with the assembly (one launch) */
-    GS_K_MG_SOLVE = 2        /* multigrid solve of one policy-fixed system (one launch:
-                                Galerkin set-up, V-cycles and the float64 stopping test) */
+    GS_K_MG_SETUP = 2,       /* Galerkin set-up of one policy-fixed system (one launch) */
+    GS_K_MG_CYCLES = 3       /* V-cycles and the float64 stopping test of one system */
 } gs_kernel_class;
 
 /* Selects one kernel class whose launches the following solves bracket with

@@ -22,7 +22,7 @@ lib = ctypes.CDLL(LIB_PATH)
 
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_ENOTCONV, GS_ETIMEOUT, GS_ECUDA, GS_ESTATE = range(7)
 GS_PREC_FP64, GS_PREC_MIXED, GS_PREC_MIXED_BF16 = range(3)
-KERNEL_CLASSES = {"none": 0, "improve": 1, "mg_solve": 2}
+KERNEL_CLASSES = {"none": 0, "improve": 1, "mg_setup": 2, "mg_cycles": 3}
 PRECISIONS = {"fp64": GS_PREC_FP64, "mixed": GS_PREC_MIXED, "mixed_bf16": GS_PREC_MIXED_BF16}
 
 

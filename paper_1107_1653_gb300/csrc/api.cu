@@ -71,7 +71,7 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
     gs_options o;
     if (opt) o = *opt;
     else gamesolve_default_options(&o);
-    if (o.precision < 0 || o.precision > 2 || o.max_outer < 1 || o.max_inner < 1 || o.nu1 < 0 ||
+    if (o.precision < GS_PREC_FP64 || o.precision > GS_PREC_MIXED || o.max_outer < 1 || o.max_inner < 1 || o.nu1 < 0 ||
         o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 1 || !(o.lin_tol >= 0) ||
         o.coarse_max < 1 || o.coarse_max > 64 || o.tail_side < 0 || !(o.eps >= 0) || !(o.fmg_c > 0) ||
         (o.fmg && !is_pow2m1(o.fmg_side)) || o.mu_mode < 0 || o.mu_mode > 1 ||
@@ -224,7 +224,7 @@ gs_status gamesolve_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8
 }
 
 gs_status gamesolve_trace(gs_solver* s, int32_t kernel_class) {
-    if (!s || kernel_class < GS_K_NONE || kernel_class > GS_K_MG_SOLVE) return GS_EINVAL;
+    if (!s || kernel_class < GS_K_NONE || kernel_class > GS_K_MG_CYCLES) return GS_EINVAL;
     return guarded([&]() -> gs_status {
         trace_reset(s, kernel_class);
         return GS_OK;

@@ -599,17 +599,20 @@ extern "C" int gamesolve_debug_phase_prof(unsigned long long* ts, int* tags, int
 }
 #endif
 
-void launch_mg_solve(const SolveArgs& a, cudaStream_t st) {
+void launch_mg_setup(const SolveArgs& a, cudaStream_t st) {
     const Occupancy& o = occupancy();
     const int nL = (int)a.L[a.nlev - 1].n;
     void* args[] = {(void*)&a};
-    if (a.do_setup) {
-        const size_t smem = (size_t)2 * nL * nL * sizeof(double);
-        GS_CUDA(cudaLaunchCooperativeKernel((const void*)k_mg_setup,
-                                            dim3(grid_blocks(a, o.setup_per_sm, o.sms)),
-                                            dim3(kMGThreads), args, smem, st));
-        note_launches(1);
-    }
+    const size_t smem = (size_t)2 * nL * nL * sizeof(double);
+    GS_CUDA(cudaLaunchCooperativeKernel((const void*)k_mg_setup,
+                                        dim3(grid_blocks(a, o.setup_per_sm, o.sms)),
+                                        dim3(kMGThreads), args, smem, st));
+    note_launches(1);
+}
+
+void launch_mg_cycles(const SolveArgs& a, cudaStream_t st) {
+    const Occupancy& o = occupancy();
+    void* args[] = {(void*)&a};
     const int elem = a.mixed ? 4 : 8;
     const size_t smem = tail_smem_bytes(a, elem);
     const void* fn = a.mixed ? (const void*)k_mg_cycles<float> : (const void*)k_mg_cycles<double>;

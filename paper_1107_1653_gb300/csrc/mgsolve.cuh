@@ -63,9 +63,11 @@ struct SolveArgs {
     LevelArgs L[kMaxLevels];
 };
 
-// Launches the cooperative set-up (if a.do_setup) and solve on `st`
-// (asynchronous).  bar and out must be zeroed on the stream before the launch.
-void launch_mg_solve(const SolveArgs& a, cudaStream_t st);
+// Cooperative launches on `st` (asynchronous): the Galerkin set-up, then the
+// V-cycles with the stopping test.  bar and out must be zeroed on the stream
+// before the first of them.
+void launch_mg_setup(const SolveArgs& a, cudaStream_t st);
+void launch_mg_cycles(const SolveArgs& a, cudaStream_t st);
 
 // Shared memory the tail levels >= a.smem_from need (elem = 4 or 8 bytes).
 size_t tail_smem_bytes(const SolveArgs& a, int elem);

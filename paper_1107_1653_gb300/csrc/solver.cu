@@ -343,9 +343,13 @@ bool linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bo
     while (a.smem_from < a.nlev && tail_smem_bytes(a, mixed ? 4 : 8) > (size_t)kTailSmemMax)
         ++a.smem_from;
     GS_CUDA(cudaMemsetAsync(s->mgd, 0, sizeof(MGState), s->st));
+    if (do_setup) {
+        KScope ks(s, GS_K_MG_SETUP);
+        launch_mg_setup(a, s->st);
+    }
     {
-        KScope ks(s, GS_K_MG_SOLVE);
-        launch_mg_solve(a, s->st);
+        KScope ks(s, GS_K_MG_CYCLES);
+        launch_mg_cycles(a, s->st);
     }
     GS_CUDA(cudaMemcpyAsync(s->mgh, s->mgd, sizeof(MGState), cudaMemcpyDeviceToHost, s->st));
     sync(s);
