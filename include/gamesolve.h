@@ -192,6 +192,35 @@ gs_status gamesolve_trace_read(gs_solver* s, double* total_ms, int64_t* launches
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t gamesolve_kernel_launches(void);
 
+/* Allocation-free policy-fixed solve for small Isaacs grids.  The paper has
+ * no counterpart: this is a service for callers that cannot let a library
+ * allocate device memory (a host whose device memory is all owned by its own
+ * caching allocator, a real-time loop that must not pay for cudaMalloc /
+ * cudaFree or the device-wide synchronisation they can imply, or code running
+ * where CUDA allocation calls are not permitted).
+ * It solves the same system as gamesolve_policy_solve, (I - mu M^{alpha beta})
+ * w = r^{alpha beta} on the Isaacs game of gamesolve_set_isaacs_grid (side,
+ * variant, seed, xi; literal mu), with the default multigrid options and the
+ * given precision, and allocates no device memory: its scratch is one
+ * 2.5 MiB file-scope device array that every GPU loading the library holds
+ * until the process exits.
+ *  - side must be 2^k - 1 and at most 127 (GS_EINVAL beyond that).
+ *  - alpha (n bytes), beta (n*m1 bytes), w0 (n doubles, NULL = start from 0),
+ *    xi (n doubles, NULL = SplitMix64 stream `seed`) and the output w (n
+ *    doubles) must be device memory of the current device (GS_EINVAL otherwise).
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the array and leaves its contents behind; calls that
+ *    overlap on the GPU (other streams, other host threads) race on it.
+ *  - stream: cudaStream_t for all work (NULL = legacy default stream); the call
+ *    returns when its work is done.  stats may be NULL. */
+gs_status gamesolve_isaacs_policy_solve_static(int32_t side, int32_t variant, uint64_t seed,
+                                               const double* xi, const uint8_t* alpha,
+                                               const uint8_t* beta, const double* w0, double* w,
+                                               int32_t precision, void* stream,
+                                               gs_solve_stats* stats);
+
 /* Frees the solver and all of its device memory.  NULL is a no-op. */
 void gamesolve_destroy(gs_solver* s);
 

@@ -67,6 +67,9 @@ _SIGS = {
     "gamesolve_get_policy": (_S, [_P, _P, _P]),
     "gamesolve_improve": (_S, [_P, _P, _P, _P, _P]),
     "gamesolve_policy_solve": (_S, [_P, _P, _P, _P, _P, ctypes.POINTER(gs_solve_stats)]),
+    "gamesolve_isaacs_policy_solve_static": (_S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                                  _P, _P, _P, _P, _P, ctypes.c_int32, _P,
+                                                  ctypes.POINTER(gs_solve_stats)]),
     "gamesolve_trace": (_S, [_P, ctypes.c_int32]),
     "gamesolve_trace_read": (_S, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "gamesolve_kernel_launches": (ctypes.c_uint64, []),

@@ -135,6 +135,17 @@ const DevScalars& read_scalars(gs_solver* s) {
 
 }  // namespace
 
+void launch_pack_beta(const uint8_t* src, int m1, size_t n, uint32_t* beta, uint8_t* beta4,
+                      cudaStream_t st) {
+    k_pack_beta<<<div_up(n, 256), 256, 0, st>>>(src, m1, n, beta, beta4);
+    GS_CHECK_LAUNCH();
+}
+
+void launch_check_actions(const uint8_t* a, size_t n, int limit, int* bad, cudaStream_t st) {
+    k_check_actions<<<div_up(n, 256), 256, 0, st>>>(a, n, limit, bad);
+    GS_CHECK_LAUNCH();
+}
+
 // ------------------------------------------------------------------ set-up
 IsaacsConsts make_isaacs_consts(int side, int variant, int mu_mode) {
     IsaacsConsts K{};
@@ -445,6 +456,15 @@ void default_policies(gs_solver* s, IsaacsGrid& g) {
 }
 
 }  // namespace
+
+bool solve_policy_system(gs_solver* s, IsaacsGrid& g, int* cycles, double* res) {
+    Counters cnt;
+    g.hier_valid = false;
+    const bool exact = linear_solve(s, g, cnt, 0.0, true);
+    *cycles = cnt.cycles;
+    *res = cnt.last_lin_res;
+    return exact;
+}
 
 gs_status run_solve(gs_solver* s, gs_solve_stats* stats) {
     Problem& P = *s->prob;

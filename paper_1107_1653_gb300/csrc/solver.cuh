@@ -116,6 +116,12 @@ gs_status run_improve(gs_solver* s, const double* v, uint8_t* alpha_out, uint8_t
                       double* fv_out);
 gs_status run_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* beta,
                            const double* w0, double* w_out, gs_solve_stats* stats);
+// Multigrid solve of the assembled policy-fixed system of g to the float64
+// floor (fresh hierarchy); g.v holds the initial guess and receives w.
+bool solve_policy_system(gs_solver* s, IsaacsGrid& g, int* cycles, double* res);
+void launch_pack_beta(const uint8_t* src, int m1, size_t n, uint32_t* beta, uint8_t* beta4,
+                      cudaStream_t st);
+void launch_check_actions(const uint8_t* a, size_t n, int limit, int* bad, cudaStream_t st);
 void trace_harvest(gs_solver* s);
 unsigned long long launch_count();
 void trace_reset(gs_solver* s, int cls);
