@@ -111,12 +111,36 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt);
  * for k in [row_ptr[row], row_ptr[row+1]); reward has n*m1*m2 entries r(x,a,b).
  * Rows may be substochastic (the missing mass leaves the game), so a row
  * without successors is a "stop" action.
- * Errors (GS_EINVAL, solver unchanged): n < 1, m1 or m2 outside [1, 8],
- * row_ptr not non-decreasing from 0, a column out of range, a negative
- * probability, a row sum above 1 + 1e-12, mu outside (0, 1). */
+ * The game is solved by the same one-block-per-game policy iteration as a
+ * batch (at most 16384 states in mixed precision, 8192 in float64); warm
+ * starts (set_initial), improve and policy_solve are for Isaacs grids.
+ * Errors (GS_EINVAL, solver unchanged): n < 1 or too large, m1 or m2 outside
+ * [1, 8], row_ptr not non-decreasing from 0, a column out of range, a
+ * probability outside [0, 1], a row sum above 1 + 1e-12, mu outside (0, 1). */
 gs_status gamesolve_set_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2,
                              const int64_t* row_ptr, const int32_t* col,
                              const double* prob, const double* reward, double mu);
+
+/* Sets a batch of independent finite games (Sec. 2) solved together by one
+ * persistent launch: game g has state_offsets[g+1] - state_offsets[g] states
+ * (state_offsets has count + 1 entries, starting at 0), m1 and m2 actions for
+ * every game, and discount mu[g].  The CSR table concatenates the games' rows
+ * in order (game g's row (x*m1 + a)*m2 + b follows all rows of games < g);
+ * row_ptr has (total states)*m1*m2 + 1 entries starting at 0; col[k] is a
+ * state index within the row's own game.  Values, policies and statistics are
+ * read back concatenated in the same state order.  Each game must have at most
+ * 16384 states (mixed precision) or 8192 (float64).
+ * Errors: as gamesolve_set_game, per row and per game. */
+gs_status gamesolve_set_game_batch(gs_solver* s, int32_t count, int32_t m1, int32_t m2,
+                                   const int64_t* state_offsets, const int64_t* row_ptr,
+                                   const int32_t* col, const double* prob,
+                                   const double* reward, const double* mu);
+
+/* Per-game results of the last solve of a game batch: stats[4g .. 4g+3] =
+ * (MAX policy iterations, linear systems, multigrid cycles, converged) and
+ * res[g] = |F(v) - v|_inf at the returned value.  Either pointer may be NULL.
+ * Errors: GS_ESTATE when no solved batch is held. */
+gs_status gamesolve_get_batch_stats(const gs_solver* s, int32_t* stats, double* res);
 
 /* Sets the finite-difference Isaacs game on the unit square (Sec. 3.3, the
  * upwind scheme (decent) with the centred scheme (centre), scaled to the form

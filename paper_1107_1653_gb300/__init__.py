@@ -60,6 +60,9 @@ _SIGS = {
     "gamesolve_create": (_S, [ctypes.POINTER(_P), ctypes.POINTER(gs_options)]),
     "gamesolve_set_game": (_S, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
                                 ctypes.c_double]),
+    "gamesolve_set_game_batch": (_S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                      _P, _P, _P, _P]),
+    "gamesolve_get_batch_stats": (_S, [_P, _P, _P]),
     "gamesolve_set_isaacs_grid": (_S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P]),
     "gamesolve_set_initial": (_S, [_P, _P, _P, _P]),
     "gamesolve_solve": (_S, [_P, ctypes.POINTER(gs_solve_stats)]),
@@ -171,7 +174,24 @@ class GameSolver:
         prob, reward = _as(prob, np.float64), _as(reward, np.float64)
         _check(lib.gamesolve_set_game(self.h, n, m1, m2, _ptr(row_ptr), _ptr(col), _ptr(prob),
                                       _ptr(reward), mu), "gamesolve_set_game")
-        self.n, self.m1 = n, m1
+        self.n, self.m1, self.count = n, m1, 1
+
+    def set_game_batch(self, state_offsets, m1, m2, row_ptr, col, prob, reward, mu):
+        off = _as(state_offsets, np.int64)
+        row_ptr, col = _as(row_ptr, np.int64), _as(col, np.int32)
+        prob, reward, mu = _as(prob, np.float64), _as(reward, np.float64), _as(mu, np.float64)
+        count = len(off) - 1
+        _check(lib.gamesolve_set_game_batch(self.h, count, m1, m2, _ptr(off), _ptr(row_ptr),
+                                            _ptr(col), _ptr(prob), _ptr(reward), _ptr(mu)),
+               "gamesolve_set_game_batch")
+        self.n, self.m1, self.count = int(off[-1]), m1, count
+
+    def batch_stats(self):
+        st = np.empty((self.count, 4), np.int32)
+        res = np.empty(self.count, np.float64)
+        _check(lib.gamesolve_get_batch_stats(self.h, _ptr(st), _ptr(res)),
+               "gamesolve_get_batch_stats")
+        return st, res
 
     def set_initial(self, v0=None, alpha0=None, beta0=None):
         v0, alpha0, beta0 = _as(v0, np.float64), _as(alpha0, np.uint8), _as(beta0, np.uint8)

@@ -113,8 +113,46 @@ gs_status gamesolve_set_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2,
         set_last_error("set_game: invalid argument");
         return GS_EINVAL;
     }
-    set_last_error("set_game: finite games are not supported by this build");
-    return GS_EINVAL;
+    return guarded([&]() -> gs_status {
+        const int64_t off[2] = {0, n};
+        auto P = build_game_problem(s, 1, m1, m2, off, row_ptr, col, prob, reward, &mu);
+        s->prob = std::move(P);
+        reset_initial(s);
+        return GS_OK;
+    });
+}
+
+gs_status gamesolve_set_game_batch(gs_solver* s, int32_t count, int32_t m1, int32_t m2,
+                                   const int64_t* state_offsets, const int64_t* row_ptr,
+                                   const int32_t* col, const double* prob, const double* reward,
+                                   const double* mu) {
+    if (!s || count < 1 || m1 < 1 || m1 > 8 || m2 < 1 || m2 > 8 || !state_offsets || !row_ptr ||
+        !col || !prob || !reward || !mu) {
+        set_last_error("set_game_batch: invalid argument");
+        return GS_EINVAL;
+    }
+    return guarded([&]() -> gs_status {
+        auto P = build_game_problem(s, count, m1, m2, state_offsets, row_ptr, col, prob, reward, mu);
+        s->prob = std::move(P);
+        reset_initial(s);
+        return GS_OK;
+    });
+}
+
+gs_status gamesolve_get_batch_stats(const gs_solver* s, int32_t* stats, double* res) {
+    if (!s) return GS_EINVAL;
+    if (!s->prob || s->prob->kind != 2) {
+        set_last_error("get_batch_stats: no game batch set");
+        return GS_ESTATE;
+    }
+    const GameProblem& G = *s->prob->game;
+    if (G.stats_h.empty()) {
+        set_last_error("get_batch_stats: not solved yet");
+        return GS_ESTATE;
+    }
+    if (stats) std::memcpy(stats, G.stats_h.data(), sizeof(int32_t) * 4 * G.count);
+    if (res) std::memcpy(res, G.res_h.data(), sizeof(double) * G.count);
+    return GS_OK;
 }
 
 gs_status gamesolve_set_isaacs_grid(gs_solver* s, int32_t side, int32_t variant, uint64_t seed,
@@ -141,6 +179,10 @@ gs_status gamesolve_set_initial(gs_solver* s, const double* v0, const uint8_t* a
     if (!s->prob) {
         set_last_error("set_initial: no problem set");
         return GS_ESTATE;
+    }
+    if (s->prob->kind != 1) {
+        set_last_error("set_initial: warm starts are for Isaacs grids in this build");
+        return GS_EINVAL;
     }
     return guarded([&]() -> gs_status {
         IsaacsGrid& g = *s->prob->grids.back();
@@ -178,19 +220,22 @@ gs_status gamesolve_solve(gs_solver* s, gs_solve_stats* stats) {
         set_last_error("solve: no problem set");
         return GS_ESTATE;
     }
+    if (s->prob->kind == 2) return guarded([&]() { return run_games(s, stats); });
     return guarded([&]() { return run_solve(s, stats); });
 }
 
 gs_status gamesolve_get_value(const gs_solver* s, double* v_out, int64_t n) {
     if (!s || !v_out) return GS_EINVAL;
     if (!s->prob) return GS_ESTATE;
-    const IsaacsGrid& g = *s->prob->grids.back();
-    if (n != (int64_t)g.n) {
-        set_last_error("get_value: n = %lld, problem has %zu states", (long long)n, g.n);
+    const bool games = s->prob->kind == 2;
+    const size_t total = games ? (size_t)s->prob->game->n_total : s->prob->grids.back()->n;
+    const double* src = games ? s->prob->game->v : s->prob->grids.back()->v;
+    if (n != (int64_t)total) {
+        set_last_error("get_value: n = %lld, problem has %zu states", (long long)n, total);
         return GS_EINVAL;
     }
     return guarded([&]() -> gs_status {
-        GS_CUDA(cudaMemcpyAsync(v_out, g.v, g.n * sizeof(double), cudaMemcpyDefault, s->st));
+        GS_CUDA(cudaMemcpyAsync(v_out, src, total * sizeof(double), cudaMemcpyDefault, s->st));
         GS_CUDA(cudaStreamSynchronize(s->st));
         return GS_OK;
     });
@@ -200,6 +245,16 @@ gs_status gamesolve_get_policy(const gs_solver* s, uint8_t* alpha, uint8_t* beta
     if (!s) return GS_EINVAL;
     if (!s->prob) return GS_ESTATE;
     gs_solver* sm = const_cast<gs_solver*>(s);
+    if (s->prob->kind == 2) {
+        const GameProblem& G = *s->prob->game;
+        return guarded([&]() -> gs_status {
+            if (alpha) GS_CUDA(cudaMemcpyAsync(alpha, G.alpha, G.n_total, cudaMemcpyDefault, s->st));
+            if (beta)
+                GS_CUDA(cudaMemcpyAsync(beta, G.beta, G.n_total * G.m1, cudaMemcpyDefault, s->st));
+            GS_CUDA(cudaStreamSynchronize(s->st));
+            return GS_OK;
+        });
+    }
     return guarded([&]() -> gs_status {
         const IsaacsGrid& g = *s->prob->grids.back();
         if (alpha) GS_CUDA(cudaMemcpyAsync(alpha, g.alpha, g.n, cudaMemcpyDefault, s->st));
@@ -213,6 +268,10 @@ gs_status gamesolve_improve(gs_solver* s, const double* v, uint8_t* alpha_out, u
                             double* fv_out) {
     if (!s || !v) return GS_EINVAL;
     if (!s->prob) return GS_ESTATE;
+    if (s->prob->kind != 1) {
+        set_last_error("improve: available for Isaacs grids in this build");
+        return GS_EINVAL;
+    }
     return guarded([&]() { return run_improve(s, v, alpha_out, beta_out, fv_out); });
 }
 
@@ -220,6 +279,10 @@ gs_status gamesolve_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8
                                  const double* w0, double* w_out, gs_solve_stats* stats) {
     if (!s || !alpha || !beta || !w_out) return GS_EINVAL;
     if (!s->prob) return GS_ESTATE;
+    if (s->prob->kind != 1) {
+        set_last_error("policy_solve: available for Isaacs grids in this build");
+        return GS_EINVAL;
+    }
     return guarded([&]() { return run_policy_solve(s, alpha, beta, w0, w_out, stats); });
 }
 

@@ -1,0 +1,443 @@
+// Finite games given by explicit transition tables (Sec. 2): validation and
+// set-up of the CSR tables, and a persistent kernel in which each thread block
+// takes games from a queue and runs the whole policy iteration on one game
+// (Algorithm 2 with Algorithm 1 inside) -- improvement, assembly, multigrid
+// policy evaluation, stopping tests -- with the game's vectors in shared memory.
+//
+// Multigrid for the policy-fixed system (I - mu M) w = r of a general game: the
+// smoother is Jacobi relaxation; the coarse space is spanned by the constant
+// vector, whose Galerkin operator is 1^T A 1 = sum of A's row sums.  For a
+// stochastic M the constant vector is the slow mode of I - mu M (eigenvalue
+// 1 - mu), which relaxation cannot remove and the coarse correction removes
+// exactly; the other modes contract at the rate of M's second eigenvalue.
+#include <cfloat>
+
+#include "games.cuh"
+
+namespace gs {
+
+namespace {
+
+constexpr int kThreads = 512;
+
+// ------------------------------------------------------------------ validation
+__global__ void k_game_validate(GameTables T, int count, const int64_t* __restrict__ st_off,
+                                int* __restrict__ bad) {
+    const int64_t R = (int64_t)T.m1 * T.m2;
+    const int64_t rows = st_off[count] * R;
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        // game of this row: binary search over the state offsets
+        const int64_t x = row / R;
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (st_off[mid] <= x) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t n = st_off[lo + 1] - st_off[lo];
+        const int64_t k0 = T.row_ptr[row], k1 = T.row_ptr[row + 1];
+        int err = 0;
+        if (k1 < k0) err |= 1;
+        double sum = 0.0;
+        for (int64_t k = k0; k < k1 && !(err & 1); ++k) {
+            const int32_t c = T.col[k];
+            const double p = T.prob[k];
+            if (c < 0 || c >= n) err |= 2;
+            if (!(p >= 0.0) || !(p <= 1.0)) err |= 4;
+            sum += p;
+        }
+        if (sum > 1.0 + 1e-12) err |= 8;
+        if (!(fabs(T.rew[row]) <= DBL_MAX)) err |= 16;
+        if (err) atomicOr(bad, err);
+    }
+}
+
+// Per row: leakage 1 - mu sum_k p_k (float64) and the float32 copy of p.
+__global__ void k_game_prepare(GameTables T, int count, const int64_t* __restrict__ st_off,
+                               const double* __restrict__ mu, double* __restrict__ leak,
+                               float* __restrict__ prob32) {
+    const int64_t R = (int64_t)T.m1 * T.m2;
+    const int64_t rows = st_off[count] * R;
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = row / R;
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (st_off[mid] <= x) lo = mid;
+            else hi = mid - 1;
+        }
+        double sum = 0.0;
+        for (int64_t k = T.row_ptr[row]; k < T.row_ptr[row + 1]; ++k) {
+            sum += T.prob[k];
+            prob32[k] = (float)T.prob[k];
+        }
+        leak[row] = 1.0 - mu[lo] * sum;
+    }
+}
+
+// ------------------------------------------------------------------ block helpers
+__device__ __forceinline__ double warp_maxd(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide reductions; every thread gets the result.  `red` is shared scratch.
+__device__ double block_max(double v, double* red) {
+    v = warp_maxd(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    return m;
+}
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];   // fixed order
+    return s;
+}
+
+// ------------------------------------------------------------------ one game
+struct Game {
+    GameTables T;
+    int64_t x0, n, row0;   // first state, states, first row
+    double mu;
+    int R;                 // m1 * m2
+};
+
+// F(v; x, a, b) = mu sum_k p_k v(col_k) + r(x, a, b)  (Eq. (ILPI)); v indexed locally.
+__device__ __forceinline__ double row_value(const Game& G, int64_t row, const double* v) {
+    double s = 0.0;
+    for (int64_t k = G.T.row_ptr[row]; k < G.T.row_ptr[row + 1]; ++k)
+        s += G.T.prob[k] * v[G.T.col[k]];
+    return G.mu * s + G.T.rew[row];
+}
+
+// Policy improvement at local state i (modes as for the Isaacs grid).
+// Returns the number of changed policy entries; *res gets |F(v) - v| (outer).
+__device__ int improve_state(const Game& G, const BatchOut& O, int mode, int64_t i, double tau,
+                             const double* v, double* res) {
+    const int m1 = G.T.m1, m2 = G.T.m2;
+    const int64_t x = G.x0 + i;
+    const int64_t rb = G.row0 + i * G.R;
+    const int acur = O.alpha[x];
+    double Fa[8];
+    int changed = 0;
+    for (int a = 0; a < m1; ++a) {
+        if (mode == 1 && a != acur) continue;
+        uint8_t& bref = O.beta[x * m1 + a];
+        const int bcur = bref;
+        double best = 0.0, fcur = 0.0;
+        int first = 0;
+        for (int b = 0; b < m2; ++b) {
+            const double F = row_value(G, rb + a * m2 + b, v);
+            if (b == 0 || F < best) { best = F; first = b; }
+            if (b == bcur) fcur = F;
+        }
+        const int bnew = (fcur - best > tau) ? first : bcur;
+        if (bnew != bcur) {
+            bref = (uint8_t)bnew;
+            if (mode == 1) changed = 1;
+        }
+        Fa[a] = best;
+    }
+    int anew = acur;
+    if (mode == 0) {
+        double fmax_ = Fa[0];
+        int first = 0;
+        for (int a = 1; a < m1; ++a)
+            if (Fa[a] > fmax_) { fmax_ = Fa[a]; first = a; }
+        anew = (fmax_ - Fa[acur] > tau) ? first : acur;
+        changed = anew != acur;
+        *res = fabs(fmax_ - v[i]);
+        O.alpha[x] = (uint8_t)anew;
+    }
+    const int64_t row = rb + anew * m2 + O.beta[x * m1 + anew];
+    O.sel[x] = row;
+    O.rhs[x] = G.T.rew[row];
+    return changed;
+}
+
+// (A e)_i and the diagonal of A = I - mu M for the selected row, leakage form:
+// (A e)_i = s_i e_i + mu sum_k p_k (e_i - e_col), s_i = 1 - mu sum_k p_k.
+template <typename T>
+__device__ __forceinline__ void apply_row(const Game& G, const BatchOut& O, int64_t i, const T* e,
+                                          T* Ae, T* diag) {
+    const int64_t row = O.sel[G.x0 + i];
+    const T ei = e[i];
+    const T mu = (T)G.mu;
+    T acc = (T)G.T.leak[row] * ei, off = 0;
+    for (int64_t k = G.T.row_ptr[row]; k < G.T.row_ptr[row + 1]; ++k) {
+        const int32_t c = G.T.col[k];
+        const T p = sizeof(T) == 4 ? (T)G.T.prob32[k] : (T)G.T.prob[k];
+        acc += mu * p * (ei - e[c]);
+        if (c != i) off += mu * p;
+    }
+    *Ae = acc;
+    *diag = (T)G.T.leak[row] + off;
+}
+
+// Diagonal of A for the selected row: s_i + mu sum_{k: col_k != i} p_k.
+template <typename T>
+__device__ __forceinline__ T diag_row(const Game& G, const BatchOut& O, int64_t i) {
+    const int64_t row = O.sel[G.x0 + i];
+    T off = 0;
+    for (int64_t k = G.T.row_ptr[row]; k < G.T.row_ptr[row + 1]; ++k)
+        if (G.T.col[k] != i) off += (T)G.mu * (sizeof(T) == 4 ? (T)G.T.prob32[k] : (T)G.T.prob[k]);
+    return (T)G.T.leak[row] + off;
+}
+
+template <typename T>
+struct Scratch {
+    T* r;   // right-hand side of the correction equation (the float64 residual, rounded)
+    T* e;   // correction
+    T* t;   // Jacobi work vector
+    double* red_d;
+    T* red_t;
+    int* red_i;
+};
+
+// float64 residual rhs - (v - mu M v) -> S.r; returns |r|_inf, sets *vmax.
+template <typename T>
+__device__ double check(const Game& G, const BatchOut& O, const double* v, const Scratch<T>& S,
+                        double* vmax) {
+    double rm = 0.0, vm = 0.0;
+    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
+        const int64_t row = O.sel[G.x0 + i];
+        double s = 0.0;
+        for (int64_t k = G.T.row_ptr[row]; k < G.T.row_ptr[row + 1]; ++k)
+            s += G.T.prob[k] * v[G.T.col[k]];
+        const double r = O.rhs[G.x0 + i] - (v[i] - G.mu * s);
+        S.r[i] = (T)r;
+        rm = fmax(rm, fabs(r));
+        vm = fmax(vm, fabs(v[i]));
+    }
+    *vmax = block_max(vm, S.red_d);
+    return block_max(rm, S.red_d);
+}
+
+// One two-level cycle on A e = r from e = 0, then v += e.
+template <typename T>
+__device__ void cycle(const Game& G, const BatchOut& O, double* v, Scratch<T>& S, T asum,
+                      int nu1, int nu2) {
+    // pre-relaxation (Jacobi; the first sweep from zero)
+    for (int k = 0; k < nu1; ++k) {
+        for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
+            T Ae, d;
+            if (k == 0) {
+                S.t[i] = S.r[i] / diag_row<T>(G, O, i);
+            } else {
+                apply_row<T>(G, O, i, S.e, &Ae, &d);
+                S.t[i] = S.e[i] + (S.r[i] - Ae) / d;
+            }
+        }
+        __syncthreads();
+        T* sw = S.e; S.e = S.t; S.t = sw;
+    }
+    if (nu1 == 0) {
+        for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) S.e[i] = 0;
+        __syncthreads();
+    }
+    // coarse correction on the constant vector: e += (1^T (r - A e)) / (1^T A 1)
+    T part = 0;
+    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
+        T Ae, d;
+        apply_row<T>(G, O, i, S.e, &Ae, &d);
+        part += S.r[i] - Ae;
+    }
+    const T c = asum != T(0) ? block_sum(part, S.red_t) / asum : T(0);
+    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) S.e[i] += c;
+    __syncthreads();
+    // post-relaxation
+    for (int k = 0; k < nu2; ++k) {
+        for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
+            T Ae, d;
+            apply_row<T>(G, O, i, S.e, &Ae, &d);
+            S.t[i] = S.e[i] + (S.r[i] - Ae) / d;
+        }
+        __syncthreads();
+        T* sw = S.e; S.e = S.t; S.t = sw;
+    }
+    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) v[i] += (double)S.e[i];
+    __syncthreads();
+}
+
+// Policy evaluation: cycles until the float64 floor / tolerance (exact) or a
+// residual drop by rel_tol (inexact).  Returns true when exact.
+template <typename T>
+__device__ bool evaluate(const Game& G, const BatchOut& O, const BatchOpts& P, double* v,
+                         Scratch<T>& S, double rel_tol, int* cycles) {
+    double part = 0.0;
+    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) part += G.T.leak[O.sel[G.x0 + i]];
+    const T asum = (T)block_sum(part, S.red_d);
+    double vm;
+    double res = check(G, O, v, S, &vm);
+    const double res0 = res;
+    double prev = res;
+    int slow = 0;
+    for (int cyc = 0;; ++cyc) {
+        if (res <= P.lin_tol * fmax(vm, 1e-300) || res == 0.0) return true;
+        if (cyc > 0) {
+            slow = res > 0.5 * prev ? slow + 1 : 0;
+            if (slow >= 2 && res < 1e-12 * fmax(vm, 1e-300)) return true;
+            if (res <= rel_tol * res0) return false;
+            prev = fmin(prev, res);
+        }
+        if (cyc >= P.max_cycles) return true;
+        cycle<T>(G, O, v, S, asum, P.nu1, P.nu2);
+        ++*cycles;
+        res = check(G, O, v, S, &vm);
+    }
+}
+
+template <typename T>
+__device__ int improve_all(const Game& G, const BatchOut& O, int mode, const double* v,
+                           Scratch<T>& S, double* res_out) {
+    double vm = 0.0;
+    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) vm = fmax(vm, fabs(v[i]));
+    vm = block_max(vm, S.red_d);
+    const double tau = 1e-13 * fmax(1.0, vm);
+    int changed = 0;
+    double res = 0.0;
+    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
+        double r = 0.0;
+        changed += improve_state(G, O, mode, i, tau, v, &r);
+        res = fmax(res, r);
+    }
+    if (res_out) *res_out = block_max(res, S.red_d);
+    return block_sum(changed, S.red_i);
+}
+
+// Algorithm 2 with Algorithm 1 inside for game g (see the Isaacs driver for
+// the stopping rules and the exact confirmation of inexact evaluations).
+template <typename T>
+__device__ void solve_game(const BatchArgs& B, int g, char* smem) {
+    Game G;
+    G.T = B.T;
+    G.x0 = B.st_off[g];
+    G.n = B.st_off[g + 1] - G.x0;
+    G.R = B.T.m1 * B.T.m2;
+    G.row0 = G.x0 * G.R;
+    G.mu = B.mu[g];
+    const BatchOut& O = B.out;
+    const BatchOpts& P = B.opt;
+    __shared__ double red_d[32];
+    __shared__ T red_t[32];
+    __shared__ int red_i[32];
+    Scratch<T> S;
+    S.r = (T*)smem;
+    S.e = S.r + B.max_n;
+    S.t = S.e + B.max_n;
+    S.red_d = red_d;
+    S.red_t = red_t;
+    S.red_i = red_i;
+    double* v = O.v + G.x0;
+    const int a0 = P.default_alpha;
+    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
+        v[i] = 0.0;
+        O.alpha[G.x0 + i] = (uint8_t)(a0 < G.T.m1 ? a0 : 0);
+        for (int a = 0; a < G.T.m1; ++a) O.beta[(G.x0 + i) * G.T.m1 + a] = 0;
+    }
+    __syncthreads();
+    improve_all(G, O, 2, v, S, (double*)nullptr);   // MIN's first reply, assembly
+    __syncthreads();
+    int outer = 0, systems = 0, cycles = 0, converged = 0;
+    double res = 0.0;
+    while (true) {
+        for (int j = 0; j < P.max_inner; ++j) {
+            const bool exact = evaluate<T>(G, O, P, v, S, P.pi_rtol, &cycles);
+            ++systems;
+            __syncthreads();
+            if (improve_all(G, O, 1, v, S, (double*)nullptr) != 0) continue;
+            __syncthreads();
+            if (!exact) {
+                evaluate<T>(G, O, P, v, S, 0.0, &cycles);
+                __syncthreads();
+                if (improve_all(G, O, 1, v, S, (double*)nullptr) != 0) continue;
+                __syncthreads();
+            }
+            break;
+        }
+        ++outer;
+        __syncthreads();
+        const int ach = improve_all(G, O, 0, v, S, &res);
+        __syncthreads();
+        if (res <= P.eps || ach == 0) {
+            converged = 1;
+            break;
+        }
+        if (outer >= P.max_outer) break;
+    }
+    if (threadIdx.x == 0) {
+        O.gstats[4 * g + 0] = outer;
+        O.gstats[4 * g + 1] = systems;
+        O.gstats[4 * g + 2] = cycles;
+        O.gstats[4 * g + 3] = converged;
+        O.gres[g] = res;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_games_pi(const __grid_constant__ BatchArgs B) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int s_game;
+    while (true) {
+        if (threadIdx.x == 0) s_game = atomicAdd(B.queue, 1);
+        __syncthreads();
+        const int g = s_game;
+        __syncthreads();
+        if (g >= B.count) break;
+        solve_game<T>(B, g, smem);
+    }
+}
+
+}  // namespace
+
+void launch_game_validate(const GameTables& T, int count, const int64_t* st_off, int64_t rows,
+                          int* bad, cudaStream_t st) {
+    const unsigned g = (unsigned)std::min<int64_t>((rows + 255) / 256, 152 * 32);
+    k_game_validate<<<std::max(1u, g), 256, 0, st>>>(T, count, st_off, bad);
+    GS_CHECK_LAUNCH();
+}
+
+void launch_game_prepare(const GameTables& T, int count, const int64_t* st_off, int64_t rows,
+                         const double* mu, double* leak, float* prob32, cudaStream_t st) {
+    const unsigned g = (unsigned)std::min<int64_t>((rows + 255) / 256, 152 * 32);
+    k_game_prepare<<<std::max(1u, g), 256, 0, st>>>(T, count, st_off, mu, leak, prob32);
+    GS_CHECK_LAUNCH();
+}
+
+size_t games_smem_bytes(int max_n, bool mixed) {
+    return (size_t)3 * max_n * (mixed ? sizeof(float) : sizeof(double));
+}
+
+void launch_games_pi(const BatchArgs& B, bool mixed, cudaStream_t st) {
+    const size_t smem = games_smem_bytes(B.max_n, mixed);
+    const void* fn = mixed ? (const void*)k_games_pi<float> : (const void*)k_games_pi<double>;
+    GS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    GS_CUDA(cudaGetDevice(&dev));
+    GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
+    const int blocks = std::max(1, std::min(B.count, std::max(1, per_sm) * sms));
+    void* args[] = {(void*)&B};
+    GS_CUDA(cudaLaunchKernel(fn, dim3(blocks), dim3(kThreads), args, smem, st));
+    note_launches(1);
+}
+
+}  // namespace gs

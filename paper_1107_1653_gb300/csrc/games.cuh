@@ -1,0 +1,59 @@
+// Finite games given by CSR transition tables: device-side argument blocks.
+#pragma once
+
+#include "common.cuh"
+
+namespace gs {
+
+// Concatenated CSR tables of one or more games.  Rows of game g are
+// (x * m1 + a) * m2 + b for its states x, numbered after the earlier games'
+// rows; columns are state indices within the game.
+struct GameTables {
+    int m1, m2;
+    const int64_t* row_ptr;   // total rows + 1 (global nnz offsets)
+    const int32_t* col;
+    const double* prob;
+    const float* prob32;      // float32 copy (relaxation)
+    const double* rew;        // per row
+    const double* leak;       // per row: 1 - mu sum_k p_k
+};
+
+struct BatchOut {
+    double* v;        // per state (global numbering): value, also the iterate
+    uint8_t* alpha;   // per state
+    uint8_t* beta;    // per state x m1
+    int64_t* sel;     // per state: the selected row of the policy-fixed system
+    double* rhs;      // per state: its reward r^{alpha beta}
+    int* gstats;      // per game: outer, systems, cycles, converged
+    double* gres;     // per game: |F(v) - v|_inf at the end
+};
+
+struct BatchOpts {
+    int max_outer, max_inner, max_cycles, nu1, nu2, default_alpha;
+    double eps, lin_tol, pi_rtol;
+};
+
+struct BatchArgs {
+    GameTables T;
+    BatchOut out;
+    BatchOpts opt;
+    int count;              // games
+    int max_n;              // largest game (sizes the shared-memory vectors)
+    const int64_t* st_off;  // count + 1 state offsets
+    const double* mu;       // per game
+    int* queue;             // work counter (zeroed before the launch)
+};
+
+// Largest game the one-block-per-game kernel takes (its three correction
+// vectors live in shared memory).
+constexpr int kGameMaxStatesMixed = 16384;
+constexpr int kGameMaxStatesFP64 = 8192;
+
+void launch_game_validate(const GameTables& T, int count, const int64_t* st_off, int64_t rows,
+                          int* bad, cudaStream_t st);
+void launch_game_prepare(const GameTables& T, int count, const int64_t* st_off, int64_t rows,
+                         const double* mu, double* leak, float* prob32, cudaStream_t st);
+size_t games_smem_bytes(int max_n, bool mixed);
+void launch_games_pi(const BatchArgs& B, bool mixed, cudaStream_t st);
+
+}  // namespace gs

@@ -7,6 +7,7 @@
 
 #include "kernels.cuh"
 #include "mgsolve.cuh"
+#include "games.cuh"
 
 namespace gs {
 
@@ -58,10 +59,28 @@ struct IsaacsGrid {
     long long stale_rows = 0;  // rows whose code changed since the hierarchy was built
 };
 
+// One or more finite games (CSR tables) on the device.
+struct GameProblem {
+    int count = 0, m1 = 0, m2 = 0, max_n = 0;
+    int64_t n_total = 0, rows = 0, nnz = 0;
+    std::vector<int64_t> st_off_h;
+    int64_t *st_off = nullptr, *row_ptr = nullptr, *sel = nullptr;
+    int32_t* col = nullptr;
+    double *prob = nullptr, *rew = nullptr, *leak = nullptr, *mu = nullptr, *v = nullptr,
+           *rhs = nullptr, *gres = nullptr;
+    float* prob32 = nullptr;
+    uint8_t *alpha = nullptr, *beta = nullptr;
+    int *gstats = nullptr, *queue = nullptr;
+    std::vector<int> stats_h;
+    std::vector<double> res_h;
+    GameTables tables() const { return {m1, m2, row_ptr, col, prob, prob32, rew, leak}; }
+};
+
 struct Problem {
     explicit Problem(size_t budget, size_t held) : arena(budget, held) {}
     Arena arena;
-    int kind = 0;                                // 1 Isaacs
+    int kind = 0;                                // 1 Isaacs, 2 finite games
+    std::unique_ptr<GameProblem> game;
     std::vector<std::unique_ptr<IsaacsGrid>> grids;   // FAMGpi levels, coarse to fine
     double* xi = nullptr;                        // finest-grid noise (when given)
 };
@@ -111,6 +130,11 @@ IsaacsConsts make_isaacs_consts(int side, int variant, int mu_mode);
 std::unique_ptr<Problem> build_isaacs_problem(gs_solver* s, int side, int variant, uint64_t seed,
                                               const double* xi);
 void reset_initial(gs_solver* s);
+std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int m2,
+                                            const int64_t* state_offsets, const int64_t* row_ptr,
+                                            const int32_t* col, const double* prob,
+                                            const double* reward, const double* mu);
+gs_status run_games(gs_solver* s, gs_solve_stats* stats);
 gs_status run_solve(gs_solver* s, gs_solve_stats* stats);
 gs_status run_improve(gs_solver* s, const double* v, uint8_t* alpha_out, uint8_t* beta_out,
                       double* fv_out);
