@@ -80,6 +80,9 @@ typedef struct {
     double  setup_reuse;   /* keep the previous Galerkin hierarchy when at most this fraction
                               of the rows of the policy-fixed system changed (0 = always
                               rebuild); the float64 residual test keeps the solution exact */
+    int32_t grid_blocks;   /* cap on the thread blocks of one grid-wide launch (0 = the whole
+                              GPU); lets solvers on different streams share the GPU */
+    int32_t reserved1;
 } gs_options;
 
 /* Statistics of the last gamesolve_solve (the columns of the paper's tables, Sec. 6). */
@@ -98,7 +101,7 @@ typedef struct {
 /* Fills *opt with the defaults: FP64, eps 0, max_outer 1000, max_inner 1000,
  * V(1,1), max_cycles 200, lin_tol 1e-15, coarse_max 9, flat, fmg_side 31,
  * fmg_c 0.1, literal mu, tail_side 31, no memory budget, default stream,
- * pi_rtol 1e-3, setup_reuse 1e-3. */
+ * pi_rtol 1e-3, setup_reuse 1e-3, grid_blocks 0. */
 void gamesolve_default_options(gs_options* opt);
 
 /* Creates a solver on the current CUDA device.  opt may be NULL (defaults).
@@ -111,9 +114,10 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt);
  * for k in [row_ptr[row], row_ptr[row+1]); reward has n*m1*m2 entries r(x,a,b).
  * Rows may be substochastic (the missing mass leaves the game), so a row
  * without successors is a "stop" action.
- * The game is solved by the same one-block-per-game policy iteration as a
- * batch (at most 16384 states in mixed precision, 8192 in float64); warm
- * starts (set_initial), improve and policy_solve are for Isaacs grids.
+ * A game of at least 4096 states runs on the whole GPU (one cooperative
+ * launch: policy iteration on the device with bounded grid barriers); a
+ * smaller one runs in one thread block.  Warm starts (set_initial), improve
+ * and policy_solve are for Isaacs grids.
  * Errors (GS_EINVAL, solver unchanged): n < 1 or too large, m1 or m2 outside
  * [1, 8], row_ptr not non-decreasing from 0, a column out of range, a
  * probability outside [0, 1], a row sum above 1 + 1e-12, mu outside (0, 1). */
@@ -128,8 +132,9 @@ gs_status gamesolve_set_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2,
  * in order (game g's row (x*m1 + a)*m2 + b follows all rows of games < g);
  * row_ptr has (total states)*m1*m2 + 1 entries starting at 0; col[k] is a
  * state index within the row's own game.  Values, policies and statistics are
- * read back concatenated in the same state order.  Each game must have at most
- * 16384 states (mixed precision) or 8192 (float64).
+ * read back concatenated in the same state order.  In a batch of two or more
+ * games each game must have at most 16384 states (mixed precision) or 8192
+ * (float64).
  * Errors: as gamesolve_set_game, per row and per game. */
 gs_status gamesolve_set_game_batch(gs_solver* s, int32_t count, int32_t m1, int32_t m2,
                                    const int64_t* state_offsets, const int64_t* row_ptr,

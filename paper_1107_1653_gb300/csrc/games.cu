@@ -13,6 +13,7 @@
 #include <cfloat>
 
 #include "games.cuh"
+#include "gridsync.cuh"
 
 namespace gs {
 
@@ -201,95 +202,142 @@ __device__ __forceinline__ T diag_row(const Game& G, const BatchOut& O, int64_t 
     return (T)G.T.leak[row] + off;
 }
 
+// Execution context of one game's policy iteration: which threads share the
+// work, how they synchronise, and where the correction vectors live.  The
+// block context runs a game inside one thread block (vectors in shared
+// memory); the grid context spreads one game over a cooperative grid (vectors
+// in global memory, bounded grid barriers, reductions through per-block
+// partials combined in a fixed order, so the result does not depend on timing).
 template <typename T>
-struct Scratch {
-    T* r;   // right-hand side of the correction equation (the float64 residual, rounded)
-    T* e;   // correction
-    T* t;   // Jacobi work vector
+struct BlockCtx {
+    T *r, *e, *t;      // correction right-hand side, correction, Jacobi work vector
     double* red_d;
-    T* red_t;
     int* red_i;
+    __device__ size_t begin() const { return threadIdx.x; }
+    __device__ size_t stride() const { return blockDim.x; }
+    __device__ bool sync() { __syncthreads(); return true; }
+    __device__ double max(double v) { return block_max(v, red_d); }
+    __device__ double sum(double v) { return block_sum(v, red_d); }
+    __device__ int sumi(int v) { return block_sum(v, red_i); }
+    __device__ bool failed() const { return false; }
+    __device__ bool leader() const { return threadIdx.x == 0; }
 };
 
-// float64 residual rhs - (v - mu M v) -> S.r; returns |r|_inf, sets *vmax.
 template <typename T>
-__device__ double check(const Game& G, const BatchOut& O, const double* v, const Scratch<T>& S,
-                        double* vmax) {
+struct GridCtx {
+    T *r, *e, *t;
+    double* part;      // [2][gridDim.x] per-block partials (alternating)
+    GridBarrier* bar;
+    double* red_d;
+    int flip;
+    bool bad;
+    __device__ size_t begin() const { return (size_t)blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ size_t stride() const { return (size_t)gridDim.x * blockDim.x; }
+    __device__ bool sync() {
+        if (!bad) bad = !GridSync{bar, gridDim.x}.sync();
+        return !bad;
+    }
+    __device__ double combine(double v, bool is_max) {
+        v = is_max ? block_max(v, red_d) : block_sum(v, red_d);
+        double* P = part + (size_t)flip * gridDim.x;
+        flip ^= 1;
+        if (threadIdx.x == 0) P[blockIdx.x] = v;
+        if (!sync()) return 0.0;
+        double acc = 0.0;
+        for (unsigned k = threadIdx.x & 31; k < gridDim.x; k += 32) {
+            const double p = __ldcg(P + k);
+            acc = is_max ? fmax(acc, p) : acc + p;
+        }
+        return is_max ? warp_maxd(acc) : warp_sum(acc);
+    }
+    __device__ double max(double v) { return combine(v, true); }
+    __device__ double sum(double v) { return combine(v, false); }
+    __device__ int sumi(int v) { return (int)combine((double)v, false); }
+    __device__ bool failed() const { return bad; }
+    __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
+};
+
+// float64 residual rhs - (v - mu M v) -> C.r; returns |r|_inf, sets *vmax.
+template <typename T, class Ctx>
+__device__ double check(const Game& G, const BatchOut& O, const double* v, Ctx& C, double* vmax) {
     double rm = 0.0, vm = 0.0;
-    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
         const int64_t row = O.sel[G.x0 + i];
         double s = 0.0;
         for (int64_t k = G.T.row_ptr[row]; k < G.T.row_ptr[row + 1]; ++k)
             s += G.T.prob[k] * v[G.T.col[k]];
         const double r = O.rhs[G.x0 + i] - (v[i] - G.mu * s);
-        S.r[i] = (T)r;
+        C.r[i] = (T)r;
         rm = fmax(rm, fabs(r));
         vm = fmax(vm, fabs(v[i]));
     }
-    *vmax = block_max(vm, S.red_d);
-    return block_max(rm, S.red_d);
+    *vmax = C.max(vm);
+    return C.max(rm);
 }
 
-// One two-level cycle on A e = r from e = 0, then v += e.
-template <typename T>
-__device__ void cycle(const Game& G, const BatchOut& O, double* v, Scratch<T>& S, T asum,
-                      int nu1, int nu2) {
+// One two-level cycle on A e = r from e = 0, then v += e.  Returns false if a
+// grid barrier gave up.
+template <typename T, class Ctx>
+__device__ bool cycle(const Game& G, const BatchOut& O, double* v, Ctx& C, T asum, int nu1, int nu2) {
     // pre-relaxation (Jacobi; the first sweep from zero)
     for (int k = 0; k < nu1; ++k) {
-        for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
-            T Ae, d;
+        for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
             if (k == 0) {
-                S.t[i] = S.r[i] / diag_row<T>(G, O, i);
+                C.t[i] = C.r[i] / diag_row<T>(G, O, i);
             } else {
-                apply_row<T>(G, O, i, S.e, &Ae, &d);
-                S.t[i] = S.e[i] + (S.r[i] - Ae) / d;
+                T Ae, d;
+                apply_row<T>(G, O, i, C.e, &Ae, &d);
+                C.t[i] = C.e[i] + (C.r[i] - Ae) / d;
             }
         }
-        __syncthreads();
-        T* sw = S.e; S.e = S.t; S.t = sw;
+        if (!C.sync()) return false;
+        T* sw = C.e; C.e = C.t; C.t = sw;
     }
     if (nu1 == 0) {
-        for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) S.e[i] = 0;
-        __syncthreads();
+        for (int64_t i = C.begin(); i < G.n; i += C.stride()) C.e[i] = 0;
+        if (!C.sync()) return false;
     }
     // coarse correction on the constant vector: e += (1^T (r - A e)) / (1^T A 1)
-    T part = 0;
-    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
+    double part = 0.0;
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
         T Ae, d;
-        apply_row<T>(G, O, i, S.e, &Ae, &d);
-        part += S.r[i] - Ae;
+        apply_row<T>(G, O, i, C.e, &Ae, &d);
+        part += (double)(C.r[i] - Ae);
     }
-    const T c = asum != T(0) ? block_sum(part, S.red_t) / asum : T(0);
-    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) S.e[i] += c;
-    __syncthreads();
+    const double tot = C.sum(part);
+    if (C.failed()) return false;
+    const T c = asum != T(0) ? (T)(tot / (double)asum) : T(0);
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) C.e[i] += c;
+    if (!C.sync()) return false;
     // post-relaxation
     for (int k = 0; k < nu2; ++k) {
-        for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
+        for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
             T Ae, d;
-            apply_row<T>(G, O, i, S.e, &Ae, &d);
-            S.t[i] = S.e[i] + (S.r[i] - Ae) / d;
+            apply_row<T>(G, O, i, C.e, &Ae, &d);
+            C.t[i] = C.e[i] + (C.r[i] - Ae) / d;
         }
-        __syncthreads();
-        T* sw = S.e; S.e = S.t; S.t = sw;
+        if (!C.sync()) return false;
+        T* sw = C.e; C.e = C.t; C.t = sw;
     }
-    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) v[i] += (double)S.e[i];
-    __syncthreads();
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) v[i] += (double)C.e[i];
+    return C.sync();
 }
 
 // Policy evaluation: cycles until the float64 floor / tolerance (exact) or a
 // residual drop by rel_tol (inexact).  Returns true when exact.
-template <typename T>
-__device__ bool evaluate(const Game& G, const BatchOut& O, const BatchOpts& P, double* v,
-                         Scratch<T>& S, double rel_tol, int* cycles) {
+template <typename T, class Ctx>
+__device__ bool evaluate(const Game& G, const BatchOut& O, const BatchOpts& P, double* v, Ctx& C,
+                         double rel_tol, int* cycles) {
     double part = 0.0;
-    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) part += G.T.leak[O.sel[G.x0 + i]];
-    const T asum = (T)block_sum(part, S.red_d);
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) part += G.T.leak[O.sel[G.x0 + i]];
+    const T asum = (T)C.sum(part);
     double vm;
-    double res = check(G, O, v, S, &vm);
+    double res = check<T>(G, O, v, C, &vm);
     const double res0 = res;
     double prev = res;
     int slow = 0;
     for (int cyc = 0;; ++cyc) {
+        if (C.failed()) return true;
         if (res <= P.lin_tol * fmax(vm, 1e-300) || res == 0.0) return true;
         if (cyc > 0) {
             slow = res > 0.5 * prev ? slow + 1 : 0;
@@ -298,34 +346,34 @@ __device__ bool evaluate(const Game& G, const BatchOut& O, const BatchOpts& P, d
             prev = fmin(prev, res);
         }
         if (cyc >= P.max_cycles) return true;
-        cycle<T>(G, O, v, S, asum, P.nu1, P.nu2);
+        if (!cycle<T>(G, O, v, C, asum, P.nu1, P.nu2)) return true;
         ++*cycles;
-        res = check(G, O, v, S, &vm);
+        res = check<T>(G, O, v, C, &vm);
     }
 }
 
-template <typename T>
-__device__ int improve_all(const Game& G, const BatchOut& O, int mode, const double* v,
-                           Scratch<T>& S, double* res_out) {
+template <class Ctx>
+__device__ int improve_all(const Game& G, const BatchOut& O, int mode, const double* v, Ctx& C,
+                           double* res_out) {
     double vm = 0.0;
-    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) vm = fmax(vm, fabs(v[i]));
-    vm = block_max(vm, S.red_d);
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) vm = fmax(vm, fabs(v[i]));
+    vm = C.max(vm);
     const double tau = 1e-13 * fmax(1.0, vm);
     int changed = 0;
     double res = 0.0;
-    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
         double r = 0.0;
         changed += improve_state(G, O, mode, i, tau, v, &r);
         res = fmax(res, r);
     }
-    if (res_out) *res_out = block_max(res, S.red_d);
-    return block_sum(changed, S.red_i);
+    if (res_out) *res_out = C.max(res);
+    return C.sumi(changed);
 }
 
 // Algorithm 2 with Algorithm 1 inside for game g (see the Isaacs driver for
 // the stopping rules and the exact confirmation of inexact evaluations).
-template <typename T>
-__device__ void solve_game(const BatchArgs& B, int g, char* smem) {
+template <typename T, class Ctx>
+__device__ void solve_game(const BatchArgs& B, int g, Ctx& C) {
     Game G;
     G.T = B.T;
     G.x0 = B.st_off[g];
@@ -335,75 +383,90 @@ __device__ void solve_game(const BatchArgs& B, int g, char* smem) {
     G.mu = B.mu[g];
     const BatchOut& O = B.out;
     const BatchOpts& P = B.opt;
-    __shared__ double red_d[32];
-    __shared__ T red_t[32];
-    __shared__ int red_i[32];
-    Scratch<T> S;
-    S.r = (T*)smem;
-    S.e = S.r + B.max_n;
-    S.t = S.e + B.max_n;
-    S.red_d = red_d;
-    S.red_t = red_t;
-    S.red_i = red_i;
     double* v = O.v + G.x0;
     const int a0 = P.default_alpha;
-    for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) {
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
         v[i] = 0.0;
         O.alpha[G.x0 + i] = (uint8_t)(a0 < G.T.m1 ? a0 : 0);
         for (int a = 0; a < G.T.m1; ++a) O.beta[(G.x0 + i) * G.T.m1 + a] = 0;
     }
-    __syncthreads();
-    improve_all(G, O, 2, v, S, (double*)nullptr);   // MIN's first reply, assembly
-    __syncthreads();
+    if (!C.sync()) return;
+    improve_all(G, O, 2, v, C, (double*)nullptr);   // MIN's first reply, assembly
+    if (!C.sync()) return;
     int outer = 0, systems = 0, cycles = 0, converged = 0;
     double res = 0.0;
     while (true) {
         for (int j = 0; j < P.max_inner; ++j) {
-            const bool exact = evaluate<T>(G, O, P, v, S, P.pi_rtol, &cycles);
+            const bool exact = evaluate<T>(G, O, P, v, C, P.pi_rtol, &cycles);
             ++systems;
-            __syncthreads();
-            if (improve_all(G, O, 1, v, S, (double*)nullptr) != 0) continue;
-            __syncthreads();
+            if (!C.sync()) return;
+            if (improve_all(G, O, 1, v, C, (double*)nullptr) != 0) continue;
+            if (!C.sync()) return;
             if (!exact) {
-                evaluate<T>(G, O, P, v, S, 0.0, &cycles);
-                __syncthreads();
-                if (improve_all(G, O, 1, v, S, (double*)nullptr) != 0) continue;
-                __syncthreads();
+                evaluate<T>(G, O, P, v, C, 0.0, &cycles);
+                if (!C.sync()) return;
+                if (improve_all(G, O, 1, v, C, (double*)nullptr) != 0) continue;
+                if (!C.sync()) return;
             }
             break;
         }
         ++outer;
-        __syncthreads();
-        const int ach = improve_all(G, O, 0, v, S, &res);
-        __syncthreads();
+        if (!C.sync()) return;
+        const int ach = improve_all(G, O, 0, v, C, &res);
+        if (!C.sync()) return;
         if (res <= P.eps || ach == 0) {
             converged = 1;
             break;
         }
         if (outer >= P.max_outer) break;
     }
-    if (threadIdx.x == 0) {
+    if (C.leader()) {
         O.gstats[4 * g + 0] = outer;
         O.gstats[4 * g + 1] = systems;
         O.gstats[4 * g + 2] = cycles;
         O.gstats[4 * g + 3] = converged;
         O.gres[g] = res;
     }
-    __syncthreads();
+    C.sync();
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_games_pi(const __grid_constant__ BatchArgs B) {
     extern __shared__ __align__(16) char smem[];
     __shared__ int s_game;
+    __shared__ double red_d[32];
+    __shared__ int red_i[32];
     while (true) {
         if (threadIdx.x == 0) s_game = atomicAdd(B.queue, 1);
         __syncthreads();
         const int g = s_game;
         __syncthreads();
         if (g >= B.count) break;
-        solve_game<T>(B, g, smem);
+        BlockCtx<T> C;
+        C.r = (T*)smem;
+        C.e = C.r + B.max_n;
+        C.t = C.e + B.max_n;
+        C.red_d = red_d;
+        C.red_i = red_i;
+        solve_game<T>(B, g, C);
     }
+}
+
+// One game over a cooperative grid (games too large for one block).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_game_pi_grid(const __grid_constant__ BatchArgs B,
+                                                           GridWork W) {
+    __shared__ double red_d[32];
+    GridCtx<T> C;
+    C.r = (T*)W.r;
+    C.e = (T*)W.e;
+    C.t = (T*)W.t;
+    C.part = W.part;
+    C.bar = W.bar;
+    C.red_d = red_d;
+    C.flip = 0;
+    C.bad = false;
+    solve_game<T>(B, 0, C);
 }
 
 }  // namespace
@@ -420,6 +483,30 @@ void launch_game_prepare(const GameTables& T, int count, const int64_t* st_off, 
     const unsigned g = (unsigned)std::min<int64_t>((rows + 255) / 256, 152 * 32);
     k_game_prepare<<<std::max(1u, g), 256, 0, st>>>(T, count, st_off, mu, leak, prob32);
     GS_CHECK_LAUNCH();
+}
+
+int game_grid_blocks(int64_t n, int cap) {
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        int dev = 0;
+        GS_CUDA(cudaGetDevice(&dev));
+        GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int a = 0, b = 0;
+        GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_game_pi_grid<float>, kThreads, 0));
+        GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_game_pi_grid<double>, kThreads, 0));
+        per_sm = std::max(1, std::min(a, b));
+    }
+    int blocks = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)per_sm * sms);
+    if (cap > 0) blocks = std::min(blocks, cap);
+    return std::max(1, blocks);
+}
+
+void launch_game_pi_grid(const BatchArgs& B, const GridWork& W, int blocks, bool mixed,
+                         cudaStream_t st) {
+    const void* fn = mixed ? (const void*)k_game_pi_grid<float> : (const void*)k_game_pi_grid<double>;
+    void* args[] = {(void*)&B, (void*)&W};
+    GS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kThreads), args, 0, st));
+    note_launches(1);
 }
 
 size_t games_smem_bytes(int max_n, bool mixed) {

@@ -1,7 +1,7 @@
 // Finite games given by CSR transition tables: device-side argument blocks.
 #pragma once
 
-#include "common.cuh"
+#include "gridsync.cuh"
 
 namespace gs {
 
@@ -44,6 +44,13 @@ struct BatchArgs {
     int* queue;             // work counter (zeroed before the launch)
 };
 
+// Work vectors of the grid-wide single-game kernel (global memory).
+struct GridWork {
+    void *r, *e, *t;     // n elements each (float32 or float64)
+    double* part;        // 2 x (blocks) per-block partials
+    GridBarrier* bar;    // zeroed before the launch
+};
+
 // Largest game the one-block-per-game kernel takes (its three correction
 // vectors live in shared memory).
 constexpr int kGameMaxStatesMixed = 16384;
@@ -55,5 +62,12 @@ void launch_game_prepare(const GameTables& T, int count, const int64_t* st_off, 
                          const double* mu, double* leak, float* prob32, cudaStream_t st);
 size_t games_smem_bytes(int max_n, bool mixed);
 void launch_games_pi(const BatchArgs& B, bool mixed, cudaStream_t st);
+// Thread blocks for the grid-wide kernel on a game of n states (cap > 0 limits them).
+int game_grid_blocks(int64_t n, int cap);
+void launch_game_pi_grid(const BatchArgs& B, const GridWork& W, int blocks, bool mixed,
+                         cudaStream_t st);
+
+// Games of at least this many states, set alone, run on the whole grid.
+constexpr int64_t kGameGridMinStates = 4096;
 
 }  // namespace gs

@@ -32,7 +32,8 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
     }
     const bool mixed = s->opt.precision != GS_PREC_FP64;
     const int64_t cap = mixed ? kGameMaxStatesMixed : kGameMaxStatesFP64;
-    if (max_n > cap) {
+    const bool grid = count == 1 && max_n >= kGameGridMinStates;
+    if (!grid && max_n > cap) {
         set_last_error("set_game: a game has %lld states; this build takes at most %lld per game",
                        (long long)max_n, (long long)cap);
         throw Error{GS_EINVAL};
@@ -84,6 +85,14 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
     G->gstats = ar.alloc<int>(4 * (size_t)count);
     G->gres = ar.alloc<double>(count);
     G->queue = ar.alloc<int>(2);
+    if (grid) {
+        G->grid = true;
+        G->wr = ar.alloc<double>(n_total);
+        G->we = ar.alloc<double>(n_total);
+        G->wt = ar.alloc<double>(n_total);
+        G->part = ar.alloc<double>(2 * 152 * 64);
+        G->bar = ar.alloc<GridBarrier>(1);
+    }
     GS_CUDA(cudaMemcpyAsync(G->st_off, off.data(), sizeof(int64_t) * (count + 1),
                             cudaMemcpyHostToDevice, st));
     GS_CUDA(cudaMemcpyAsync(G->row_ptr, row_ptr, sizeof(int64_t) * (rows + 1), cudaMemcpyDefault, st));
@@ -136,8 +145,15 @@ gs_status run_games(gs_solver* s, gs_solve_stats* stats) {
     GS_CUDA(cudaEventCreate(&e0));
     GS_CUDA(cudaEventCreate(&e1));
     GS_CUDA(cudaMemsetAsync(G.queue, 0, sizeof(int), st));
+    if (G.grid) GS_CUDA(cudaMemsetAsync(G.bar, 0, sizeof(GridBarrier), st));
     GS_CUDA(cudaEventRecord(e0, st));
-    launch_games_pi(B, mixed, st);
+    if (G.grid) {
+        GridWork W{G.wr, G.we, G.wt, G.part, G.bar};
+        const int blocks = std::min(game_grid_blocks(G.n_total, s->opt.grid_blocks), 152 * 64);
+        launch_game_pi_grid(B, W, blocks, mixed, st);
+    } else {
+        launch_games_pi(B, mixed, st);
+    }
     GS_CUDA(cudaEventRecord(e1, st));
     G.stats_h.resize(4 * (size_t)G.count);
     G.res_h.resize(G.count);
@@ -145,7 +161,15 @@ gs_status run_games(gs_solver* s, gs_solve_stats* stats) {
                             cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaMemcpyAsync(G.res_h.data(), G.gres, sizeof(double) * G.count,
                             cudaMemcpyDeviceToHost, st));
+    GridBarrier hb{};
+    if (G.grid) GS_CUDA(cudaMemcpyAsync(&hb, G.bar, sizeof hb, cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
+    if (hb.error) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        set_last_error("game solve: a grid barrier wait timed out");
+        return GS_ETIMEOUT;
+    }
     float ms = 0;
     GS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);

@@ -5,20 +5,13 @@
 // gives up sets an error flag and the kernels return.
 #include <mutex>
 
+#include "gridsync.cuh"
 #include "mgsolve.cuh"
 #include "stencil.cuh"
 
 namespace gs {
 
 namespace {
-
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // Optional phase timestamps (diagnostic builds with -DGS_PHASE_PROF): block 0
 // records the global timer after every grid-wide barrier.
@@ -39,42 +32,6 @@ __device__ __forceinline__ void prof_mark(int tag) {
 #else
 __device__ __forceinline__ void prof_mark(int) {}
 #endif
-
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  One
-// word counts arrivals: block 0 adds 2^31 - (nb - 1) and every other block
-// adds 1, so the top bit flips exactly when the last block arrives and the low
-// bits return to their value; waiters watch the top bit.  A wait gives up
-// after kBarrierTimeoutNs and raises the error flag, which releases the others.
-struct Grid {
-    GridBarrier* b;
-    unsigned nb;
-    __device__ bool sync() const {
-        __shared__ int s_ok;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int ok = 1;
-            const unsigned add = blockIdx.x == 0 ? 0x80000000u - (nb - 1) : 1u;
-            volatile unsigned* word = &b->count;
-            __threadfence();
-            const unsigned old = atomicAdd(&b->count, add);
-            if (((old ^ *word) & 0x80000000u) == 0) {
-                const unsigned long long t0 = global_ns();
-                while (((old ^ *word) & 0x80000000u) == 0) {
-                    if (*(volatile int*)&b->error) { ok = 0; break; }
-                    if (global_ns() - t0 > kBarrierTimeoutNs) {
-                        atomicExch(&b->error, 1);
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-            __threadfence();
-            s_ok = ok;
-        }
-        __syncthreads();
-        return s_ok != 0;
-    }
-};
 
 __device__ __forceinline__ int colour_ox(int c) { return c == 0 || c == 3 ? 1 : 0; }
 __device__ __forceinline__ int colour_oy(int c) { return c == 0 || c == 2 ? 1 : 0; }
@@ -276,7 +233,7 @@ __device__ void block_vcycle(const SolveArgs& a, const LevelArgs* tl, const doub
 // Algorithm 3 with gamma = 1 over the whole hierarchy.
 template <typename T>
 __device__ bool grid_vcycle(const SolveArgs& a, const LevelArgs* tl, const double* inv,
-                            const Grid& G, size_t gt, size_t gs, bool fine_zero) {
+                            const GridSync& G, size_t gt, size_t gs, bool fine_zero) {
     for (int l = 0; l < a.tail; ++l) {
         const int ncol = l == 0 ? 2 : 4;
         const bool z = l > 0 || fine_zero;
@@ -350,7 +307,7 @@ __device__ void setup_items(const SolveArgs& a, int l, int kind, size_t start, s
 // policy codes, then the explicit inverse of the coarsest operator.
 __global__ void __launch_bounds__(kMGThreads) k_mg_setup(const __grid_constant__ SolveArgs a) {
     extern __shared__ double smem[];
-    const Grid G{a.bar, gridDim.x};
+    const GridSync G{a.bar, gridDim.x};
     const size_t gt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t gs = (size_t)gridDim.x * blockDim.x;
     const int Lc = a.nlev - 1;
@@ -474,7 +431,7 @@ template <typename T>
 __global__ void __launch_bounds__(kMGThreads) k_mg_cycles(const __grid_constant__ SolveArgs a) {
     extern __shared__ __align__(16) char smem_c[];
     __shared__ LevelArgs tl[kMaxLevels];
-    const Grid G{a.bar, gridDim.x};
+    const GridSync G{a.bar, gridDim.x};
     const size_t gt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t gs = (size_t)gridDim.x * blockDim.x;
     if (!G.sync()) return;   // set-up complete (and error state shared)
@@ -563,7 +520,8 @@ Occupancy& occupancy() {
 int grid_blocks(const SolveArgs& a, int per_sm, int sms) {
     if (a.tail == 0) return 1;
     const size_t want = (a.L[0].n / 2 + kMGThreads - 1) / kMGThreads;
-    const size_t cap = (size_t)per_sm * sms;
+    size_t cap = (size_t)per_sm * sms;
+    if (a.max_blocks > 0) cap = std::min(cap, (size_t)a.max_blocks);
     return (int)std::max<size_t>(1, std::min(want, cap));
 }
 

@@ -3,7 +3,7 @@
 // Galerkin set-up, the V-cycles (Algorithm 3) and the float64 stopping test.
 #pragma once
 
-#include "common.cuh"
+#include "gridsync.cuh"
 
 namespace gs {
 
@@ -27,13 +27,6 @@ struct LevelArgs {
     float* P32;
 };
 
-// Bounded grid barrier state; `error` is set when a wait gives up.
-struct GridBarrier {
-    unsigned int count;
-    unsigned int gen;
-    int error;
-    int pad;
-};
 
 struct SolveOut {
     unsigned long long rmax[2];   // |b - A v|_inf per residual evaluation (bits), ping-pong
@@ -54,6 +47,7 @@ struct SolveArgs {
     int nu1, nu2, max_cycles;
     int mixed;       // float32 V-cycles on the float64 residual (iterative refinement)
     int do_setup;    // build interpolation, Galerkin operators and coarse inverse first
+    int max_blocks;  // cap on the grid (0 = whole GPU)
     double lin_tol;
     double rel_tol;  // also stop once the residual fell by this factor (0: floor only)
     double* inv;     // inverse of the coarsest operator (n_L x n_L)

@@ -323,6 +323,7 @@ bool linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bo
     a.max_cycles = s->opt.max_cycles;
     a.mixed = mixed ? 1 : 0;
     a.do_setup = do_setup ? 1 : 0;
+    a.max_blocks = s->opt.grid_blocks;
     a.lin_tol = s->opt.lin_tol;
     a.rel_tol = rel_tol;
     a.inv = g.inv;

@@ -71,6 +71,9 @@ struct GameProblem {
     float* prob32 = nullptr;
     uint8_t *alpha = nullptr, *beta = nullptr;
     int *gstats = nullptr, *queue = nullptr;
+    bool grid = false;                     // one large game on the whole grid
+    double *wr = nullptr, *we = nullptr, *wt = nullptr, *part = nullptr;
+    GridBarrier* bar = nullptr;
     std::vector<int> stats_h;
     std::vector<double> res_h;
     GameTables tables() const { return {m1, m2, row_ptr, col, prob, prob32, rew, leak}; }

@@ -32,8 +32,9 @@ def test_every_declared_symbol_is_exported(gs):
 
 
 def test_struct_layouts_match_header(gs):
-    # gs_options: 112 bytes, the stream pointer at 88; gs_solve_stats: 48 bytes
-    assert ctypes.sizeof(gs.gs_options) == 112 and gs.gs_options.stream.offset == 88
+    # gs_options: 120 bytes, the stream pointer at 88; gs_solve_stats: 48 bytes
+    assert ctypes.sizeof(gs.gs_options) == 120 and gs.gs_options.stream.offset == 88
+    assert gs.gs_options.grid_blocks.offset == 112
     assert gs.gs_options.pi_rtol.offset == 96
     assert ctypes.sizeof(gs.gs_solve_stats) == 48
 

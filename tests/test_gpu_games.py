@@ -152,3 +152,19 @@ def test_game_validation(gs):
             s.set_game(n, 4, 4, rp, col, prob, rew, 1.0)
         s.set_game(n, 4, 4, rp, col, prob, rew, mu)   # the valid table is accepted
         assert s.solve()["converged"] == 1
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("n,blocks", [(5000, 0), (12000, 0), (12000, 8)])
+def test_large_game_on_the_grid(gs, n, blocks, prec):
+    """Games of >= 4096 states set alone run on a cooperative grid (policy
+    iteration on the device, bounded grid barriers); grid_blocks caps it."""
+    rp, col, prob, rew, mu = synth.random_game(n, 70 + n)
+    _, ref = oracle_of(n, 4, 4, rp, col, prob, rew, mu)
+    with gs.GameSolver(precision=prec, grid_blocks=blocks) as s:
+        s.set_game(n, 4, 4, rp, col, prob, rew, mu)
+        st = s.solve()
+        v = s.get_value()
+        a, b = s.get_policy()
+    assert st["converged"] == 1
+    assert check(v, a, b, ref) <= TOL[prec], st
