@@ -178,6 +178,169 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """C4: 4096 random games (n ~ U{256..8192}, m1 = m2 = 4, 8 successors,
+    Dirichlet(1), rewards U(-1,1), mu = 0.99) in one persistent launch."""
+    import numpy as np
+    import torch
+    import synth
+    torch.cuda.set_device(0)
+    import paper_1107_1653_gb300 as gs
+    count, seed = args.games, 4
+    sizes = synth.batch_game_sizes(count, seed)
+    t0 = time.perf_counter()
+    off, rp, col, prob, rew, mu = synth.random_game_batch(sizes, seed, workers=os.cpu_count())
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    s = gs.GameSolver(precision=args.precision, stream=stream)
+    # inputs resident: the tables go to the device before timing
+    s.set_game_batch(off, 4, 4, rp, col, prob, rew, mu)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        s.solve()
+    times, st = [], None
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st = s.solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    gst, gres = s.batch_stats()
+    sec = statistics.mean(times)
+    n_tot = int(off[-1])
+    nnz = len(col)
+    # algorithmic float64 work of the improvements: every evaluation of a row
+    # costs 2 flops per successor; per game one reply + one full improvement
+    # per outer iteration (m1*m2 rows per state) and one inner improvement per
+    # evaluation (m2 rows per state)
+    rows_full = 16
+    imp = sum(int(n) * 8 * 2 * (rows_full * (1 + int(o)) + 4 * 2 * int(sy))
+              for n, o, sy in zip(sizes, gst[:, 0], gst[:, 1]))
+    # e2e: host tables -> set_game_batch -> solve -> values and policies back
+    e2e = []
+    v_h = np.empty(n_tot)
+    a_h = np.empty(n_tot, np.uint8)
+    b_h = np.empty((n_tot, 4), np.uint8)
+    for _ in range(2):
+        t1 = time.perf_counter()
+        s.set_game_batch(off, 4, 4, rp, col, prob, rew, mu)
+        s.solve()
+        s.get_value(out=v_h)
+        s.get_policy(alpha_out=a_h, beta_out=b_h)
+        e2e.append(time.perf_counter() - t1)
+    s.close()
+    line = {
+        "metric": "random games solved/s (batch of 4096, n~U{256..8192})", "value": count / sec,
+        "unit": "games/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": "random_games_batch4096", "games": count, "states": n_tot,
+                   "nnz": nnz, "seed": seed, "precision": args.precision,
+                   "l2": "flushed between steps (256 MiB write)",
+                   "outer_max": int(gst[:, 0].max()), "systems": int(gst[:, 1].sum()),
+                   "cycles": int(gst[:, 2].sum()), "converged": int(gst[:, 3].min()),
+                   "res_max": float(gres.max())},
+        "states_per_s": n_tot / sec,
+        "fp64_improvement_tflops": imp / sec / 1e12,
+        "generation_s": t_gen,
+        "e2e": {"value": count / statistics.mean(e2e), "unit": "games/s",
+                "h2d_bytes_per_step": int(rp.nbytes + col.nbytes + prob.nbytes + rew.nbytes),
+                "d2h_bytes_per_step": int(v_h.nbytes + a_h.nbytes + b_h.nbytes)},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args):
+    """C5: Poisson stream of requests, 70% Isaacs grids (sides 63..1023) and
+    30% random games (n ~ U{1e3..1e6}), mixed precision, arrival rate 80% of
+    the closed-loop capacity; p50/p99 latency and solves/s."""
+    import numpy as np
+    import torch
+    import synth
+    torch.cuda.set_device(0)
+    import paper_1107_1653_gb300 as gs
+    rng = np.random.default_rng(5)
+    # pool of games at the quantile midpoints of U{1e3..1e6}; a request draws
+    # n ~ U and takes the pool game of its quantile bucket (the tables stay on
+    # the device and requests borrow them, as a server caching its models would)
+    qs = (np.arange(args.pool) + 0.5) / args.pool
+    pool_n = (1000 + qs * (1_000_000 - 1000)).astype(np.int64)
+    t0 = time.perf_counter()
+    pool = []
+    for i, n in enumerate(pool_n):
+        rp, col, prob, rew, mu = synth.random_game_parallel(int(n), 5000 + i, workers=os.cpu_count())
+        pool.append((int(n), torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(),
+                     torch.from_numpy(prob).cuda(), torch.from_numpy(rew).cuda(), mu))
+    t_gen = time.perf_counter() - t0
+    sides = (63, 127, 255, 511, 1023)
+
+    def draw(k):
+        if rng.random() < 0.7:
+            return ("isaacs", int(rng.choice(sides)), 5 + k)
+        n = int(rng.integers(1000, 1_000_001))
+        return ("game", min(args.pool - 1, int((n - 1000) / (999_001 / args.pool))))
+
+    def submit(srv, r):
+        if r[0] == "isaacs":
+            return srv.submit_isaacs(r[1], 0, r[2])
+        n, rp, col, prob, rew, mu = pool[r[1]]
+        return srv.submit_game(n, 4, 4, rp, col, prob, rew, mu, borrow=True)
+
+    with gs.GameServer(slots=args.slots, precision="mixed") as srv:
+        # closed-loop capacity: a burst of requests submitted at once
+        burst = [draw(k) for k in range(args.burst)]
+        t1 = time.perf_counter()
+        tickets = [submit(srv, r) for r in burst]
+        for t in tickets:
+            srv.wait(t)
+            srv.result(t)
+        cap = len(burst) / (time.perf_counter() - t1)
+        rate = 0.8 * cap
+        reqs = [draw(10_000 + k) for k in range(args.requests)]
+        gaps = rng.exponential(1.0 / rate, size=len(reqs))
+        tickets = []
+        t_start = time.perf_counter()
+        due = t_start
+        for r, g in zip(reqs, gaps):
+            due += g
+            d = due - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(submit(srv, r))
+        infos = []
+        for t in tickets:
+            infos.append(srv.wait(t))
+            srv.result(t)
+        makespan = time.perf_counter() - t_start
+    lat = np.array([i["t_end"] - i["t_submit"] for i in infos])
+    ok = sum(1 for i in infos if i["status"] == 0)
+    kinds = [r[0] for r in reqs]
+    lat_i = lat[[k == "isaacs" for k in kinds]]
+    lat_g = lat[[k == "game" for k in kinds]]
+    line = {
+        "metric": "serving: p50/p99 latency and solves/s (70% Isaacs 63..1023, 30% games 1e3..1e6)",
+        "value": ok / makespan, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "serving_mix", "requests": len(reqs), "slots": args.slots,
+                   "arrival": "Poisson", "rate_per_s": rate, "capacity_per_s": cap,
+                   "game_pool": [int(n) for n in pool_n], "isaacs_sides": list(sides)},
+        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+        "p50_ms_isaacs": float(np.percentile(lat_i, 50) * 1e3) if len(lat_i) else None,
+        "p99_ms_isaacs": float(np.percentile(lat_i, 99) * 1e3) if len(lat_i) else None,
+        "p50_ms_games": float(np.percentile(lat_g, 50) * 1e3) if len(lat_g) else None,
+        "p99_ms_games": float(np.percentile(lat_g, 99) * 1e3) if len(lat_g) else None,
+        "completed": ok, "makespan_s": makespan, "generation_s": t_gen,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile(args):
     """One solve of the workload and nothing else (a short command for ncu)."""
     import torch
@@ -349,6 +512,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--side", type=int, default=SIDE)
+    ap.add_argument("--workload", default="isaacs", choices=["isaacs", "batch", "serving"],
+                    help="isaacs: the metric's 1023^2 solve (default); batch: 4096 random "
+                         "games; serving: a Poisson request stream")
+    ap.add_argument("--games", type=int, default=4096)
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--burst", type=int, default=64)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--pool", type=int, default=8)
     ap.add_argument("--profile", action="store_true",
                     help="run one solve only (for ncu); prints the solve statistics")
     args = ap.parse_args()
@@ -359,6 +530,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

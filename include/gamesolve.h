@@ -250,6 +250,75 @@ gs_status gamesolve_isaacs_policy_solve_static(int32_t side, int32_t variant, ui
                                                int32_t precision, void* stream,
                                                gs_solve_stats* stats);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop around the solvers: requests are queued in arrival order and
+ * admitted to worker slots as slots and device memory free up.  Each slot has
+ * its own CUDA stream and solver, its grid-wide launches capped to a share of
+ * the GPU, so the work of the requests in flight overlaps on the device.  A
+ * request's multigrid hierarchy and policies stay on the device for its whole
+ * policy iteration; its value and policies are copied to host memory when it
+ * completes.  Results do not depend on what else is in flight (the kernels'
+ * arithmetic does not depend on timing; only the number of blocks a grid-wide
+ * game reduction uses can change its rounding). */
+typedef struct gs_server gs_server;
+
+typedef struct {
+    int32_t kind;            /* 1 Isaacs grid, 2 finite game */
+    int32_t side;            /* Isaacs: grid side (2^k - 1) */
+    int32_t variant;         /* Isaacs: 0 plain, 1 obstacle */
+    int32_t m1, m2;          /* game: actions */
+    uint64_t seed;           /* Isaacs: noise stream */
+    int64_t n;               /* game: states */
+    const int64_t* row_ptr;  /* game: CSR table as for gamesolve_set_game (copied at submit) */
+    const int32_t* col;
+    const double* prob;
+    const double* reward;
+    double mu;               /* game: discount */
+    int32_t flags;           /* GS_REQ_BORROW: the table is not copied at submit; the caller
+                                keeps it valid (host or device memory) until the request is done */
+    int32_t reserved;
+} gs_request;
+
+enum { GS_REQ_BORROW = 1 };
+
+typedef struct {
+    int32_t state;           /* 0 queued, 1 running, 2 done */
+    int32_t status;          /* gs_status of the solve, once done */
+    double t_submit, t_start, t_end;   /* seconds since the server was created */
+    int64_t n;               /* states of the request */
+    gs_solve_stats stats;    /* statistics of its solve */
+} gs_ticket_info;
+
+/* Starts `slots` worker threads on the current device, each creating a solver
+ * with `opt` (NULL = defaults) on its own stream.  mem_budget: device bytes the
+ * requests in flight may hold together (0 = half the free memory); a request
+ * larger than the budget runs when nothing else is in flight.
+ * Errors: GS_EINVAL (slots outside [1, 64] or bad options), GS_ECUDA. */
+gs_status gamesolve_server_create(gs_server** out, const gs_options* opt, int32_t slots,
+                                  uint64_t mem_budget);
+
+/* Queues a request; its data is copied before the call returns unless the
+ * request borrows it (GS_REQ_BORROW).  *ticket
+ * identifies it.  Errors: GS_EINVAL (invalid request).  Table errors found
+ * when it runs are reported in its ticket's status. */
+gs_status gamesolve_server_submit(gs_server* srv, const gs_request* req, int64_t* ticket);
+
+/* State of a request without waiting (GS_EINVAL for an unknown ticket). */
+gs_status gamesolve_server_poll(gs_server* srv, int64_t ticket, gs_ticket_info* info);
+
+/* Waits until the request is done, then fills *info (may be NULL). */
+gs_status gamesolve_server_wait(gs_server* srv, int64_t ticket, gs_ticket_info* info);
+
+/* Copies a done request's value (n doubles) and policies (n bytes, n*m1
+ * bytes; any pointer may be NULL) and forgets the ticket.  Returns the
+ * request's solve status; GS_ESTATE if it is not done yet. */
+gs_status gamesolve_server_result(gs_server* srv, int64_t ticket, double* v_out, int64_t n,
+                                  uint8_t* alpha, uint8_t* beta);
+
+/* Stops the workers after the requests in flight finish; queued requests
+ * that have not started are dropped.  NULL is a no-op. */
+void gamesolve_server_destroy(gs_server* srv);
+
 /* Frees the solver and all of its device memory.  NULL is a no-op. */
 void gamesolve_destroy(gs_solver* s);
 

@@ -54,6 +54,27 @@ class gs_solve_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gs_request(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("side", ctypes.c_int32), ("variant", ctypes.c_int32),
+        ("m1", ctypes.c_int32), ("m2", ctypes.c_int32), ("seed", ctypes.c_uint64),
+        ("n", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+        ("prob", ctypes.c_void_p), ("reward", ctypes.c_void_p), ("mu", ctypes.c_double),
+        ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+GS_REQ_BORROW = 1
+
+
+class gs_ticket_info(ctypes.Structure):
+    _fields_ = [
+        ("state", ctypes.c_int32), ("status", ctypes.c_int32),
+        ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_end", ctypes.c_double),
+        ("n", ctypes.c_int64), ("stats", gs_solve_stats),
+    ]
+
+
 _P = ctypes.c_void_p
 _S = ctypes.c_int
 _SIGS = {
@@ -77,6 +98,13 @@ _SIGS = {
     "gamesolve_trace": (_S, [_P, ctypes.c_int32]),
     "gamesolve_trace_read": (_S, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "gamesolve_kernel_launches": (ctypes.c_uint64, []),
+    "gamesolve_server_create": (_S, [ctypes.POINTER(_P), ctypes.POINTER(gs_options), ctypes.c_int32,
+                                     ctypes.c_uint64]),
+    "gamesolve_server_submit": (_S, [_P, ctypes.POINTER(gs_request), ctypes.POINTER(ctypes.c_int64)]),
+    "gamesolve_server_poll": (_S, [_P, ctypes.c_int64, ctypes.POINTER(gs_ticket_info)]),
+    "gamesolve_server_wait": (_S, [_P, ctypes.c_int64, ctypes.POINTER(gs_ticket_info)]),
+    "gamesolve_server_result": (_S, [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P]),
+    "gamesolve_server_destroy": (None, [_P]),
     "gamesolve_destroy": (None, [_P]),
     "gamesolve_strerror": (ctypes.c_char_p, [_S]),
     "gamesolve_last_error": (ctypes.c_char_p, []),
@@ -243,6 +271,82 @@ class GameSolver:
         _check(lib.gamesolve_policy_solve(self.h, _ptr(alpha), _ptr(beta), _ptr(w0), _ptr(w),
                                           ctypes.byref(st)), "gamesolve_policy_solve")
         return w, st.as_dict()
+
+
+class GameServer:
+    """Owns one gs_server (continuous batching of solve requests)."""
+
+    def __init__(self, slots=4, mem_budget=0, **opts):
+        self.opts = default_options(**opts)
+        h = _P()
+        _check(lib.gamesolve_server_create(ctypes.byref(h), ctypes.byref(self.opts), slots,
+                                           mem_budget), "gamesolve_server_create")
+        self.h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gamesolve_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit_isaacs(self, side, variant=0, seed=1):
+        r = gs_request(kind=1, side=side, variant=variant, seed=seed)
+        t = ctypes.c_int64()
+        _check(lib.gamesolve_server_submit(self.h, ctypes.byref(r), ctypes.byref(t)),
+               "gamesolve_server_submit")
+        self._keep[t.value] = (side * side, 5 if variant == 1 else 4)
+        return t.value
+
+    def submit_game(self, n, m1, m2, row_ptr, col, prob, reward, mu, borrow=False):
+        """borrow=True: the arrays (host or CUDA) are read when the request runs
+        and must stay alive and unchanged until it is done."""
+        row_ptr, col = _as(row_ptr, np.int64), _as(col, np.int32)
+        prob, reward = _as(prob, np.float64), _as(reward, np.float64)
+        r = gs_request(kind=2, n=n, m1=m1, m2=m2, row_ptr=_ptr(row_ptr), col=_ptr(col),
+                       prob=_ptr(prob), reward=_ptr(reward), mu=mu,
+                       flags=GS_REQ_BORROW if borrow else 0)
+        t = ctypes.c_int64()
+        _check(lib.gamesolve_server_submit(self.h, ctypes.byref(r), ctypes.byref(t)),
+               "gamesolve_server_submit")
+        self._keep[t.value] = (n, m1)
+        return t.value
+
+    @staticmethod
+    def _info(info):
+        d = {k: getattr(info, k) for k, _ in gs_ticket_info._fields_ if k != "stats"}
+        d["stats"] = info.stats.as_dict()
+        return d
+
+    def poll(self, ticket):
+        info = gs_ticket_info()
+        _check(lib.gamesolve_server_poll(self.h, ticket, ctypes.byref(info)), "gamesolve_server_poll")
+        return self._info(info)
+
+    def wait(self, ticket):
+        info = gs_ticket_info()
+        _check(lib.gamesolve_server_wait(self.h, ticket, ctypes.byref(info)), "gamesolve_server_wait")
+        return self._info(info)
+
+    def result(self, ticket):
+        n, m1 = self._keep.pop(ticket)
+        v = np.empty(n, np.float64)
+        a = np.empty(n, np.uint8)
+        b = np.empty((n, m1), np.uint8)
+        _check(lib.gamesolve_server_result(self.h, ticket, _ptr(v), n, _ptr(a), _ptr(b)),
+               "gamesolve_server_result", (GS_OK, GS_ENOTCONV))
+        return v, a, b
 
 
 def exported_symbols():

@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "solver.cuh"
 
@@ -27,6 +28,21 @@ static gs_status guarded(F&& f) {
         set_last_error("unexpected host exception");
         return GS_ECUDA;
     }
+}
+
+// Memory freed back to the device's stream-ordered pool stays there for the
+// next problem instead of returning to the driver at every synchronisation.
+static void keep_pool_memory(int dev) {
+    static std::once_flag once[64];
+    if (dev < 0 || dev >= 64) return;
+    std::call_once(once[dev], [dev]() {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    });
 }
 
 static bool is_pow2m1(int side) {
@@ -83,6 +99,7 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
     return guarded([&]() -> gs_status {
         int dev = 0;
         GS_CUDA(cudaGetDevice(&dev));
+        keep_pool_memory(dev);
         auto* s = new gs_solver();
         s->opt = o;
         s->st = (cudaStream_t)o.stream;

@@ -57,7 +57,7 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
     const int64_t nnz = nnz_ends[1];
 
     size_t held = s->prob ? s->prob->arena.held() : 0;
-    auto P = std::make_unique<Problem>(s->opt.mem_budget, held);
+    auto P = std::make_unique<Problem>(s->opt.mem_budget, held, s->st);
     P->kind = 2;
     auto G = std::make_unique<GameProblem>();
     G->count = count;

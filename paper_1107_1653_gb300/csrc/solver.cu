@@ -13,7 +13,7 @@ namespace gs {
 
 // ------------------------------------------------------------------ memory
 Arena::~Arena() {
-    for (void* p : ptrs_) cudaFree(p);
+    for (void* p : ptrs_) cudaFreeAsync(p, st_);
 }
 
 void* Arena::raw(size_t bytes) {
@@ -24,10 +24,10 @@ void* Arena::raw(size_t bytes) {
         throw Error{GS_ENOMEM};
     }
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = cudaMallocAsync(&p, bytes, st_);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        set_last_error("cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        set_last_error("cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
         throw Error{e == cudaErrorMemoryAllocation ? GS_ENOMEM : GS_ECUDA};
     }
     ptrs_.push_back(p);
@@ -236,7 +236,7 @@ static void alloc_grid(gs_solver* s, Arena& ar, IsaacsGrid& g) {
 std::unique_ptr<Problem> build_isaacs_problem(gs_solver* s, int side, int variant, uint64_t seed,
                                               const double* xi) {
     size_t held = s->prob ? s->prob->arena.held() : 0;
-    auto P = std::make_unique<Problem>(s->opt.mem_budget, held);
+    auto P = std::make_unique<Problem>(s->opt.mem_budget, held, s->st);
     P->kind = 1;
     std::vector<int> sides{side};
     if (s->opt.fmg) {
@@ -539,7 +539,7 @@ gs_status run_improve(gs_solver* s, const double* v, uint8_t* alpha_out, uint8_t
     Problem& P = *s->prob;
     IsaacsGrid& g = *P.grids.back();
     // work on copies so that the solver's state is untouched
-    Arena scratch(0, 0);
+    Arena scratch(0, 0, s->st);
     double* vd = scratch.alloc<double>(g.n);
     uint8_t* a = scratch.alloc<uint8_t>(g.n);
     uint32_t* b = scratch.alloc<uint32_t>(g.n);
@@ -576,7 +576,7 @@ gs_status run_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* be
     IsaacsGrid& g = *P.grids.back();
     const int m1 = g.variant == 1 ? 5 : 4;
     // validate actions on the device before touching the state
-    Arena scratch(0, 0);
+    Arena scratch(0, 0, s->st);
     uint8_t* a = scratch.alloc<uint8_t>(g.n);
     uint8_t* bst = scratch.alloc<uint8_t>(g.n * m1);
     int* bad = scratch.alloc<int>(2);

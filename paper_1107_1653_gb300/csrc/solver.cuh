@@ -12,9 +12,12 @@
 namespace gs {
 
 // All device allocations of one problem, counted against the memory budget.
+// Allocations are stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// owner's stream), so replacing a problem never synchronises the device.
 class Arena {
 public:
-    Arena(size_t budget, size_t already_held) : budget_(budget), base_(already_held) {}
+    Arena(size_t budget, size_t already_held, cudaStream_t st = nullptr)
+        : budget_(budget), base_(already_held), st_(st) {}
     ~Arena();
     Arena(const Arena&) = delete;
     Arena& operator=(const Arena&) = delete;
@@ -27,6 +30,7 @@ public:
 private:
     void* raw(size_t bytes);
     size_t budget_, base_, held_ = 0;
+    cudaStream_t st_;
     std::vector<void*> ptrs_;
 };
 
@@ -80,7 +84,7 @@ struct GameProblem {
 };
 
 struct Problem {
-    explicit Problem(size_t budget, size_t held) : arena(budget, held) {}
+    Problem(size_t budget, size_t held, cudaStream_t st) : arena(budget, held, st) {}
     Arena arena;
     int kind = 0;                                // 1 Isaacs, 2 finite games
     std::unique_ptr<GameProblem> game;

@@ -57,7 +57,7 @@ DRAWS_PER_ROW = 17  # 8 successor draws, 8 exponential draws, 1 reward draw
 
 
 def random_game(n: int, seed: int, m1: int = 4, m2: int = 4, k: int = 8,
-                mu: float = 0.99):
+                mu: float = 0.99, rows=None):
     """A random finite discounted game in the C-ABI's CSR layout.
 
     Rows are indexed (x * m1 + a) * m2 + b.  Each row has ``k`` distinct
@@ -71,12 +71,14 @@ def random_game(n: int, seed: int, m1: int = 4, m2: int = 4, k: int = 8,
     adjustment), draws 8..8+k-1 the exponentials, draw 16 the reward.
 
     Returns (row_ptr int64[R+1], col int32[R*k], prob float64[R*k],
-    reward float64[R], mu) with R = n*m1*m2.
+    reward float64[R], mu) with R = n*m1*m2.  ``rows=(r0, r1)`` draws only
+    those rows (the same values as the whole game's), with row_ptr from 0.
     """
     if not (1 <= k <= 8) or k > n:
         raise ValueError("need 1 <= k <= min(8, n)")
-    R = n * m1 * m2
-    base = np.arange(R, dtype=np.uint64) * np.uint64(DRAWS_PER_ROW)
+    r0, r1 = (0, n * m1 * m2) if rows is None else rows
+    R = r1 - r0
+    base = np.arange(r0, r1, dtype=np.uint64) * np.uint64(DRAWS_PER_ROW)
     picks = np.empty((R, k), dtype=np.int64)
     for t in range(k):
         u = uniform01(seed, base + np.uint64(t))
@@ -113,3 +115,80 @@ def batch_game_sizes(count: int, seed: int, nmin: int = 256, nmax: int = 8192) -
 def batch_game_seed(seed: int, i: int) -> int:
     """Stream of game i of a batch: SplitMix64 seeded with seed XOR i."""
     return (seed ^ i) & 0xFFFFFFFFFFFFFFFF
+
+
+def _batch_part(args):
+    """Worker: games [g0, g1) of a batch (module level so a spawn pool can run it)."""
+    sizes, seed, g0, g1, m1, m2, k, mu = args
+    out = []
+    for g in range(g0, g1):
+        _, col, prob, rew, _ = random_game(int(sizes[g]), batch_game_seed(seed, g), m1, m2, k, mu)
+        out.append((col, prob, rew))
+    return g0, out
+
+
+def random_game_batch(sizes, seed: int, m1: int = 4, m2: int = 4, k: int = 8,
+                      mu: float = 0.99, workers: int = 0):
+    """A batch of random games (game g from the stream seed XOR g) in the
+    concatenated CSR layout of gamesolve_set_game_batch.
+
+    Returns (state_offsets, row_ptr, col, prob, reward, mu_per_game).  With
+    workers > 1 the games are drawn by a spawn-context process pool; the
+    result is identical to the serial one.
+    """
+    import multiprocessing as mp
+    sizes = np.asarray(sizes, dtype=np.int64)
+    count = len(sizes)
+    R = sizes * m1 * m2
+    row_off = np.concatenate([[0], np.cumsum(R)]).astype(np.int64)
+    total_rows = int(row_off[-1])
+    col = np.empty(total_rows * k, np.int32)
+    prob = np.empty(total_rows * k, np.float64)
+    reward = np.empty(total_rows, np.float64)
+
+    def place(g, parts):
+        for j, (c, p, r) in enumerate(parts):
+            a, b = row_off[g + j], row_off[g + j + 1]
+            col[a * k:b * k] = c
+            prob[a * k:b * k] = p
+            reward[a:b] = r
+
+    chunk = max(1, count // max(1, 4 * max(1, workers)))
+    tasks = [(sizes, seed, g, min(count, g + chunk), m1, m2, k, mu) for g in range(0, count, chunk)]
+    if workers and workers > 1 and count > 1:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            for g0, parts in pool.imap_unordered(_batch_part, tasks):
+                place(g0, parts)
+    else:
+        for t in tasks:
+            g0, parts = _batch_part(t)
+            place(g0, parts)
+    row_ptr = np.arange(total_rows + 1, dtype=np.int64) * k
+    st_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return st_off, row_ptr, col, prob, reward, np.full(count, float(mu))
+
+
+def _rows_part(args):
+    n, seed, r0, r1, m1, m2, k, mu = args
+    _, col, prob, rew, _ = random_game(n, seed, m1, m2, k, mu, rows=(r0, r1))
+    return r0, col, prob, rew
+
+
+def random_game_parallel(n: int, seed: int, m1: int = 4, m2: int = 4, k: int = 8,
+                         mu: float = 0.99, workers: int = 0):
+    """random_game drawn by row ranges in a spawn-context process pool (same result)."""
+    import multiprocessing as mp
+    R = n * m1 * m2
+    if not workers or workers < 2:
+        return random_game(n, seed, m1, m2, k, mu)
+    col = np.empty(R * k, np.int32)
+    prob = np.empty(R * k, np.float64)
+    reward = np.empty(R, np.float64)
+    step = max(1, -(-R // (4 * workers)))
+    tasks = [(n, seed, r, min(R, r + step), m1, m2, k, mu) for r in range(0, R, step)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for r0, c, p, rw in pool.imap_unordered(_rows_part, tasks):
+            col[r0 * k:r0 * k + len(c)] = c
+            prob[r0 * k:r0 * k + len(p)] = p
+            reward[r0:r0 + len(rw)] = rw
+    return np.arange(R + 1, dtype=np.int64) * k, col, prob, reward, float(mu)

@@ -1,0 +1,90 @@
+"""Serving: continuous batching of Isaacs and finite-game requests.
+
+Each result must be the same alone and in the mix: Isaacs values bit for bit
+(their kernels' arithmetic does not depend on what else runs), finite games to
+1e-12 relative (a grid-wide game's reductions may use a different number of
+blocks when the server caps its share of the GPU).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def mix():
+    reqs = []
+    for k, side in enumerate((15, 63, 127, 255, 31, 63, 127)):
+        reqs.append(("isaacs", side, k % 2, 100 + k))
+    for k, n in enumerate((300, 1500, 5000, 9000)):
+        reqs.append(("game", n, synth.random_game(n, 500 + k)))
+    return reqs
+
+
+def alone(gs, r):
+    with gs.GameSolver(precision="mixed") as s:
+        if r[0] == "isaacs":
+            s.set_isaacs_grid(r[1], r[2], r[3])
+        else:
+            n, (rp, col, prob, rew, mu) = r[1], r[2]
+            s.set_game(n, 4, 4, rp, col, prob, rew, mu)
+        s.solve()
+        v = s.get_value()
+        a, b = s.get_policy()
+    return v, a, b
+
+
+def submit(srv, r):
+    if r[0] == "isaacs":
+        return srv.submit_isaacs(r[1], r[2], r[3])
+    n, (rp, col, prob, rew, mu) = r[1], r[2]
+    return srv.submit_game(n, 4, 4, rp, col, prob, rew, mu)
+
+
+def test_results_alone_equal_in_the_mix(gs):
+    reqs = mix()
+    ref = [alone(gs, r) for r in reqs]
+    with gs.GameServer(slots=4, precision="mixed") as srv:
+        tickets = [submit(srv, r) for r in reqs]
+        infos = [srv.wait(t) for t in tickets]
+        out = [srv.result(t) for t in tickets]
+    overlap = 0
+    for i, (r, (v, a, b), (v0, a0, b0), info) in enumerate(zip(reqs, out, ref, infos)):
+        assert info["state"] == 2 and info["status"] == gs.GS_OK
+        assert info["t_submit"] <= info["t_start"] <= info["t_end"]
+        if r[0] == "isaacs":
+            assert np.array_equal(v, v0), i
+            assert np.array_equal(a, a0) and np.array_equal(b, b0)
+        else:
+            assert np.max(np.abs(v - v0)) <= 1e-12 * np.max(np.abs(v0)), i
+        for j, other in enumerate(infos):
+            if j != i and other["t_start"] < info["t_end"] and info["t_start"] < other["t_end"]:
+                overlap += 1
+    assert overlap > 0          # the requests' work did overlap
+
+
+def test_memory_budget_serialises(gs):
+    reqs = [("isaacs", 127, 0, 7 + k) for k in range(4)]
+    with gs.GameServer(slots=4, mem_budget=1 << 20) as srv:   # below any one request
+        tickets = [submit(srv, r) for r in reqs]
+        infos = [srv.wait(t) for t in tickets]
+        for t in tickets:
+            srv.result(t)
+    spans = sorted((i["t_start"], i["t_end"]) for i in infos)
+    for (s0, e0), (s1, e1) in zip(spans, spans[1:]):
+        assert s1 >= e0          # admitted one at a time
+
+
+def test_invalid_requests(gs):
+    with gs.GameServer(slots=1) as srv:
+        with pytest.raises(gs.GameSolveError):
+            srv.submit_isaacs(100)
+        rp, col, prob, rew, mu = synth.random_game(50, 2)
+        bad = prob.copy()
+        bad[3] = -1.0
+        t = srv.submit_game(50, 4, 4, rp, col, bad, rew, mu)
+        info = srv.wait(t)
+        assert info["status"] == gs.GS_EINVAL
+        with pytest.raises(gs.GameSolveError):
+            srv.result(t)
