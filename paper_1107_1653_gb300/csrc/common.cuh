@@ -76,6 +76,9 @@ struct IsaacsConsts {
     // float copies of the off-diagonal entries of am (index 1..4 used).
     float amf[kCodes][5];
     float kappa_f;        // kappa rounded to float
+    // Factored Shapley rows: mu w0 (no-drift weight), mu delta (half-drift
+    // weight), 0.1 kappa (reward per unit of a - b).
+    double w0mu, gmu, c01;
 };
 
 // Device-side scalars: reductions written by kernels, read by the host once

@@ -58,31 +58,35 @@ __device__ __forceinline__ int warp_isum(int v) {
     return v;
 }
 
-// F(v; x, a, b) = mu sum_y p(y|x,a,b) v(y) + r(x,a,b) for the stencil of (a, b).
+// Shapley rows of the Isaacs game, factored.  With S the sum of the four
+// neighbour values, w0 = 1/(2 c0) the weight of a direction without drift and
+// delta = h/(2 c0) the extra weight of half a unit of drift, the drift
+// (e_a - e_b)/2 puts delta on direction a and on the direction opposite to b
+// (both on a when b is opposite to a), and a == b puts 2 delta on x itself:
+//   F(v; x, a, b) = base + A_a + T_b            (a != b)
+//   F(v; x, a, a) = base + 2 g v(x)
+// with g = mu delta, base = mu w0 S + r0(x), A_a = g v(x + e_a) + c a,
+// T_b = g v(x - e_b) - c b and c = 0.1 (1 - mu).  For fixed a, F(v; x, a, .)
+// is base + A_a + u_b with u_b = T_b (b != a) and u_a = 2 g v(x) - A_a, so the
+// argmin over b and the keep-current test compare the u_b.
 struct Nbr {
     double vE, vW, vN, vS, vx;
 };
-__device__ __forceinline__ double shapley_ab(const IsaacsConsts* K, const Nbr& nb, double r0,
-                                             int a, int b) {
-    const double* p = K->p[4 * a + b];
-    const double s = p[0] * nb.vE + p[1] * nb.vW + p[2] * nb.vN + p[3] * nb.vS + p[4] * nb.vx;
-    return K->mu * s + (r0 + K->dr[a][b]);
-}
 
 // MIN's reply at fixed a with the keep-current rule: returns the new b and
 // sets *fmin to min_b F(v; x, a, b).
-__device__ __forceinline__ int reply_b(const IsaacsConsts* K, const Nbr& nb, double r0, int a,
+__device__ __forceinline__ int reply_b(const double T[4], double A, double D, double base, int a,
                                        int bcur, double tau, double* fmin) {
-    double F[4];
+    double u[4];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) F[b] = shapley_ab(K, nb, r0, a, b);
-    double m = F[0];
+    for (int b = 0; b < 4; ++b) u[b] = (b == a) ? D - A : T[b];
+    double m = u[0];
     int first = 0;
 #pragma unroll
     for (int b = 1; b < 4; ++b)
-        if (F[b] < m) { m = F[b]; first = b; }
-    *fmin = m;
-    return (F[bcur] - m > tau) ? first : bcur;
+        if (u[b] < m) { m = u[b]; first = b; }
+    *fmin = base + A + m;
+    return (u[bcur] - m > tau) ? first : bcur;
 }
 
 template <int MODE>
@@ -90,7 +94,7 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
                                  const double* __restrict__ v, const double* __restrict__ r0,
                                  uint8_t* __restrict__ alpha, uint32_t* __restrict__ beta,
                                  uint8_t* __restrict__ code, double* __restrict__ rhs,
-                                 double* __restrict__ fv, DevScalars* sc) {
+                                 double* __restrict__ fv, DevScalars* sc, double tau_host) {
     const size_t n = (size_t)side * side;
     const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = x < n;
@@ -98,7 +102,9 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
     int changed = 0, code_changed = 0;
     if (active) {
         const int i = (int)(x % side), j = (int)(x / side);
-        const double tau = 1e-13 * fmax(1.0, __longlong_as_double((long long)sc->vmax));
+        const double tau = tau_host >= 0.0
+                               ? tau_host
+                               : 1e-13 * fmax(1.0, __longlong_as_double((long long)sc->vmax));
         Nbr nb;
         nb.vx = v[x];
         nb.vE = i + 1 < side ? v[x + 1] : 0.0;
@@ -106,6 +112,13 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
         nb.vN = j + 1 < side ? v[x + side] : 0.0;
         nb.vS = j > 0 ? v[x - side] : 0.0;
         const double rx = r0[x];
+        const double g = K->gmu, c = K->c01;
+        const double base = K->w0mu * (nb.vE + nb.vW + nb.vN + nb.vS) + rx;
+        const double D = 2.0 * g * nb.vx;
+        // T_b = g v(x - e_b) - c b for b = +x1, -x1, +x2, -x2
+        const double T[4] = {g * nb.vW, g * nb.vE - c, g * nb.vS - 2.0 * c, g * nb.vN - 3.0 * c};
+        // A_a = g v(x + e_a) + c a
+        const double A[4] = {g * nb.vE, g * nb.vW + c, g * nb.vN + 2.0 * c, g * nb.vS + 3.0 * c};
         const int acur = alpha[x];
         const uint32_t bw = beta[x];
         uint32_t bnew = bw;
@@ -114,7 +127,7 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
             if (acur < 4) {
                 const int bc = (bw >> (8 * acur)) & 0xff;
                 double fmin;
-                const int b = reply_b(K, nb, rx, acur, bc, tau, &fmin);
+                const int b = reply_b(T, A[acur], D, base, acur, bc, tau, &fmin);
                 if (b != bc) {
                     changed = 1;
                     bnew = (bw & ~(0xffu << (8 * acur))) | ((uint32_t)b << (8 * acur));
@@ -125,7 +138,7 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const int bc = (bw >> (8 * a)) & 0xff;
-                const int b = reply_b(K, nb, rx, a, bc, tau, &Fa[a]);
+                const int b = reply_b(T, A[a], D, base, a, bc, tau, &Fa[a]);
                 bnew = (bnew & ~(0xffu << (8 * a))) | ((uint32_t)b << (8 * a));
             }
             const int m1 = variant == 1 ? 5 : 4;
@@ -254,19 +267,19 @@ void launch_isaacs_r0(const IsaacsConsts* K, int side, double kappa, NoiseSrc ns
 
 void launch_isaacs_improve(ImproveMode mode, const IsaacsConsts* K, int side, int variant,
                            const double* v, const double* r0, uint8_t* alpha, uint32_t* beta,
-                           uint8_t* code, double* rhs, double* fv, DevScalars* sc,
+                           uint8_t* code, double* rhs, double* fv, DevScalars* sc, double tau,
                            cudaStream_t st) {
     const size_t n = (size_t)side * side;
     const unsigned g = div_up(n, kBlock);
     switch (mode) {
     case IMP_OUTER:
-        k_isaacs_improve<IMP_OUTER><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc);
+        k_isaacs_improve<IMP_OUTER><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc, tau);
         break;
     case IMP_INNER:
-        k_isaacs_improve<IMP_INNER><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc);
+        k_isaacs_improve<IMP_INNER><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc, tau);
         break;
     default:
-        k_isaacs_improve<IMP_REPLY><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc);
+        k_isaacs_improve<IMP_REPLY><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc, tau);
     }
     GS_CHECK_LAUNCH();
 }

@@ -25,9 +25,10 @@ enum ImproveMode { IMP_OUTER = 0, IMP_INNER = 1, IMP_REPLY = 2 };
 // per state: beta(x, a) for a = 0..3) are read and updated in place according
 // to the mode; code/rhs receive the policy-fixed row codes and right-hand
 // side r^{alpha beta} (assembly, Eq. (LSPI)); fv (may be null) receives F(v).
+// tau >= 0 is the keep-current tolerance; tau < 0 takes 1e-13 max(1, sc->vmax).
 void launch_isaacs_improve(ImproveMode mode, const IsaacsConsts* K, int side, int variant,
                            const double* v, const double* r0, uint8_t* alpha, uint32_t* beta,
-                           uint8_t* code, double* rhs, double* fv, DevScalars* sc,
+                           uint8_t* code, double* rhs, double* fv, DevScalars* sc, double tau,
                            cudaStream_t st);
 
 // Assembly only: code/rhs from alpha and beta.

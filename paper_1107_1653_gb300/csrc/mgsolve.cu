@@ -465,6 +465,7 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_cycles(const __grid_constant_
                 a.out->cycles = cycles;
                 a.out->reason = reason;
                 a.out->res = res;
+                a.out->vmax_final = vm;
             }
             return;
         }

@@ -34,6 +34,7 @@ struct SolveOut {
     int cycles;
     int reason;                   // 1 tolerance or float64 floor, 2 relative drop, 3 cycle cap
     double res;                   // final |b - A v|_inf
+    double vmax_final;            // |v|_inf at the final residual evaluation
 };
 
 struct SolveArgs {

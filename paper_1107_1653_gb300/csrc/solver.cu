@@ -183,6 +183,9 @@ IsaacsConsts make_isaacs_consts(int side, int variant, int mu_mode) {
     for (int c = 0; c < kCodes; ++c)
         for (int d = 0; d < 5; ++d) K.amf[c][d] = (float)K.am[c][d];
     K.kappa_f = (float)K.kappa;
+    K.w0mu = K.mu * (0.5 / c0);
+    K.gmu = K.mu * (h / (2.0 * c0));
+    K.c01 = 0.1 * K.kappa;
     return K;
 }
 
@@ -385,6 +388,10 @@ bool need_setup(const gs_solver* s, const IsaacsGrid& g) {
     return (double)g.stale_rows > s->opt.setup_reuse * (double)g.n;
 }
 
+// Keep-current tolerance 1e-13 max(1, |v|_inf) with |v|_inf from the last
+// multigrid solve's final residual evaluation (v has not changed since).
+double tie_tol(const gs_solver* s) { return 1e-13 * std::max(1.0, s->mgh->out.vmax_final); }
+
 void vmax_to_device(gs_solver* s, IsaacsGrid& g) {
     clear_scalars(s);
     launch_absmax(g.v, g.n, &s->dsc->vmax, s->st);
@@ -399,7 +406,7 @@ bool amgpi(gs_solver* s, IsaacsGrid& g, double eps, bool beta_given, Counters& c
         vmax_to_device(s, g);
         KScope ks(s, GS_K_IMPROVE);
         launch_isaacs_improve(IMP_REPLY, g.Kd, g.side, g.variant, g.v, g.r0, g.alpha, g.beta,
-                              g.code, g.rhs, nullptr, s->dsc, st);
+                              g.code, g.rhs, nullptr, s->dsc, -1.0, st);
     } else {
         launch_isaacs_assemble(g.Kd, g.side, g.alpha, g.beta, g.r0, g.code, g.rhs, st);
     }
@@ -407,10 +414,10 @@ bool amgpi(gs_solver* s, IsaacsGrid& g, double eps, bool beta_given, Counters& c
     int outer = 0;
     while (true) {
         auto inner_improve = [&]() {
-            vmax_to_device(s, g);
+            clear_scalars(s);
             KScope ks(s, GS_K_IMPROVE);
             launch_isaacs_improve(IMP_INNER, g.Kd, g.side, g.variant, g.v, g.r0, g.alpha, g.beta,
-                                  g.code, g.rhs, nullptr, s->dsc, st);
+                                  g.code, g.rhs, nullptr, s->dsc, tie_tol(s), st);
             const DevScalars& h = read_scalars(s);
             g.stale_rows += h.code_changed;
             return h.changed;
@@ -428,11 +435,11 @@ bool amgpi(gs_solver* s, IsaacsGrid& g, double eps, bool beta_given, Counters& c
             break;
         }
         ++outer;
-        vmax_to_device(s, g);
+        clear_scalars(s);
         {
             KScope ks(s, GS_K_IMPROVE);
             launch_isaacs_improve(IMP_OUTER, g.Kd, g.side, g.variant, g.v, g.r0, g.alpha, g.beta,
-                                  g.code, g.rhs, g.fv, s->dsc, st);
+                                  g.code, g.rhs, g.fv, s->dsc, tie_tol(s), st);
         }
         const DevScalars& h = read_scalars(s);
         g.stale_rows += h.code_changed;
@@ -552,7 +559,7 @@ gs_status run_improve(gs_solver* s, const double* v, uint8_t* alpha_out, uint8_t
     clear_scalars(s);
     launch_absmax(vd, g.n, &s->dsc->vmax, s->st);
     launch_isaacs_improve(IMP_OUTER, g.Kd, g.side, g.variant, vd, g.r0, a, b, code, rhs, fv, s->dsc,
-                          s->st);
+                          -1.0, s->st);
     if (alpha_out) GS_CUDA(cudaMemcpyAsync(alpha_out, a, g.n, cudaMemcpyDefault, s->st));
     if (fv_out) GS_CUDA(cudaMemcpyAsync(fv_out, fv, g.n * sizeof(double), cudaMemcpyDefault, s->st));
     if (beta_out) {
