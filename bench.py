@@ -29,6 +29,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Isaacs solves/s at 1023^2 (FP32+refine vs FP64), HBM GB/s, p50/p99 latency"
+# arithmetic types per precision option: float64; float32 V-cycles in float64
+# refinement; the same with the V-cycle weights stored in bfloat16
+DTYPES = {"fp64": "f64", "mixed": "f32+f64", "mixed_bf16": "bf16(weights)+f32+f64"}
 SIDE = 1023          # the metric's workload; --side changes it (e.g. 2047 for profiling)
 SEED = 2
 
@@ -43,10 +46,17 @@ def mg_bytes_per_state(prec: str):
         coarse1 = 2 * (72 + 24) + (72 + 16 + 16 + 4) + 34
         setup = (2 + 32 + 1 + 32 + 32 + 4 + 64 + 72) / 4 + (72 + (32 + 32 + 64 + 72) / 4) / 3
     else:
+        # float32 vectors; weights in float32 (mixed) or bfloat16 (mixed_bf16):
+        # A = 9 stored entries per coarse point, P = 8 weights per coarse cell
+        # (2 bytes per fine point in float32), each written beside its float64 master
+        wb = 2 if prec == "mixed_bf16" else 4
+        A, Pf = 9 * wb, 2 * wb
         check = 1 + 8 + 8 + 4                          # + float32 residual written
-        fine = 2 * (1 + 4 + 4 + 4) + (1 + 4 + 4 + 8 + 2) + (8 + 1 + 8) + (4 + 16)
-        coarse1 = 2 * (36 + 12) + (36 + 8 + 8 + 2) + 17
-        setup = (2 + 48 + 1 + 32 + 48 + 4 + 64 + 108) / 4 + (72 + (48 + 48 + 64 + 108) / 4) / 3
+        fine = 2 * (1 + 4 + 4 + 4) + (1 + 4 + 4 + Pf + 2) + (Pf + 1 + 8) + (4 + 16)
+        coarse1 = 2 * (A + 12) + (A + 8 + Pf + 2) + (Pf + 1 + 8)
+        Pe = 32 + 4 * wb                               # 4 edge (or corner) weights, both copies
+        Ac = 72 + A                                    # Galerkin row, both copies
+        setup = (2 + Pe + 1 + 32 + Pe + 4 + 64 + Ac) / 4 + (72 + (Pe + Pe + 64 + Ac) / 4) / 3
     cycle = fine + coarse1 / 4 * 4 / 3
     return {"check": check, "cycle": cycle, "setup": setup}
 
@@ -237,7 +247,7 @@ def run_batch(args):
         "metric": "random games solved/s (batch of 4096, n~U{256..8192})", "value": count / sec,
         "unit": "games/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64",
+        "vs_baseline": None, "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": "random_games_batch4096", "games": count, "states": n_tot,
                    "nnz": nnz, "seed": seed, "precision": args.precision,
@@ -414,17 +424,26 @@ def run_ours(args):
     ms_max = float(ms_t.item())
     value = world * 1000.0 / ms_max
 
-    # the other precision, for the FP32+refine vs FP64 comparison
-    other = "fp64" if prec != "fp64" else "mixed"
-    o_steps, o_stats, _, _, v_other, _ = timed(other, max(2, args.steps // 2), 1)
-    o_ms = statistics.mean(o_steps)
-    rel = float(np.max(np.abs(v_main - v_other)) / np.max(np.abs(v_other)))
+    # the other precisions, for the FP32+refine vs FP64 comparison: each one's
+    # time and counts, and every result's relative distance from the FP64 value
+    compare, values = {}, {prec: v_main}
+    for other in ("fp64", "mixed", "mixed_bf16"):
+        if other == prec:
+            continue
+        o_steps, o_stats, _, _, values[other], _ = timed(other, max(2, args.steps // 2), 1)
+        o_ms = statistics.mean(o_steps)
+        compare[other] = {"value": 1000.0 / o_ms, "ms_per_step": o_ms, "outer": o_stats["outer"],
+                          "systems": o_stats["systems"], "cycles": o_stats["cycles"]}
+    v64 = values["fp64"]
+    for k, v in values.items():
+        if k != "fp64":
+            compare["rel_diff_" + k + "_vs_fp64"] = float(np.max(np.abs(v - v64)) / np.max(np.abs(v64)))
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if prec != "fp64" else "f64", "data": "synthetic",
+        "dtype": DTYPES[prec], "data": "synthetic",
         "config": {"workload": f"isaacs_{SIDE}x{SIDE}_plain_{'famgpi' if args.fmg else 'amgpi'}_{prec}",
                    "side": SIDE, "states": n, "seed": SEED, "variant": "plain",
                    "precision": prec, "fmg": bool(args.fmg),
@@ -436,10 +455,7 @@ def run_ours(args):
         "p99_ms": sorted(per_step)[min(len(per_step) - 1, int(0.99 * len(per_step)))],
         "wall_s_timed_loop": t_wall,
         "gpu_launches": int(launches),
-        "compare": {other: {"value": 1000.0 / o_ms, "ms_per_step": o_ms,
-                            "outer": o_stats["outer"], "systems": o_stats["systems"],
-                            "cycles": o_stats["cycles"]},
-                    "rel_diff_vs_" + other: rel},
+        "compare": compare,
     }
     if clk:
         line["clocks"] = clk
@@ -447,7 +463,7 @@ def run_ours(args):
     # roofline of the dominant kernel: the V-cycle launch (one or two per system)
     peak, peak_kind = load_peaks()
     if tr_n:
-        kind = "mixed" if prec != "fp64" else "fp64"
+        kind = prec
         total = mg_cycle_bytes(n, kind, tr_n, stats["cycles"] * args.steps)
         bpl = total / tr_n
         avg_s = tr_ms * 1e-3 / tr_n
@@ -457,7 +473,8 @@ def run_ours(args):
                             "peak_source": peak_kind, "traffic": None,
                             "launches": tr_n, "avg_us": avg_s * 1e6,
                             "algorithmic_bytes_per_launch": bpl,
-                            "note": "working set fits in L2 (129 MB); bytes per state "
+                            "note": ("working set fits in L2 (129 MB)" if SIDE <= 1023 else
+                                     "working set exceeds the 129 MB L2") + "; bytes per state "
                                     + json.dumps({k: round(v, 1) for k, v in
                                                   mg_bytes_per_state(kind).items()})}
 

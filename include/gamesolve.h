@@ -50,7 +50,12 @@ typedef enum {
 typedef enum {
     GS_PREC_FP64 = 0,        /* every step in float64 */
     GS_PREC_MIXED = 1,       /* float32 V-cycles inside float64 iterative refinement */
-    GS_PREC_MIXED_BF16 = 2   /* reserved: bfloat16 weight storage (not built; rejected) */
+    GS_PREC_MIXED_BF16 = 2   /* as MIXED, with the V-cycle's coarse operators and
+                                interpolation weights (Isaacs grids) or the transition
+                                probabilities (finite games) stored in bfloat16; the
+                                arithmetic stays float32, and residuals, Galerkin
+                                products, the coarsest solve and the improvement stay
+                                float64, so the result meets the same float64 floor */
 } gs_precision;
 
 /* Solver options.  Fill with gamesolve_default_options, then override. */

@@ -87,7 +87,7 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
     gs_options o;
     if (opt) o = *opt;
     else gamesolve_default_options(&o);
-    if (o.precision < GS_PREC_FP64 || o.precision > GS_PREC_MIXED || o.max_outer < 1 || o.max_inner < 1 || o.nu1 < 0 ||
+    if (o.precision < GS_PREC_FP64 || o.precision > GS_PREC_MIXED_BF16 || o.max_outer < 1 || o.max_inner < 1 || o.nu1 < 0 ||
         o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 1 || !(o.lin_tol >= 0) ||
         o.coarse_max < 1 || o.coarse_max > 64 || o.tail_side < 0 || !(o.eps >= 0) || !(o.fmg_c > 0) ||
         (o.fmg && !is_pow2m1(o.fmg_side)) || o.mu_mode < 0 || o.mu_mode > 1 ||

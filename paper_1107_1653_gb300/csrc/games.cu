@@ -54,10 +54,10 @@ __global__ void k_game_validate(GameTables T, int count, const int64_t* __restri
     }
 }
 
-// Per row: leakage 1 - mu sum_k p_k (float64) and the float32 copy of p.
+// Per row: leakage 1 - mu sum_k p_k (float64) and the float32 or bfloat16 copy of p.
 __global__ void k_game_prepare(GameTables T, int count, const int64_t* __restrict__ st_off,
                                const double* __restrict__ mu, double* __restrict__ leak,
-                               float* __restrict__ prob32) {
+                               float* __restrict__ prob32, __nv_bfloat16* __restrict__ prob16) {
     const int64_t R = (int64_t)T.m1 * T.m2;
     const int64_t rows = st_off[count] * R;
     for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
@@ -72,7 +72,8 @@ __global__ void k_game_prepare(GameTables T, int count, const int64_t* __restric
         double sum = 0.0;
         for (int64_t k = T.row_ptr[row]; k < T.row_ptr[row + 1]; ++k) {
             sum += T.prob[k];
-            prob32[k] = (float)T.prob[k];
+            if (prob16) prob16[k] = __double2bfloat16(T.prob[k]);
+            else prob32[k] = (float)T.prob[k];
         }
         leak[row] = 1.0 - mu[lo] * sum;
     }
@@ -173,6 +174,13 @@ __device__ int improve_state(const Game& G, const BatchOut& O, int mode, int64_t
     return changed;
 }
 
+// Transition probability k in the relaxation's precision.
+template <typename T>
+__device__ __forceinline__ T prob_at(const GameTables& tb, int64_t k) {
+    if constexpr (sizeof(T) == 8) return tb.prob[k];
+    else return tb.prob16 ? __bfloat162float(tb.prob16[k]) : tb.prob32[k];
+}
+
 // (A e)_i and the diagonal of A = I - mu M for the selected row, leakage form:
 // (A e)_i = s_i e_i + mu sum_k p_k (e_i - e_col), s_i = 1 - mu sum_k p_k.
 template <typename T>
@@ -184,7 +192,7 @@ __device__ __forceinline__ void apply_row(const Game& G, const BatchOut& O, int6
     T acc = (T)G.T.leak[row] * ei, off = 0;
     for (int64_t k = G.T.row_ptr[row]; k < G.T.row_ptr[row + 1]; ++k) {
         const int32_t c = G.T.col[k];
-        const T p = sizeof(T) == 4 ? (T)G.T.prob32[k] : (T)G.T.prob[k];
+        const T p = prob_at<T>(G.T, k);
         acc += mu * p * (ei - e[c]);
         if (c != i) off += mu * p;
     }
@@ -198,7 +206,7 @@ __device__ __forceinline__ T diag_row(const Game& G, const BatchOut& O, int64_t 
     const int64_t row = O.sel[G.x0 + i];
     T off = 0;
     for (int64_t k = G.T.row_ptr[row]; k < G.T.row_ptr[row + 1]; ++k)
-        if (G.T.col[k] != i) off += (T)G.mu * (sizeof(T) == 4 ? (T)G.T.prob32[k] : (T)G.T.prob[k]);
+        if (G.T.col[k] != i) off += (T)G.mu * prob_at<T>(G.T, k);
     return (T)G.T.leak[row] + off;
 }
 
@@ -479,9 +487,10 @@ void launch_game_validate(const GameTables& T, int count, const int64_t* st_off,
 }
 
 void launch_game_prepare(const GameTables& T, int count, const int64_t* st_off, int64_t rows,
-                         const double* mu, double* leak, float* prob32, cudaStream_t st) {
+                         const double* mu, double* leak, float* prob32, __nv_bfloat16* prob16,
+                         cudaStream_t st) {
     const unsigned g = (unsigned)std::min<int64_t>((rows + 255) / 256, 152 * 32);
-    k_game_prepare<<<std::max(1u, g), 256, 0, st>>>(T, count, st_off, mu, leak, prob32);
+    k_game_prepare<<<std::max(1u, g), 256, 0, st>>>(T, count, st_off, mu, leak, prob32, prob16);
     GS_CHECK_LAUNCH();
 }
 

@@ -1,6 +1,8 @@
 // Finite games given by CSR transition tables: device-side argument blocks.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "gridsync.cuh"
 
 namespace gs {
@@ -13,7 +15,8 @@ struct GameTables {
     const int64_t* row_ptr;   // total rows + 1 (global nnz offsets)
     const int32_t* col;
     const double* prob;
-    const float* prob32;      // float32 copy (relaxation)
+    const float* prob32;      // float32 copy (relaxation; null with bfloat16 storage)
+    const __nv_bfloat16* prob16;   // bfloat16 copy (relaxation; null unless chosen)
     const double* rew;        // per row
     const double* leak;       // per row: 1 - mu sum_k p_k
 };
@@ -58,8 +61,11 @@ constexpr int kGameMaxStatesFP64 = 8192;
 
 void launch_game_validate(const GameTables& T, int count, const int64_t* st_off, int64_t rows,
                           int* bad, cudaStream_t st);
+// Writes the leakage per row and the rounded copy of p (float32 into prob32, or
+// bfloat16 into prob16: exactly one of them is non-null).
 void launch_game_prepare(const GameTables& T, int count, const int64_t* st_off, int64_t rows,
-                         const double* mu, double* leak, float* prob32, cudaStream_t st);
+                         const double* mu, double* leak, float* prob32, __nv_bfloat16* prob16,
+                         cudaStream_t st);
 size_t games_smem_bytes(int max_n, bool mixed);
 void launch_games_pi(const BatchArgs& B, bool mixed, cudaStream_t st);
 // Thread blocks for the grid-wide kernel on a game of n states (cap > 0 limits them).

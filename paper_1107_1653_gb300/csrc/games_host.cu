@@ -67,6 +67,7 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
     G->rows = rows;
     G->nnz = nnz;
     G->max_n = (int)max_n;
+    G->prob_bf16 = s->opt.precision == GS_PREC_MIXED_BF16;
     G->st_off_h = off;
     Arena& ar = P->arena;
     G->st_off = ar.alloc<int64_t>(count + 1);
@@ -114,7 +115,9 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
                        bad & 8 ? "row sum above 1 " : "", bad & 16 ? "reward not finite" : "");
         throw Error{GS_EINVAL};
     }
-    launch_game_prepare(T, count, G->st_off, rows, G->mu, G->leak, G->prob32, st);
+    launch_game_prepare(T, count, G->st_off, rows, G->mu, G->leak,
+                        G->prob_bf16 ? nullptr : G->prob32,
+                        G->prob_bf16 ? (__nv_bfloat16*)G->prob32 : nullptr, st);
     GS_CUDA(cudaStreamSynchronize(st));
     P->game = std::move(G);
     return P;

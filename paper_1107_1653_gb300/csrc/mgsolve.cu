@@ -87,9 +87,9 @@ __device__ void relax_fine_update(const L0Op<float>& op, const LevelArgs& L, dou
     }
 }
 
-template <typename T>
+template <typename T, typename W>
 __device__ void relax_coarse(const LevelArgs& L, int c, bool zero, size_t start, size_t stride) {
-    const L9Op<T> op{(const T*)L.A, L.n, L.side};
+    const L9Op<T, W> op{(const W*)L.A, L.n, L.side};
     T* u = (T*)L.u;
     const T* f = (const T*)L.f;
     const int ox = colour_ox(c), oy = colour_oy(c);
@@ -101,13 +101,13 @@ __device__ void relax_coarse(const LevelArgs& L, int c, bool zero, size_t start,
 
 // f_{l+1} = R (f_l - A_l u_l) with the fine residuals formed on the fly;
 // u_{l+1} = 0.
-template <typename T, class Op>
+template <typename T, typename W, class Op>
 __device__ void restrict_with(const Op& op, const LevelArgs& L, const LevelArgs& C, size_t start,
                               size_t stride) {
     const int sc = L.sc;
     const T* u = (const T*)L.u;
     const T* f = (const T*)L.f;
-    const T* P = (const T*)L.P;
+    const W* P = (const W*)L.P;
     T* fc = (T*)C.f;
     T* uc = (T*)C.u;
     const size_t nc = (size_t)sc * sc;
@@ -118,7 +118,7 @@ __device__ void restrict_with(const Op& op, const LevelArgs& L, const LevelArgs&
         for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
             for (int di = -1; di <= 1; ++di) {
-                acc += restrict_weight(P, sc, I, J, di, dj) * op.resid(f, u, 2 * I + 1 + di, 2 * J + 1 + dj);
+                acc += (T)restrict_weight(P, sc, I, J, di, dj) * op.resid(f, u, 2 * I + 1 + di, 2 * J + 1 + dj);
             }
         fc[t] = acc;
         uc[t] = T(0);
@@ -126,11 +126,12 @@ __device__ void restrict_with(const Op& op, const LevelArgs& L, const LevelArgs&
 }
 
 // u_l += P u_{l+1}, one item per coarse cell (its corner, edge and C points).
-template <typename T>
+template <typename T, typename W>
 __device__ void prolong_phase(const LevelArgs& L, const LevelArgs& C, size_t start, size_t stride) {
     const int sc = L.sc, sf = L.side, nc1 = sc + 1;
     const size_t ncell = (size_t)nc1 * nc1;
-    const T* P = (const T*)L.P;
+    const W* Pw = (const W*)L.P;
+    auto P = [&](int k, size_t c) -> T { return (T)wval(Pw[k * ncell + c]); };
     const T* uc = (const T*)C.u;
     T* uf = (T*)L.u;
     for (size_t t = start; t < ncell; t += stride) {
@@ -139,29 +140,27 @@ __device__ void prolong_phase(const LevelArgs& L, const LevelArgs& C, size_t sta
             return (p < 0 || q < 0 || p >= sc || q >= sc) ? T(0) : uc[(size_t)q * sc + p];
         };
         const T uSW = U(I - 1, J - 1), uSE = U(I, J - 1), uNW = U(I - 1, J), uNE = U(I, J);
-        uf[(size_t)(2 * J) * sf + 2 * I] += P[PSW * ncell + t] * uSW + P[PSE * ncell + t] * uSE +
-                                            P[PNW * ncell + t] * uNW + P[PNE * ncell + t] * uNE;
-        if (J < sc)
-            uf[(size_t)(2 * J + 1) * sf + 2 * I] += P[PXW * ncell + t] * uNW + P[PXE * ncell + t] * uNE;
-        if (I < sc)
-            uf[(size_t)(2 * J) * sf + 2 * I + 1] += P[PYS * ncell + t] * uSE + P[PYN * ncell + t] * uNE;
+        uf[(size_t)(2 * J) * sf + 2 * I] += P(PSW, t) * uSW + P(PSE, t) * uSE + P(PNW, t) * uNW +
+                                            P(PNE, t) * uNE;
+        if (J < sc) uf[(size_t)(2 * J + 1) * sf + 2 * I] += P(PXW, t) * uNW + P(PXE, t) * uNE;
+        if (I < sc) uf[(size_t)(2 * J) * sf + 2 * I + 1] += P(PYS, t) * uSE + P(PYN, t) * uNE;
         if (I < sc && J < sc) uf[(size_t)(2 * J + 1) * sf + 2 * I + 1] += uNE;
     }
 }
 
 // Level-generic wrappers (level 0 is the implicit fine operator).
-template <typename T>
+template <typename T, typename W>
 __device__ void relax_level(const SolveArgs& a, const LevelArgs& L, int l, int c, bool zero,
                             size_t start, size_t stride) {
     if (l == 0) relax_fine<T>(L0Op<T>{a.K, a.code, L.side}, L, c, zero, start, stride);
-    else relax_coarse<T>(L, c, zero, start, stride);
+    else relax_coarse<T, W>(L, c, zero, start, stride);
 }
 
-template <typename T>
+template <typename T, typename W>
 __device__ void restrict_level(const SolveArgs& a, const LevelArgs& L, const LevelArgs& C, int l,
                                size_t start, size_t stride) {
-    if (l == 0) restrict_with<T>(L0Op<T>{a.K, a.code, L.side}, L, C, start, stride);
-    else restrict_with<T>(L9Op<T>{(const T*)L.A, L.n, L.side}, L, C, start, stride);
+    if (l == 0) restrict_with<T, W>(L0Op<T>{a.K, a.code, L.side}, L, C, start, stride);
+    else restrict_with<T, W>(L9Op<T, W>{(const W*)L.A, L.n, L.side}, L, C, start, stride);
 }
 
 // Exact solve on the coarsest level by its explicit inverse (one block).
@@ -183,7 +182,7 @@ __device__ void coarse_apply_block(const LevelArgs& L, const double* inv) {
 
 // V-cycle over levels [lbeg, nlev) by thread block 0 alone, on the level
 // descriptors `tl` (shared-memory copies of the levels >= a.smem_from).
-template <typename T>
+template <typename T, typename W>
 __device__ void block_vcycle(const SolveArgs& a, const LevelArgs* tl, const double* inv, int lbeg,
                              bool first_zero) {
     const size_t s0 = threadIdx.x, st = blockDim.x;
@@ -204,20 +203,20 @@ __device__ void block_vcycle(const SolveArgs& a, const LevelArgs* tl, const doub
         const bool z = l > lbeg || first_zero;
         for (int k = 0; k < a.nu1; ++k)
             for (int c = 0; c < ncol; ++c) {
-                relax_level<T>(a, tl[l], l, c, z && k == 0 && c == 0, s0, st);
+                relax_level<T, W>(a, tl[l], l, c, z && k == 0 && c == 0, s0, st);
                 __syncthreads();
             }
-        restrict_level<T>(a, tl[l], tl[l + 1], l, s0, st);
+        restrict_level<T, W>(a, tl[l], tl[l + 1], l, s0, st);
         __syncthreads();
     }
     coarse_apply_block<T>(tl[Lc], inv);
     for (int l = Lc - 1; l >= lbeg; --l) {
         const int ncol = l == 0 ? 2 : 4;
-        prolong_phase<T>(tl[l], tl[l + 1], s0, st);
+        prolong_phase<T, W>(tl[l], tl[l + 1], s0, st);
         __syncthreads();
         for (int k = 0; k < a.nu2; ++k)
             for (int c = 0; c < ncol; ++c) {
-                relax_level<T>(a, tl[l], l, c, false, s0, st);
+                relax_level<T, W>(a, tl[l], l, c, false, s0, st);
                 __syncthreads();
             }
     }
@@ -231,7 +230,7 @@ __device__ void block_vcycle(const SolveArgs& a, const LevelArgs* tl, const doub
 }
 
 // Algorithm 3 with gamma = 1 over the whole hierarchy.
-template <typename T>
+template <typename T, typename W>
 __device__ bool grid_vcycle(const SolveArgs& a, const LevelArgs* tl, const double* inv,
                             const GridSync& G, size_t gt, size_t gs, bool fine_zero) {
     for (int l = 0; l < a.tail; ++l) {
@@ -239,20 +238,20 @@ __device__ bool grid_vcycle(const SolveArgs& a, const LevelArgs* tl, const doubl
         const bool z = l > 0 || fine_zero;
         for (int k = 0; k < a.nu1; ++k)
             for (int c = 0; c < ncol; ++c) {
-                relax_level<T>(a, a.L[l], l, c, z && k == 0 && c == 0, gt, gs);
+                relax_level<T, W>(a, a.L[l], l, c, z && k == 0 && c == 0, gt, gs);
                 if (!G.sync()) return false;
                 prof_mark(1000 + 10 * l + c);
             }
-        restrict_level<T>(a, a.L[l], a.L[l + 1], l, gt, gs);
+        restrict_level<T, W>(a, a.L[l], a.L[l + 1], l, gt, gs);
         if (!G.sync()) return false;
         prof_mark(2000 + 10 * l);
     }
-    if (blockIdx.x == 0) block_vcycle<T>(a, tl, inv, a.tail, a.tail > 0 ? true : fine_zero);
+    if (blockIdx.x == 0) block_vcycle<T, W>(a, tl, inv, a.tail, a.tail > 0 ? true : fine_zero);
     if (!G.sync()) return false;
     prof_mark(4000);
     for (int l = a.tail - 1; l >= 0; --l) {
         const int ncol = l == 0 ? 2 : 4;
-        prolong_phase<T>(a.L[l], a.L[l + 1], gt, gs);
+        prolong_phase<T, W>(a.L[l], a.L[l + 1], gt, gs);
         if (!G.sync()) return false;
         prof_mark(3000 + 10 * l);
         for (int k = 0; k < a.nu2; ++k)
@@ -265,7 +264,7 @@ __device__ bool grid_vcycle(const SolveArgs& a, const LevelArgs* tl, const doubl
                         continue;
                     }
                 }
-                relax_level<T>(a, a.L[l], l, c, false, gt, gs);
+                relax_level<T, W>(a, a.L[l], l, c, false, gt, gs);
                 if (!G.sync()) return false;
                 prof_mark(1000 + 10 * l + c);
             }
@@ -278,27 +277,27 @@ __device__ bool grid_vcycle(const SolveArgs& a, const LevelArgs* tl, const doubl
 __device__ void setup_items(const SolveArgs& a, int l, int kind, size_t start, size_t stride) {
     const LevelArgs& L = a.L[l];
     const int sc = L.sc;
-    float* P32 = a.mixed ? L.P32 : nullptr;
+    const WOut Pw{a.mixed && !a.wbf16 ? L.P32 : nullptr, a.wbf16 ? (__nv_bfloat16*)L.P32 : nullptr};
     if (kind < 2) {
         const size_t ncell = (size_t)(sc + 1) * (sc + 1);
         for (size_t t = start; t < ncell; t += stride) {
             if (l == 0) {
                 const Src5 src{a.K, a.code, L.side};
-                if (kind == 0) interp_edges_item(src, sc, t, L.P64, P32);
-                else interp_corners_item(src, sc, t, L.P64, P32);
+                if (kind == 0) interp_edges_item(src, sc, t, L.P64, Pw);
+                else interp_corners_item(src, sc, t, L.P64, Pw);
             } else {
                 const Src9 src{L.A64, L.side, L.n};
-                if (kind == 0) interp_edges_item(src, sc, t, L.P64, P32);
-                else interp_corners_item(src, sc, t, L.P64, P32);
+                if (kind == 0) interp_edges_item(src, sc, t, L.P64, Pw);
+                else interp_corners_item(src, sc, t, L.P64, Pw);
             }
         }
     } else {
         const size_t nc = (size_t)sc * sc;
         const LevelArgs& C = a.L[l + 1];
-        float* A32 = a.mixed ? C.A32 : nullptr;
+        const WOut Aw{a.mixed && !a.wbf16 ? C.A32 : nullptr, a.wbf16 ? (__nv_bfloat16*)C.A32 : nullptr};
         for (size_t t = start; t < nc; t += stride) {
-            if (l == 0) rap_item(Src5{a.K, a.code, L.side}, sc, t, L.P64, C.A64, A32);
-            else rap_item(Src9{L.A64, L.side, L.n}, sc, t, L.P64, C.A64, A32);
+            if (l == 0) rap_item(Src5{a.K, a.code, L.side}, sc, t, L.P64, C.A64, Aw);
+            else rap_item(Src9{L.A64, L.side, L.n}, sc, t, L.P64, C.A64, Aw);
         }
     }
 }
@@ -390,7 +389,7 @@ __device__ void axpy_phase(const SolveArgs& a, size_t gt, size_t gs) {
 
 // Copies the tail levels' operators and transfers (fixed during one launch)
 // into block 0's shared memory and builds their descriptors.
-template <typename T>
+template <typename T, typename W>
 __device__ void stage_tail(const SolveArgs& a, char* smem, LevelArgs* tl, double** inv_out) {
     for (int l = threadIdx.x; l < a.nlev; l += blockDim.x) tl[l] = a.L[l];
     __syncthreads();
@@ -403,15 +402,15 @@ __device__ void stage_tail(const SolveArgs& a, char* smem, LevelArgs* tl, double
     };
     for (int l = a.smem_from; l <= Lc; ++l) {
         const LevelArgs& G = a.L[l];
-        T* A = (T*)take(9 * G.n * sizeof(T));
+        W* A = (W*)take(9 * G.n * sizeof(W));
         const size_t ncell = (size_t)(G.sc + 1) * (G.sc + 1);
-        T* P = l < Lc ? (T*)take(8 * ncell * sizeof(T)) : nullptr;
+        W* P = l < Lc ? (W*)take(8 * ncell * sizeof(W)) : nullptr;
         T* u = (T*)take(G.n * sizeof(T));
         T* f = (T*)take(G.n * sizeof(T));
-        const T* gA = (const T*)G.A;
+        const W* gA = (const W*)G.A;
         for (size_t k = threadIdx.x; k < 9 * G.n; k += blockDim.x) A[k] = gA[k];
         if (P) {
-            const T* gP = (const T*)G.P;
+            const W* gP = (const W*)G.P;
             for (size_t k = threadIdx.x; k < 8 * ncell; k += blockDim.x) P[k] = gP[k];
         }
         if (threadIdx.x == 0) {
@@ -427,7 +426,7 @@ __device__ void stage_tail(const SolveArgs& a, char* smem, LevelArgs* tl, double
     __syncthreads();
 }
 
-template <typename T>
+template <typename T, typename W>
 __global__ void __launch_bounds__(kMGThreads) k_mg_cycles(const __grid_constant__ SolveArgs a) {
     extern __shared__ __align__(16) char smem_c[];
     __shared__ LevelArgs tl[kMaxLevels];
@@ -437,7 +436,7 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_cycles(const __grid_constant_
     if (!G.sync()) return;   // set-up complete (and error state shared)
     prof_mark(8000);
     double* inv = a.inv;
-    if (blockIdx.x == 0) stage_tail<T>(a, smem_c, tl, &inv);
+    if (blockIdx.x == 0) stage_tail<T, W>(a, smem_c, tl, &inv);
     int slot = 0;
     check_phase(a, slot, gt, gs);
     if (!G.sync()) return;
@@ -473,7 +472,7 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_cycles(const __grid_constant_
             a.out->rmax[slot ^ 1] = 0ull;
             a.out->vmax[slot ^ 1] = 0ull;
         }
-        if (!grid_vcycle<T>(a, tl, inv, G, gt, gs, a.mixed != 0)) return;
+        if (!grid_vcycle<T, W>(a, tl, inv, G, gt, gs, a.mixed != 0)) return;
         if (a.mixed && (a.tail == 0 || a.nu2 == 0)) {   // not fused into the fine relaxation
             axpy_phase(a, gt, gs);
             if (!G.sync()) return;
@@ -490,7 +489,7 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_cycles(const __grid_constant_
 struct Occupancy {
     int sms = 0;
     int setup_per_sm = 0;
-    int cyc_per_sm[2] = {0, 0};
+    int cyc_per_sm[3] = {0, 0, 0};   // float32, float64, float32 on bfloat16 weights
 };
 
 Occupancy& occupancy() {
@@ -504,14 +503,20 @@ Occupancy& occupancy() {
         const int big = kTailSmemMax;
         GS_CUDA(cudaFuncSetAttribute(k_mg_setup, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      64 * 128 * 8));
-        GS_CUDA(cudaFuncSetAttribute(k_mg_cycles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-        GS_CUDA(cudaFuncSetAttribute(k_mg_cycles<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+        GS_CUDA(cudaFuncSetAttribute(k_mg_cycles<float, float>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+        GS_CUDA(cudaFuncSetAttribute(k_mg_cycles<double, double>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+        GS_CUDA(cudaFuncSetAttribute(k_mg_cycles<float, __nv_bfloat16>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, big));
         GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.setup_per_sm, k_mg_setup, kMGThreads,
                                                               64 * 128 * 8));
-        GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.cyc_per_sm[0], k_mg_cycles<float>,
+        GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.cyc_per_sm[0], k_mg_cycles<float, float>,
                                                               kMGThreads, big));
-        GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.cyc_per_sm[1], k_mg_cycles<double>,
+        GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.cyc_per_sm[1], k_mg_cycles<double, double>,
                                                               kMGThreads, big));
+        GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &o.cyc_per_sm[2], k_mg_cycles<float, __nv_bfloat16>, kMGThreads, big));
         o.setup_per_sm = o.setup_per_sm < 1 ? 1 : o.setup_per_sm;
         for (int& c : o.cyc_per_sm) c = c < 1 ? 1 : c;
     }
@@ -528,14 +533,16 @@ int grid_blocks(const SolveArgs& a, int per_sm, int sms) {
 
 }  // namespace
 
-size_t tail_smem_bytes(const SolveArgs& a, int elem) {
+size_t tail_smem_bytes(const SolveArgs& a) {
+    const int elem = a.mixed ? 4 : 8;
+    const int welem = a.wbf16 ? 2 : elem;
     const int Lc = a.nlev - 1;
     size_t off = 0;
     auto take = [&](size_t bytes) { off += (bytes + 15) & ~size_t(15); };
     for (int l = a.smem_from; l <= Lc; ++l) {
         const LevelArgs& G = a.L[l];
-        take(9 * G.n * elem);
-        if (l < Lc) take(8 * (size_t)(G.sc + 1) * (G.sc + 1) * elem);
+        take(9 * G.n * welem);
+        if (l < Lc) take(8 * (size_t)(G.sc + 1) * (G.sc + 1) * welem);
         take(G.n * elem);
         take(G.n * elem);
     }
@@ -572,10 +579,12 @@ void launch_mg_setup(const SolveArgs& a, cudaStream_t st) {
 void launch_mg_cycles(const SolveArgs& a, cudaStream_t st) {
     const Occupancy& o = occupancy();
     void* args[] = {(void*)&a};
-    const int elem = a.mixed ? 4 : 8;
-    const size_t smem = tail_smem_bytes(a, elem);
-    const void* fn = a.mixed ? (const void*)k_mg_cycles<float> : (const void*)k_mg_cycles<double>;
-    GS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid_blocks(a, o.cyc_per_sm[a.mixed ? 0 : 1], o.sms)),
+    const size_t smem = tail_smem_bytes(a);
+    const int kind = !a.mixed ? 1 : a.wbf16 ? 2 : 0;
+    const void* fn = kind == 1   ? (const void*)k_mg_cycles<double, double>
+                     : kind == 2 ? (const void*)k_mg_cycles<float, __nv_bfloat16>
+                                 : (const void*)k_mg_cycles<float, float>;
+    GS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid_blocks(a, o.cyc_per_sm[kind], o.sms)),
                                         dim3(kMGThreads), args, smem, st));
     note_launches(1);
 }

@@ -19,12 +19,13 @@ struct LevelArgs {
     size_t n;
     void* u;             // V-cycle unknown (float32 in the mixed path, else float64)
     void* f;             // V-cycle right-hand side
-    const void* A;       // V-cycle operator, levels >= 1 (float32 leakage or float64)
+    const void* A;       // V-cycle operator, levels >= 1 (float32/bfloat16 leakage or float64)
     const void* P;       // V-cycle interpolation weights from level + 1
     double* A64;         // Galerkin operator, levels >= 1 (written by the set-up)
-    float* A32;          // its float32 leakage copy (mixed path)
+    float* A32;          // its rounded leakage copy (mixed path: float32, or bfloat16 in
+                         // the first half of the same buffer)
     double* P64;         // interpolation weights (written by the set-up)
-    float* P32;
+    float* P32;          // their rounded copy (float32, or bfloat16 likewise)
 };
 
 
@@ -47,6 +48,7 @@ struct SolveArgs {
     int smem_from;   // levels >= smem_from (>= max(tail, 1)) live in block 0's shared memory
     int nu1, nu2, max_cycles;
     int mixed;       // float32 V-cycles on the float64 residual (iterative refinement)
+    int wbf16;       // mixed path with bfloat16 storage of the V-cycle operators and weights
     int do_setup;    // build interpolation, Galerkin operators and coarse inverse first
     int max_blocks;  // cap on the grid (0 = whole GPU)
     double lin_tol;
@@ -64,7 +66,7 @@ struct SolveArgs {
 void launch_mg_setup(const SolveArgs& a, cudaStream_t st);
 void launch_mg_cycles(const SolveArgs& a, cudaStream_t st);
 
-// Shared memory the tail levels >= a.smem_from need (elem = 4 or 8 bytes).
-size_t tail_smem_bytes(const SolveArgs& a, int elem);
+// Shared memory the tail levels >= a.smem_from need.
+size_t tail_smem_bytes(const SolveArgs& a);
 
 }  // namespace gs

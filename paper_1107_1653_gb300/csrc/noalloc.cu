@@ -203,7 +203,7 @@ extern "C" gs_status gamesolve_isaacs_policy_solve_static(int32_t side, int32_t 
         set_last_error("static solve: side must be 2^k - 1 and at most %d", kStaticMaxSide);
         return GS_EINVAL;
     }
-    if ((variant != 0 && variant != 1) || precision < GS_PREC_FP64 || precision > GS_PREC_MIXED ||
+    if ((variant != 0 && variant != 1) || precision < GS_PREC_FP64 || precision > GS_PREC_MIXED_BF16 ||
         !alpha || !beta || !w) {
         set_last_error("static solve: invalid argument");
         return GS_EINVAL;

@@ -325,6 +325,7 @@ bool linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bo
     a.nu2 = s->opt.nu2;
     a.max_cycles = s->opt.max_cycles;
     a.mixed = mixed ? 1 : 0;
+    a.wbf16 = s->opt.precision == GS_PREC_MIXED_BF16 ? 1 : 0;
     a.do_setup = do_setup ? 1 : 0;
     a.max_blocks = s->opt.grid_blocks;
     a.lin_tol = s->opt.lin_tol;
@@ -355,7 +356,7 @@ bool linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bo
     }
     // levels from smem_from on are staged in block 0's shared memory, as many as fit
     a.smem_from = std::max(a.tail, 1);
-    while (a.smem_from < a.nlev && tail_smem_bytes(a, mixed ? 4 : 8) > (size_t)kTailSmemMax)
+    while (a.smem_from < a.nlev && tail_smem_bytes(a) > (size_t)kTailSmemMax)
         ++a.smem_from;
     GS_CUDA(cudaMemsetAsync(s->mgd, 0, sizeof(MGState), s->st));
     if (do_setup) {

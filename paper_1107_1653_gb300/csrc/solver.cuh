@@ -72,7 +72,8 @@ struct GameProblem {
     int32_t* col = nullptr;
     double *prob = nullptr, *rew = nullptr, *leak = nullptr, *mu = nullptr, *v = nullptr,
            *rhs = nullptr, *gres = nullptr;
-    float* prob32 = nullptr;
+    float* prob32 = nullptr;   // rounded copy of prob: float32, or bfloat16 in its first half
+    bool prob_bf16 = false;
     uint8_t *alpha = nullptr, *beta = nullptr;
     int *gstats = nullptr, *queue = nullptr;
     bool grid = false;                     // one large game on the whole grid
@@ -80,7 +81,10 @@ struct GameProblem {
     GridBarrier* bar = nullptr;
     std::vector<int> stats_h;
     std::vector<double> res_h;
-    GameTables tables() const { return {m1, m2, row_ptr, col, prob, prob32, rew, leak}; }
+    GameTables tables() const {
+        return {m1,   m2, row_ptr, col, prob, prob_bf16 ? nullptr : prob32,
+                prob_bf16 ? (const __nv_bfloat16*)prob32 : nullptr, rew, leak};
+    }
 };
 
 struct Problem {

@@ -11,9 +11,30 @@
 // R = P^T and the coarse operator is the Galerkin product A^{l+1} = R A^l P.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace gs {
+
+// ------------------------------------------------------------------ weight storage
+// The V-cycle's operators and interpolation weights are stored in float64,
+// float32 or bfloat16 and used in the cycle's arithmetic type: wval widens a
+// stored weight (bfloat16 to float32, the others unchanged).
+__device__ __forceinline__ double wval(double x) { return x; }
+__device__ __forceinline__ float wval(float x) { return x; }
+__device__ __forceinline__ float wval(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// Destination of the set-up's rounded copies: float32, bfloat16 or none.
+struct WOut {
+    float* f32;
+    __nv_bfloat16* b16;
+    __device__ __forceinline__ bool any() const { return f32 || b16; }
+    __device__ __forceinline__ void put(size_t k, double v) const {
+        if (f32) f32[k] = (float)v;
+        else if (b16) b16[k] = __double2bfloat16(v);
+    }
+};
 
 // ------------------------------------------------------------------ rows
 // Explicit 9-point rows A[d * n + x] (float64).
@@ -143,32 +164,32 @@ struct L0Op<float> {
 
 // 9-point levels: float64 rows hold the entries of A; float32 rows hold the
 // row sum in slot 0 and the off-diagonal entries in slots 1..8.
-template <typename T>
+template <typename T, typename W = T>
 struct L9Op {
-    const T* A;
+    const W* A;
     size_t n;
     int side;
     __device__ __forceinline__ T resid(const T* f, const T* u, int i, int j) const {
         const size_t x = (size_t)j * side + i;
         const T ux = u[x];
-        T Au = A[x] * ux;
+        T Au = (T)wval(A[x]) * ux;
 #pragma unroll
         for (int d = 1; d < 9; ++d) {
             const int gi = i + dir_di(d), gj = j + dir_dj(d);
             const bool in = gi >= 0 && gj >= 0 && gi < side && gj < side;
             const T ud = in ? u[(size_t)gj * side + gi] : T(0);
-            if constexpr (sizeof(T) == 8) Au += A[d * n + x] * ud;
-            else Au += A[d * n + x] * (ud - ux);
+            if constexpr (sizeof(T) == 8) Au += (T)wval(A[d * n + x]) * ud;
+            else Au += (T)wval(A[d * n + x]) * (ud - ux);
         }
         return f[x] - Au;
     }
     __device__ __forceinline__ void relax(const T* f, T* u, int i, int j, bool zero) const {
         const size_t x = (size_t)j * side + i;
         T s = f[x];
-        T diag = A[x];
+        T diag = (T)wval(A[x]);
 #pragma unroll
         for (int d = 1; d < 9; ++d) {
-            const T a = A[d * n + x];
+            const T a = (T)wval(A[d * n + x]);
             if constexpr (sizeof(T) == 4) diag -= a;
             if (zero) continue;
             const int gi = i + dir_di(d), gj = j + dir_dj(d);
@@ -183,7 +204,7 @@ struct L9Op {
 // Edge weights of cell t = (I, J), I, J in [0, sc].
 template <class Src>
 __device__ __forceinline__ void interp_edges_item(const Src& src, int sc, size_t t, double* P,
-                                                  float* P32) {
+                                                  const WOut& Pw) {
     const int nc1 = sc + 1;
     const size_t ncell = (size_t)nc1 * nc1;
     const int I = (int)(t % nc1), J = (int)(t / nc1);
@@ -209,11 +230,11 @@ __device__ __forceinline__ void interp_edges_item(const Src& src, int sc, size_t
     P[PXE * ncell + t] = wxE;
     P[PYS * ncell + t] = wyS;
     P[PYN * ncell + t] = wyN;
-    if (P32) {
-        P32[PXW * ncell + t] = (float)wxW;
-        P32[PXE * ncell + t] = (float)wxE;
-        P32[PYS * ncell + t] = (float)wyS;
-        P32[PYN * ncell + t] = (float)wyN;
+    if (Pw.any()) {
+        Pw.put(PXW * ncell + t, wxW);
+        Pw.put(PXE * ncell + t, wxE);
+        Pw.put(PYS * ncell + t, wyS);
+        Pw.put(PYN * ncell + t, wyN);
     }
 }
 
@@ -221,7 +242,7 @@ __device__ __forceinline__ void interp_edges_item(const Src& src, int sc, size_t
 // interpolated values of its 8 neighbours (needs the edge weights).
 template <class Src>
 __device__ __forceinline__ void interp_corners_item(const Src& src, int sc, size_t t, double* P,
-                                                    float* P32) {
+                                                    const WOut& Pw) {
     const int nc1 = sc + 1;
     const size_t ncell = (size_t)nc1 * nc1;
     const int I = (int)(t % nc1), J = (int)(t / nc1);
@@ -246,59 +267,33 @@ __device__ __forceinline__ void interp_corners_item(const Src& src, int sc, size
     P[PSE * ncell + t] = wSE;
     P[PNW * ncell + t] = wNW;
     P[PNE * ncell + t] = wNE;
-    if (P32) {
-        P32[PSW * ncell + t] = (float)wSW;
-        P32[PSE * ncell + t] = (float)wSE;
-        P32[PNW * ncell + t] = (float)wNW;
-        P32[PNE * ncell + t] = (float)wNE;
+    if (Pw.any()) {
+        Pw.put(PSW * ncell + t, wSW);
+        Pw.put(PSE * ncell + t, wSE);
+        Pw.put(PNW * ncell + t, wNW);
+        Pw.put(PNE * ncell + t, wNE);
     }
-}
-
-// Coarse points from which the fine point (gi, gj) interpolates, with weights.
-template <typename W>
-__device__ __forceinline__ int interp_of(const W* P, int sc, int gi, int gj, int cI[4], int cJ[4],
-                                         W w[4]) {
-    const int nc1 = sc + 1;
-    const size_t ncell = (size_t)nc1 * nc1;
-    const int I = gi >> 1, J = gj >> 1;
-    const size_t c = (size_t)J * nc1 + I;
-    const int oi = gi & 1, oj = gj & 1;
-    if (oi && oj) {
-        cI[0] = I; cJ[0] = J; w[0] = W(1);
-        return 1;
-    }
-    if (!oi && oj) {
-        cI[0] = I - 1; cJ[0] = J; w[0] = P[PXW * ncell + c];
-        cI[1] = I;     cJ[1] = J; w[1] = P[PXE * ncell + c];
-        return 2;
-    }
-    if (oi && !oj) {
-        cI[0] = I; cJ[0] = J - 1; w[0] = P[PYS * ncell + c];
-        cI[1] = I; cJ[1] = J;     w[1] = P[PYN * ncell + c];
-        return 2;
-    }
-    cI[0] = I - 1; cJ[0] = J - 1; w[0] = P[PSW * ncell + c];
-    cI[1] = I;     cJ[1] = J - 1; w[1] = P[PSE * ncell + c];
-    cI[2] = I - 1; cJ[2] = J;     w[2] = P[PNW * ncell + c];
-    cI[3] = I;     cJ[3] = J;     w[3] = P[PNE * ncell + c];
-    return 4;
 }
 
 // Weight of the fine point (2I+1+di, 2J+1+dj) towards the coarse point (I, J):
 // the restriction coefficient R = P^T.
 template <typename W>
-__device__ __forceinline__ W restrict_weight(const W* P, int sc, int I, int J, int di, int dj) {
+__device__ __forceinline__ auto restrict_weight(const W* P, int sc, int I, int J, int di, int dj)
+    -> decltype(wval(P[0])) {
+    using R = decltype(wval(P[0]));
     const int nc1 = sc + 1;
     const size_t ncell = (size_t)nc1 * nc1;
-    if (di == 0 && dj == 0) return W(1);
+    if (di == 0 && dj == 0) return R(1);
     if (dj == 0)   // x-edge: (2I, .) is cell (I, J) east weight; (2I+2, .) cell (I+1, J) west weight
-        return di < 0 ? P[PXE * ncell + (size_t)J * nc1 + I] : P[PXW * ncell + (size_t)J * nc1 + I + 1];
+        return wval(di < 0 ? P[PXE * ncell + (size_t)J * nc1 + I] : P[PXW * ncell + (size_t)J * nc1 + I + 1]);
     if (di == 0)
-        return dj < 0 ? P[PYN * ncell + (size_t)J * nc1 + I] : P[PYS * ncell + (size_t)(J + 1) * nc1 + I];
+        return wval(dj < 0 ? P[PYN * ncell + (size_t)J * nc1 + I]
+                           : P[PYS * ncell + (size_t)(J + 1) * nc1 + I]);
     if (dj < 0)
-        return di < 0 ? P[PNE * ncell + (size_t)J * nc1 + I] : P[PNW * ncell + (size_t)J * nc1 + I + 1];
-    return di < 0 ? P[PSE * ncell + (size_t)(J + 1) * nc1 + I]
-                  : P[PSW * ncell + (size_t)(J + 1) * nc1 + I + 1];
+        return wval(di < 0 ? P[PNE * ncell + (size_t)J * nc1 + I]
+                           : P[PNW * ncell + (size_t)J * nc1 + I + 1]);
+    return wval(di < 0 ? P[PSE * ncell + (size_t)(J + 1) * nc1 + I]
+                       : P[PSW * ncell + (size_t)(J + 1) * nc1 + I + 1]);
 }
 
 // Adds v to the coarse stencil entry towards (I + tx, J + ty) if that point is
@@ -340,10 +335,11 @@ __device__ __forceinline__ void rap_scatter(const double* P, int sc, int I, int 
 }
 
 // Galerkin coarse row A_c(t, .) = (P^T A P)(t, .) for the coarse point t
-// (float64 accumulation); also its float32 leakage form when A32 is given.
+// (float64 accumulation); also its rounded leakage form (row sum, then the
+// off-diagonal entries) when Aw has a destination.
 template <class Src>
 __device__ __forceinline__ void rap_item(const Src& src, int sc, size_t t, const double* P,
-                                         double* Ac, float* A32) {
+                                         double* Ac, const WOut& Aw) {
     const size_t nc = (size_t)sc * sc;
     const int I = (int)(t % sc), J = (int)(t / sc);
     const int sf = 2 * sc + 1;
@@ -373,10 +369,10 @@ __device__ __forceinline__ void rap_item(const Src& src, int sc, size_t t, const
         Ac[d * nc + t] = acc[d];
         s += acc[d];
     }
-    if (A32) {
-        A32[t] = (float)s;
+    if (Aw.any()) {
+        Aw.put(t, s);
 #pragma unroll
-        for (int d = 1; d < 9; ++d) A32[d * nc + t] = (float)acc[d];
+        for (int d = 1; d < 9; ++d) Aw.put(d * nc + t, acc[d]);
     }
 }
 

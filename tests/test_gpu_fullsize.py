@@ -2,7 +2,7 @@
 
 The FP64 oracle solves the same game with sparse LU (a few minutes on one
 core); the GPU runs in the launch configuration bench.py times.  Checked:
-the value (1e-10 relative FP64 path, 1e-9 mixed path), the policies where
+the value (1e-10 relative FP64 path, 1e-9 mixed paths), the policies where
 the oracle's max-min gap exceeds 1e-8, and, from the oracle's own Shapley
 operator at every state, that the GPU value is a fixed point of Eq. (eq1).
 """
@@ -23,7 +23,7 @@ def reference():
     return game, oracle.policy_iteration(game)
 
 
-@pytest.mark.parametrize("prec,fmg", [("fp64", 0), ("mixed", 0), ("mixed", 1)])
+@pytest.mark.parametrize("prec,fmg", [("fp64", 0), ("mixed", 0), ("mixed", 1), ("mixed_bf16", 0)])
 def test_isaacs_1023_parity(gs, reference, prec, fmg):
     game, ref = reference
     with gs.GameSolver(precision=prec, fmg=fmg, fmg_side=31) as s:

@@ -12,7 +12,7 @@ from oracle.game import game_from_csr
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "mixed": 1e-9}
+TOL = {"fp64": 1e-10, "mixed": 1e-9, "mixed_bf16": 1e-9}
 
 
 def oracle_of(n, m1, m2, rp, col, prob, rew, mu):
@@ -67,7 +67,7 @@ def test_tiny_games(gs, n, m1, m2, prec):
     assert check(v, a, b, ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
 @pytest.mark.parametrize("n", [256, 1000, 4096])
 def test_random_game(gs, n, prec):
     rp, col, prob, rew, mu = synth.random_game(n, 4 + n)
@@ -113,7 +113,7 @@ def batch(sizes, seed):
             np.concatenate(rews), np.array(mus)), parts
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "fp64", "mixed_bf16"])
 def test_game_batch(gs, prec):
     sizes = synth.batch_game_sizes(24, 4, nmin=256, nmax=1500)
     (off, rp, col, prob, rew, mu), parts = batch(sizes, 4)
@@ -154,7 +154,7 @@ def test_game_validation(gs):
         assert s.solve()["converged"] == 1
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "fp64", "mixed_bf16"])
 @pytest.mark.parametrize("n,blocks", [(5000, 0), (12000, 0), (12000, 8)])
 def test_large_game_on_the_grid(gs, n, blocks, prec):
     """Games of >= 4096 states set alone run on a cooperative grid (policy

@@ -14,7 +14,7 @@ from oracle.fmg import famg_pi, interp_value, interp_policy
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "mixed": 1e-9}
+TOL = {"fp64": 1e-10, "mixed": 1e-9, "mixed_bf16": 1e-9}
 _CACHE = {}
 
 
@@ -38,7 +38,7 @@ def check_policies(alpha, beta, ref, m1):
     assert beta.shape == (len(alpha), m1)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
 @pytest.mark.parametrize("side", [1, 3, 7, 15, 63, 255])
 def test_solve_parity_plain(gs, side, prec):
     game, ref = oracle_solve(side, 0, 1)
@@ -52,7 +52,7 @@ def test_solve_parity_plain(gs, side, prec):
     check_policies(a, b, ref, 4)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
 @pytest.mark.parametrize("side", [15, 63])
 def test_solve_parity_obstacle(gs, side, prec):
     game, ref = oracle_solve(side, 1, 2)
@@ -102,7 +102,7 @@ def test_improve_parity(gs, side):
     assert np.array_equal(b[sure_b], b_ref[sure_b])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
 @pytest.mark.parametrize("side", [7, 63, 255])
 def test_policy_solve_parity(gs, side, prec):
     """The multigrid solve of Eq. (LSPI) for fixed policies vs a direct solve."""
@@ -116,6 +116,23 @@ def test_policy_solve_parity(gs, side, prec):
         s.set_isaacs_grid(side, 0, 1)
         w, st = s.policy_solve(alpha, beta)
     assert rel_err(w, w_ref) <= TOL[prec] / 10, (rel_err(w, w_ref), st)
+
+
+def test_bf16_storage_takes_effect(gs):
+    """bfloat16 weights change the V-cycle's iterates (not bit-identical to the
+    float32-weight path) but not the float64 answer they refine."""
+    side = 255
+    rng = np.random.default_rng(5)
+    alpha = rng.integers(0, 4, size=side * side).astype(np.uint8)
+    beta = rng.integers(0, 4, size=(side * side, 4)).astype(np.uint8)
+    out = {}
+    for prec in ("mixed", "mixed_bf16"):
+        with gs.GameSolver(precision=prec) as s:
+            s.set_isaacs_grid(side, 0, 1)
+            out[prec] = s.policy_solve(alpha, beta)
+    (w32, st32), (w16, st16) = out["mixed"], out["mixed_bf16"]
+    assert not np.array_equal(w32, w16)
+    assert rel_err(w16, w32) <= 1e-12, (st32, st16)
 
 
 @pytest.mark.parametrize("variant", [0, 1])
@@ -156,12 +173,14 @@ def test_status_codes(gs):
         assert e.value.status == gs.GS_ENOMEM
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
 @pytest.mark.parametrize("tail_side", [1, 7, 15, 31, 63])
 def test_vcycle_count_size_independent(gs, prec, tail_side):
     """AMG cycles per system stay bounded as the grid grows (the paper's tables
     report 3-5 W-cycles per system at every size), whatever the split between
-    grid-wide and single-block levels."""
+    grid-wide and single-block levels.  Rounding the coarse operators to
+    bfloat16 (8 significant bits) perturbs the preconditioner, not the float64
+    residual it drives down, so it may cost a few more cycles."""
     rng = np.random.default_rng(11)
     for side in (63, 255, 1023):
         n = side * side
@@ -170,5 +189,5 @@ def test_vcycle_count_size_independent(gs, prec, tail_side):
         with gs.GameSolver(precision=prec, tail_side=tail_side) as s:
             s.set_isaacs_grid(side, 0, 1)
             _, st = s.policy_solve(alpha, beta)
-        assert st["cycles"] <= 14, (side, st)
+        assert st["cycles"] <= (20 if prec == "mixed_bf16" else 14), (side, st)
         assert st["res_inf"] < 1e-14

@@ -16,7 +16,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "mixed": 1e-9}   # the value tolerances of the parity tests
+TOL = {"fp64": 1e-10, "mixed": 1e-9, "mixed_bf16": 1e-9}   # the value tolerances of the parity tests
 
 
 def _static_solve(gs, torch, side, variant, seed, alpha_d, beta_d, w_d, precision):
@@ -29,7 +29,7 @@ def _static_solve(gs, torch, side, variant, seed, alpha_d, beta_d, w_d, precisio
     return code, st
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_bf16"])
 @pytest.mark.parametrize("side,variant", [(127, 0), (63, 1)])
 def test_static_solve_matches_allocating_solve(gs, side, variant, precision):
     import torch
