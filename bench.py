@@ -121,6 +121,23 @@ def dist_setup():
     return world, rank, local
 
 
+def replicas_max_ms(ms: float, world: int, device) -> float:
+    """Per-step time of the whole job: the maximum over the replicas' ranks."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, ms_max: float, units_per_step: float = 1.0) -> float:
+    """Units per second of all replicas: each rank processes its own units per
+    step, and the job's step ends with its slowest rank."""
+    return world * units_per_step * 1000.0 / ms_max
+
+
 def oracle_sample(systems_per_solve: int, outer_per_solve: int):
     """Seconds of one oracle policy evaluation + improvement at 1023^2.
 
@@ -418,11 +435,8 @@ def run_ours(args):
         prec, args.steps, args.warmup, trace=args.trace_kernel)
     clk = clocks.stop()
     ms = statistics.mean(per_step)
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * 1000.0 / ms_max
+    ms_max = replicas_max_ms(ms, world, "cuda")
+    value = whole_job_value(world, ms_max)
 
     # the other precisions, for the FP32+refine vs FP64 comparison: each one's
     # time and counts, and every result's relative distance from the FP64 value
