@@ -164,7 +164,7 @@ gs_status gamesolve_get_batch_stats(const gs_solver* s, int32_t* stats, double* 
  * coordinate fastest), host or device; NULL draws xi(x) = 0.1 u_x - 0.05 with
  * u_x the x-th double of the SplitMix64 stream `seed`.
  * The multigrid hierarchy coarsens by 2 per level, so side must be 2^k - 1.
- * Errors: GS_EINVAL if side is not 2^k - 1 (k >= 1), side is below
+ * Errors: GS_EINVAL if side is not 2^k - 1 (1 <= k <= 14), side is below
  * options.fmg_side when options.fmg is set, or variant is not 0 or 1. */
 gs_status gamesolve_set_isaacs_grid(gs_solver* s, int32_t side, int32_t variant,
                                     uint64_t seed, const double* xi);

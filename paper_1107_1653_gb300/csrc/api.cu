@@ -175,8 +175,8 @@ gs_status gamesolve_get_batch_stats(const gs_solver* s, int32_t* stats, double* 
 
 gs_status gamesolve_set_isaacs_grid(gs_solver* s, int32_t side, int32_t variant, uint64_t seed,
                                     const double* xi) {
-    if (!s || !is_pow2m1(side) || (variant != 0 && variant != 1)) {
-        set_last_error("set_isaacs_grid: side must be 2^k - 1 and variant 0 or 1");
+    if (!s || !is_pow2m1(side) || side > kIsaacsMaxSide || (variant != 0 && variant != 1)) {
+        set_last_error("set_isaacs_grid: side must be 2^k - 1 <= 16383 and variant 0 or 1");
         return GS_EINVAL;
     }
     if (s->opt.fmg && side < s->opt.fmg_side) {

@@ -91,6 +91,34 @@ struct DevScalars {
     int code_changed;            // rows of the policy-fixed system that changed
 };
 
+// Quotient and remainder of x by d (1 <= d < 2^14, x < 2^28, so x / d < 2^20)
+// from a float32 reciprocal: the float quotient's relative error is at most
+// 3 * 2^-24 (rounding of x, of 1/d and of the product), under 0.2 in absolute
+// terms, so the truncated quotient is off by at most one and one correction
+// step makes it exact.  Replaces 64-bit integer division in the index
+// arithmetic of every grid-stride loop.
+struct FastDiv {
+    unsigned d;
+    float inv;
+    __device__ __forceinline__ explicit FastDiv(unsigned d_) : d(d_), inv(1.0f / (float)d_) {}
+    __device__ __forceinline__ unsigned divmod(unsigned x, unsigned* r) const {
+        unsigned q = __float2uint_rz(__uint2float_rn(x) * inv);
+        int rem = (int)(x - q * d);
+        if (rem < 0) {
+            --q;
+            rem += (int)d;
+        } else if (rem >= (int)d) {
+            ++q;
+            rem -= (int)d;
+        }
+        *r = (unsigned)rem;
+        return q;
+    }
+};
+
+// Largest Isaacs grid side: keeps every level index below 2^28 (FastDiv).
+constexpr int kIsaacsMaxSide = 16383;
+
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* dst, double v) {
     atomicMax(dst, (unsigned long long)__double_as_longlong(v));
 }

@@ -46,22 +46,28 @@ __device__ void relax_fine(const L0Op<T>& op, const LevelArgs& L, int c, bool ze
     T* __restrict__ u = (T*)L.u;
     const T* __restrict__ f = (const T*)L.f;
     const int side = L.side, hs = (side + 1) / 2;
-    const size_t cnt = (size_t)side * hs;
-    size_t t = start;
-    // two independent points per step: the colour's updates read only the other colour
-    for (; t + stride < cnt; t += 2 * stride) {
-        const size_t t2 = t + stride;
-        const int j1 = (int)(t / hs), i1 = ((j1 + c) & 1) + 2 * (int)(t % hs);
-        const int j2 = (int)(t2 / hs), i2 = ((j2 + c) & 1) + 2 * (int)(t2 % hs);
-        T v1 = T(0), v2 = T(0);
-        const bool ok1 = i1 < side, ok2 = i2 < side;
-        if (ok1) v1 = op.relaxed(f, u, i1, j1, zero);
-        if (ok2) v2 = op.relaxed(f, u, i2, j2, zero);
-        if (ok1) u[(size_t)j1 * side + i1] = v1;
-        if (ok2) u[(size_t)j2 * side + i2] = v2;
+    const unsigned cnt = (unsigned)side * hs, st = (unsigned)stride;
+    const FastDiv dv(hs);
+    unsigned t = (unsigned)start;
+    // four independent points per step: the colour's updates read only the other colour
+    constexpr int K = 4;
+    for (; t + (K - 1) * st < cnt; t += K * st) {
+        int i[K], j[K];
+        T val[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            unsigned r;
+            j[k] = (int)dv.divmod(t + k * st, &r);
+            i[k] = ((j[k] + c) & 1) + 2 * (int)r;
+            val[k] = i[k] < side ? op.relaxed(f, u, i[k], j[k], zero) : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (i[k] < side) u[(size_t)j[k] * side + i[k]] = val[k];
     }
-    if (t < cnt) {
-        const int j = (int)(t / hs), i = ((j + c) & 1) + 2 * (int)(t % hs);
+    for (; t < cnt; t += st) {
+        unsigned r;
+        const int j = (int)dv.divmod(t, &r), i = ((j + c) & 1) + 2 * (int)r;
         if (i < side) u[(size_t)j * side + i] = op.relaxed(f, u, i, j, zero);
     }
 }
@@ -74,11 +80,32 @@ __device__ void relax_fine_update(const L0Op<float>& op, const LevelArgs& L, dou
     float* __restrict__ u = (float*)L.u;
     const float* __restrict__ f = (const float*)L.f;
     const int side = L.side;
-    for (size_t x = start; x < L.n; x += stride) {
-        const int i = (int)(x % side), j = (int)(x / side);
+    const unsigned n = (unsigned)L.n, st = (unsigned)stride;
+    const FastDiv dv(side);
+    unsigned x = (unsigned)start;
+    constexpr int K = 2;
+    for (; x + (K - 1) * st < n; x += K * st) {
+        float e[K];
+        bool mine[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            unsigned i;
+            const int j = (int)dv.divmod(x + k * st, &i);
+            mine[k] = (((int)i + j) & 1) == c;
+            e[k] = mine[k] ? op.relaxed(f, u, (int)i, j, false) : u[x + k * st];
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (mine[k]) u[x + k * st] = e[k];
+            v[x + k * st] += (double)e[k];
+        }
+    }
+    for (; x < n; x += st) {
+        unsigned i;
+        const int j = (int)dv.divmod(x, &i);
         float e;
-        if (((i + j) & 1) == c) {
-            e = op.relaxed(f, u, i, j, false);
+        if ((((int)i + j) & 1) == c) {
+            e = op.relaxed(f, u, (int)i, j, false);
             u[x] = e;
         } else {
             e = u[x];
@@ -94,25 +121,45 @@ __device__ void relax_coarse(const LevelArgs& L, int c, bool zero, size_t start,
     const T* f = (const T*)L.f;
     const int ox = colour_ox(c), oy = colour_oy(c);
     const int nx = (L.side - ox + 1) / 2, ny = (L.side - oy + 1) / 2;
-    const size_t cnt = (size_t)nx * ny;
-    for (size_t t = start; t < cnt; t += stride)
-        op.relax(f, u, ox + 2 * (int)(t % nx), oy + 2 * (int)(t / nx), zero);
+    const unsigned cnt = (unsigned)nx * ny, st = (unsigned)stride;
+    const FastDiv dv(nx);
+    unsigned t = (unsigned)start;
+    // two independent points per step (a colour's points are mutually uncoupled)
+    for (; t + st < cnt; t += 2 * st) {
+        unsigned r1, r2;
+        const int j1 = oy + 2 * (int)dv.divmod(t, &r1), i1 = ox + 2 * (int)r1;
+        const int j2 = oy + 2 * (int)dv.divmod(t + st, &r2), i2 = ox + 2 * (int)r2;
+        const T v1 = op.relaxed(f, u, i1, j1, zero);
+        const T v2 = op.relaxed(f, u, i2, j2, zero);
+        u[(size_t)j1 * L.side + i1] = v1;
+        u[(size_t)j2 * L.side + i2] = v2;
+    }
+    if (t < cnt) {
+        unsigned r;
+        const int j = oy + 2 * (int)dv.divmod(t, &r), i = ox + 2 * (int)r;
+        u[(size_t)j * L.side + i] = op.relaxed(f, u, i, j, zero);
+    }
 }
 
 // f_{l+1} = R (f_l - A_l u_l) with the fine residuals formed on the fly;
-// u_{l+1} = 0.
+// u_{l+1} = 0.  With `fuse` the coarse level's first relaxation colour (its
+// C points, relaxed from the zero start) is done here too: such a point's
+// Gauss-Seidel value is f / diag, from data this item already has.
 template <typename T, typename W, class Op>
-__device__ void restrict_with(const Op& op, const LevelArgs& L, const LevelArgs& C, size_t start,
-                              size_t stride) {
+__device__ void restrict_with(const Op& op, const LevelArgs& L, const LevelArgs& C, bool fuse,
+                              size_t start, size_t stride) {
     const int sc = L.sc;
     const T* u = (const T*)L.u;
     const T* f = (const T*)L.f;
     const W* P = (const W*)L.P;
     T* fc = (T*)C.f;
     T* uc = (T*)C.u;
-    const size_t nc = (size_t)sc * sc;
-    for (size_t t = start; t < nc; t += stride) {
-        const int I = (int)(t % sc), J = (int)(t / sc);
+    const L9Op<T, W> cop{(const W*)C.A, C.n, C.side};
+    const unsigned nc = (unsigned)sc * sc;
+    const FastDiv dv(sc);
+    for (unsigned t = (unsigned)start; t < nc; t += (unsigned)stride) {
+        unsigned Iu;
+        const int J = (int)dv.divmod(t, &Iu), I = (int)Iu;
         T acc = 0;
 #pragma unroll
         for (int dj = -1; dj <= 1; ++dj)
@@ -121,7 +168,7 @@ __device__ void restrict_with(const Op& op, const LevelArgs& L, const LevelArgs&
                 acc += (T)restrict_weight(P, sc, I, J, di, dj) * op.resid(f, u, 2 * I + 1 + di, 2 * J + 1 + dj);
             }
         fc[t] = acc;
-        uc[t] = T(0);
+        uc[t] = fuse && (I & J & 1) ? acc / cop.diag(I, J) : T(0);
     }
 }
 
@@ -134,8 +181,10 @@ __device__ void prolong_phase(const LevelArgs& L, const LevelArgs& C, size_t sta
     auto P = [&](int k, size_t c) -> T { return (T)wval(Pw[k * ncell + c]); };
     const T* uc = (const T*)C.u;
     T* uf = (T*)L.u;
-    for (size_t t = start; t < ncell; t += stride) {
-        const int I = (int)(t % nc1), J = (int)(t / nc1);
+    const FastDiv dv(nc1);
+    for (unsigned t = (unsigned)start; t < (unsigned)ncell; t += (unsigned)stride) {
+        unsigned Iu;
+        const int J = (int)dv.divmod(t, &Iu), I = (int)Iu;
         auto U = [&](int p, int q) -> T {
             return (p < 0 || q < 0 || p >= sc || q >= sc) ? T(0) : uc[(size_t)q * sc + p];
         };
@@ -158,9 +207,15 @@ __device__ void relax_level(const SolveArgs& a, const LevelArgs& L, int l, int c
 
 template <typename T, typename W>
 __device__ void restrict_level(const SolveArgs& a, const LevelArgs& L, const LevelArgs& C, int l,
-                               size_t start, size_t stride) {
-    if (l == 0) restrict_with<T, W>(L0Op<T>{a.K, a.code, L.side}, L, C, start, stride);
-    else restrict_with<T, W>(L9Op<T, W>{(const W*)L.A, L.n, L.side}, L, C, start, stride);
+                               bool fuse, size_t start, size_t stride) {
+    if (l == 0) restrict_with<T, W>(L0Op<T>{a.K, a.code, L.side}, L, C, fuse, start, stride);
+    else restrict_with<T, W>(L9Op<T, W>{(const W*)L.A, L.n, L.side}, L, C, fuse, start, stride);
+}
+
+// Whether the residual check already relaxed the fine level's first colour
+// from the zero start (mixed path: the correction starts from zero).
+__device__ __forceinline__ bool fine_colour0_in_check(const SolveArgs& a) {
+    return a.mixed && a.nu1 > 0;
 }
 
 // Exact solve on the coarsest level by its explicit inverse (one block).
@@ -201,12 +256,16 @@ __device__ void block_vcycle(const SolveArgs& a, const LevelArgs* tl, const doub
     for (int l = lbeg; l < Lc; ++l) {
         const int ncol = l == 0 ? 2 : 4;
         const bool z = l > lbeg || first_zero;
+        // first colour from the zero start already done by the restriction into
+        // this level, or (fine level) by the residual check
+        const bool done0 = z && (l > lbeg || (l == 0 && fine_colour0_in_check(a)));
         for (int k = 0; k < a.nu1; ++k)
             for (int c = 0; c < ncol; ++c) {
+                if (done0 && k == 0 && c == 0) continue;
                 relax_level<T, W>(a, tl[l], l, c, z && k == 0 && c == 0, s0, st);
                 __syncthreads();
             }
-        restrict_level<T, W>(a, tl[l], tl[l + 1], l, s0, st);
+        restrict_level<T, W>(a, tl[l], tl[l + 1], l, l + 1 < Lc && a.nu1 > 0, s0, st);
         __syncthreads();
     }
     coarse_apply_block<T>(tl[Lc], inv);
@@ -233,16 +292,23 @@ __device__ void block_vcycle(const SolveArgs& a, const LevelArgs* tl, const doub
 template <typename T, typename W>
 __device__ bool grid_vcycle(const SolveArgs& a, const LevelArgs* tl, const double* inv,
                             const GridSync& G, size_t gt, size_t gs, bool fine_zero) {
+    const int Lc = a.nlev - 1;
     for (int l = 0; l < a.tail; ++l) {
         const int ncol = l == 0 ? 2 : 4;
         const bool z = l > 0 || fine_zero;
+        // first colour from the zero start already done by the restriction into
+        // this level, or (fine level) by the residual check
+        const bool done0 = z && (l > 0 || fine_colour0_in_check(a));
         for (int k = 0; k < a.nu1; ++k)
             for (int c = 0; c < ncol; ++c) {
+                if (done0 && k == 0 && c == 0) continue;
                 relax_level<T, W>(a, a.L[l], l, c, z && k == 0 && c == 0, gt, gs);
                 if (!G.sync()) return false;
                 prof_mark(1000 + 10 * l + c);
             }
-        restrict_level<T, W>(a, a.L[l], a.L[l + 1], l, gt, gs);
+        // the block relaxes level a.tail from its own staged copy: no fusion into it
+        restrict_level<T, W>(a, a.L[l], a.L[l + 1], l, l + 1 < a.tail && l + 1 < Lc && a.nu1 > 0,
+                             gt, gs);
         if (!G.sync()) return false;
         prof_mark(2000 + 10 * l);
     }
@@ -302,26 +368,31 @@ __device__ void setup_items(const SolveArgs& a, int l, int kind, size_t start, s
     }
 }
 
+// Position of this thread in a warp-major order over the grid: warp w of
+// every block comes before warp w + 1 of any block, lanes stay consecutive.
+// A level with few items then spreads one warp per block over all SMs
+// instead of filling the first blocks (the set-up's items are float64-bound,
+// so where they run decides how fast they run).
+__device__ __forceinline__ size_t warp_spread_index() {
+    const size_t w = (size_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    return w * 32 + (threadIdx.x & 31);
+}
+
 // Interpolation weights and Galerkin operators of every level for the current
 // policy codes, then the explicit inverse of the coarsest operator.
 __global__ void __launch_bounds__(kMGThreads) k_mg_setup(const __grid_constant__ SolveArgs a) {
     extern __shared__ double smem[];
     const GridSync G{a.bar, gridDim.x};
-    const size_t gt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t gt = warp_spread_index();
     const size_t gs = (size_t)gridDim.x * blockDim.x;
     const int Lc = a.nlev - 1;
-    for (int l = 0; l < Lc && l < a.tail; ++l)
+    for (int l = 0; l < Lc; ++l)
         for (int kind = 0; kind < 3; ++kind) {
             setup_items(a, l, kind, gt, gs);
             if (!G.sync()) return;
             prof_mark(7000 + 10 * l + kind);
         }
     if (blockIdx.x == 0) {
-        for (int l = a.tail; l < Lc; ++l)
-            for (int kind = 0; kind < 3; ++kind) {
-                setup_items(a, l, kind, threadIdx.x, blockDim.x);
-                __syncthreads();
-            }
         const LevelArgs& L = a.L[Lc];
         if (Lc == 0) coarse_invert_block(Src5{a.K, a.code, L.side}, L.side, smem, a.inv, a.inv_status);
         else coarse_invert_block(Src9{L.A64, L.side, L.n}, L.side, smem, a.inv, a.inv_status);
@@ -329,53 +400,81 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_setup(const __grid_constant__
 }
 
 // ------------------------------------------------------------------ cycles
-__device__ __forceinline__ float warp_maxf(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
 
 // float64 residual b - A v of the fine system and |v|_inf; in the mixed path
 // the residual, rounded to float32, is the next correction's right-hand side.
+// |x| of a float64 as its bit pattern: non-negative doubles order like their
+// bits, so maxima can be taken with integer operations (the float64 pipe is
+// the scarce one).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// The float64 residual r = rhs - A v of the fine level with |r|_inf and
+// |v|_inf (exact, as bit patterns).  Mixed path: r is also the float32
+// right-hand side of the correction, and the correction's first relaxation
+// colour from the zero start (C points and cell corners: e = r / diag) is
+// done here; with no pre-relaxation the correction is zeroed instead.
 __device__ void check_phase(const SolveArgs& a, int slot, size_t gt, size_t gs) {
     const LevelArgs& L = a.L[0];
     const L0Op<double> op{a.K, a.code, L.side};
+    const L0Op<float> opf{a.K, a.code, L.side};
     float* __restrict__ r32 = a.mixed ? (float*)L.f : nullptr;
-    float* __restrict__ e32 = (a.mixed && a.nu1 == 0) ? (float*)L.u : nullptr;
+    float* __restrict__ e32 = a.mixed ? (float*)L.u : nullptr;
+    const bool relax0 = fine_colour0_in_check(a);
     const double* __restrict__ v = a.v;
-    // maxima in float32 (a stopping-test scale; float64 compares are slow here)
-    float rm = 0.0f, vm = 0.0f;
+    unsigned long long rm = 0, vm = 0;
     const int side = L.side;
-    size_t x = gt;
-    for (; x + 3 * gs < L.n; x += 4 * gs) {
-        double r[4], vx[4];
+    const unsigned n = (unsigned)L.n, st = (unsigned)gs;
+    const FastDiv dv(side);
+    auto finish = [&](unsigned x, int i, int j, double r) {
+        if (r32) {
+            const float rf = (float)r;
+            r32[x] = rf;
+            if (relax0) {
+                if (((i + j) & 1) == 0) e32[x] = rf / opf.diag(i, j);
+            } else {
+                e32[x] = 0.0f;
+            }
+        }
+        rm = max(rm, abs_bits(r));
+    };
+    unsigned x = (unsigned)gt;
+    constexpr int K = 4;
+    for (; x + (K - 1) * st < n; x += K * st) {
+        double r[K];
+        int i[K], j[K];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const size_t y = x + k * gs;
-            r[k] = op.resid(a.rhs, v, (int)(y % side), (int)(y / side));
-            vx[k] = v[y];
+        for (int k = 0; k < K; ++k) {
+            unsigned iu;
+            j[k] = (int)dv.divmod(x + k * st, &iu);
+            i[k] = (int)iu;
+            r[k] = op.resid(a.rhs, v, i[k], j[k]);
+            vm = max(vm, abs_bits(v[x + k * st]));
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const size_t y = x + k * gs;
-            if (r32) r32[y] = (float)r[k];
-            if (e32) e32[y] = 0.0f;
-            rm = fmaxf(rm, fabsf((float)r[k]));
-            vm = fmaxf(vm, fabsf((float)vx[k]));
-        }
+        for (int k = 0; k < K; ++k) finish(x + k * st, i[k], j[k], r[k]);
     }
-    for (; x < L.n; x += gs) {
-        const double r = op.resid(a.rhs, v, (int)(x % side), (int)(x / side));
-        if (r32) r32[x] = (float)r;
-        if (e32) e32[x] = 0.0f;
-        rm = fmaxf(rm, fabsf((float)r));
-        vm = fmaxf(vm, fabsf((float)v[x]));
+    for (; x < n; x += st) {
+        unsigned iu;
+        const int j = (int)dv.divmod(x, &iu);
+        finish(x, (int)iu, j, op.resid(a.rhs, v, (int)iu, j));
+        vm = max(vm, abs_bits(v[x]));
     }
-    rm = warp_maxf(rm);
-    vm = warp_maxf(vm);
+    rm = warp_max_u64(rm);
+    vm = warp_max_u64(vm);
     if ((threadIdx.x & 31) == 0) {
-        atomic_max_nonneg(&a.out->rmax[slot], (double)rm);
-        atomic_max_nonneg(&a.out->vmax[slot], (double)vm);
+        atomicMax(&a.out->rmax[slot], rm);
+        atomicMax(&a.out->vmax[slot], vm);
     }
 }
 

@@ -39,6 +39,7 @@ struct WOut {
 // ------------------------------------------------------------------ rows
 // Explicit 9-point rows A[d * n + x] (float64).
 struct Src9 {
+    static constexpr bool kFivePoint = false;
     const double* A;
     int side;
     size_t n;
@@ -52,6 +53,7 @@ struct Src9 {
 // Implicit 5-point rows of the fine Isaacs level: the row of A = I - mu M for
 // the policy code at the point, couplings to boundary points dropped.
 struct Src5 {
+    static constexpr bool kFivePoint = true;   // the diagonal entries are zero
     const IsaacsConsts* K;
     const uint8_t* code;
     int side;
@@ -148,6 +150,17 @@ struct L0Op<float> {
         if (j + 1 < side) Au += am[4] * (u[x + side] - ux);
         return f[x] - Au;
     }
+    // Diagonal of the row in the leakage form, as relaxed() forms it.
+    __device__ __forceinline__ float diag(int i, int j) const {
+        const int c = code[(size_t)j * side + i];
+        const float* am = K->amf[c];
+        float d = l0_rowsum_f(K, c, i, j, side);
+        if (i > 0) d -= am[1];
+        if (i + 1 < side) d -= am[2];
+        if (j > 0) d -= am[3];
+        if (j + 1 < side) d -= am[4];
+        return d;
+    }
     __device__ __forceinline__ float relaxed(const float* f, const float* u, int i, int j,
                                              bool zero) const {
         const size_t x = (size_t)j * side + i;
@@ -183,7 +196,8 @@ struct L9Op {
         }
         return f[x] - Au;
     }
-    __device__ __forceinline__ void relax(const T* f, T* u, int i, int j, bool zero) const {
+    // Gauss-Seidel value of u at (i, j) (neighbours from u; zero: u == 0).
+    __device__ __forceinline__ T relaxed(const T* f, const T* u, int i, int j, bool zero) const {
         const size_t x = (size_t)j * side + i;
         T s = f[x];
         T diag = (T)wval(A[x]);
@@ -196,7 +210,17 @@ struct L9Op {
             if (gi < 0 || gj < 0 || gi >= side || gj >= side) continue;
             s -= a * u[(size_t)gj * side + gi];
         }
-        u[x] = s / diag;
+        return s / diag;
+    }
+    // Diagonal of the row, as relaxed() forms it.
+    __device__ __forceinline__ T diag(int i, int j) const {
+        const size_t x = (size_t)j * side + i;
+        T d = (T)wval(A[x]);
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int k = 1; k < 9; ++k) d -= (T)wval(A[k * n + x]);
+        }
+        return d;
     }
 };
 
@@ -355,7 +379,11 @@ __device__ __forceinline__ void rap_item(const Src& src, int sc, size_t t, const
             src.row(2 * I + 1 + ox, 2 * J + 1 + oy, a);
 #pragma unroll
             for (int d = 0; d < 9; ++d) {
-                if (a[d] == 0.0) continue;   // folds away for the 5-point fine rows
+                // The 5-point rows' diagonal entries are zero: skip them at
+                // compile time.  No test on loaded values: it would make each
+                // weight load below wait for the row's load.
+                if constexpr (Src::kFivePoint)
+                    if (d >= DSW) continue;
                 const int qx = ox + dir_di(d), qy = oy + dir_dj(d);
                 const int gi = 2 * I + 1 + qx, gj = 2 * J + 1 + qy;
                 if (gi < 0 || gj < 0 || gi >= sf || gj >= sf) continue;
