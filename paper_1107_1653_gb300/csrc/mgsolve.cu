@@ -339,8 +339,56 @@ __device__ bool grid_vcycle(const SolveArgs& a, const LevelArgs* tl, const doubl
 }
 
 // ------------------------------------------------------------------ set-up
+// Float32 storage of level l's set-up in the mixed path: the operator the
+// next level's set-up reads (leakage form) and the interpolation weights.
+// With bfloat16 weights for the V-cycle, the float32 copies live in the
+// (otherwise unused) float64 buffers and the bfloat16 ones in the float32 buffers.
+__device__ __forceinline__ float* setup_A32(const SolveArgs& a, const LevelArgs& L) {
+    return a.wbf16 ? (float*)L.A64 : L.A32;
+}
+__device__ __forceinline__ float* setup_P32(const SolveArgs& a, const LevelArgs& L) {
+    return a.wbf16 ? (float*)L.P64 : L.P32;
+}
+
+// Mixed path set-up items (float32, exact leakage); delta(g) lives in the
+// level's float32 right-hand side vector, free during the set-up.
+__device__ void setup_items_f(const SolveArgs& a, int l, int kind, size_t start, size_t stride) {
+    const LevelArgs& L = a.L[l];
+    const int sc = L.sc;
+    float* P = setup_P32(a, L);
+    __nv_bfloat16* P16 = a.wbf16 ? (__nv_bfloat16*)L.P32 : nullptr;
+    float* delta = (float*)L.f;
+    const Src5f s5{a.K, a.code, L.side};
+    const Src9f s9{setup_A32(a, L), L.side, L.n};
+    if (kind < 2) {
+        const unsigned ncell = (unsigned)(sc + 1) * (sc + 1);
+        for (unsigned t = (unsigned)start; t < ncell; t += (unsigned)stride) {
+            if (l == 0) {
+                if (kind == 0) interp_edges_item_f(s5, sc, t, P, P16, delta);
+                else interp_corners_item_f(s5, sc, t, P, P16, delta);
+            } else {
+                if (kind == 0) interp_edges_item_f(s9, sc, t, P, P16, delta);
+                else interp_corners_item_f(s9, sc, t, P, P16, delta);
+            }
+        }
+    } else {
+        const LevelArgs& C = a.L[l + 1];
+        float* Ac = setup_A32(a, C);
+        __nv_bfloat16* A16 = a.wbf16 ? (__nv_bfloat16*)C.A32 : nullptr;
+        const unsigned nc = (unsigned)sc * sc;
+        for (unsigned t = (unsigned)start; t < nc; t += (unsigned)stride) {
+            if (l == 0) rap_item_f(s5, sc, t, P, delta, Ac, A16);
+            else rap_item_f(s9, sc, t, P, delta, Ac, A16);
+        }
+    }
+}
+
 // Set-up item kinds of one level: 0 edge weights, 1 corner weights, 2 Galerkin rows.
 __device__ void setup_items(const SolveArgs& a, int l, int kind, size_t start, size_t stride) {
+    if (a.mixed) {
+        setup_items_f(a, l, kind, start, stride);
+        return;
+    }
     const LevelArgs& L = a.L[l];
     const int sc = L.sc;
     const WOut Pw{a.mixed && !a.wbf16 ? L.P32 : nullptr, a.wbf16 ? (__nv_bfloat16*)L.P32 : nullptr};
@@ -395,6 +443,8 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_setup(const __grid_constant__
     if (blockIdx.x == 0) {
         const LevelArgs& L = a.L[Lc];
         if (Lc == 0) coarse_invert_block(Src5{a.K, a.code, L.side}, L.side, smem, a.inv, a.inv_status);
+        else if (a.mixed)
+            coarse_invert_block(Src9fd{setup_A32(a, L), L.side, L.n}, L.side, smem, a.inv, a.inv_status);
         else coarse_invert_block(Src9{L.A64, L.side, L.n}, L.side, smem, a.inv, a.inv_status);
     }
 }

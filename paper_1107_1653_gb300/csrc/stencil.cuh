@@ -322,7 +322,8 @@ __device__ __forceinline__ auto restrict_weight(const W* P, int sc, int I, int J
 
 // Adds v to the coarse stencil entry towards (I + tx, J + ty) if that point is
 // an unknown (coarse boundary points carry the Dirichlet value 0).
-__device__ __forceinline__ void rap_add(double acc[9], int I, int J, int sc, int tx, int ty, double v) {
+template <typename V>
+__device__ __forceinline__ void rap_add(V acc[9], int I, int J, int sc, int tx, int ty, V v) {
     if (I + tx >= 0 && I + tx < sc && J + ty >= 0 && J + ty < sc) acc[dir_of(tx, ty)] += v;
 }
 
@@ -331,8 +332,9 @@ __device__ __forceinline__ void rap_add(double acc[9], int I, int J, int sc, int
 // (2I+1, 2J+1).  After unrolling, qx and qy are constants: the point's type
 // (C, x-edge, y-edge, corner), its cell and its coarse targets fold away and
 // acc stays in registers.
-__device__ __forceinline__ void rap_scatter(const double* P, int sc, int I, int J, int qx, int qy,
-                                            double RA, double acc[9]) {
+template <typename V>
+__device__ __forceinline__ void rap_scatter(const V* P, int sc, int I, int J, int qx, int qy, V RA,
+                                            V acc[9]) {
     const int nc1 = sc + 1;
     const size_t ncell = (size_t)nc1 * nc1;
     const bool xC = (qx & 1) == 0, yC = (qy & 1) == 0;
@@ -401,6 +403,250 @@ __device__ __forceinline__ void rap_item(const Src& src, int sc, size_t t, const
         Aw.put(t, s);
 #pragma unroll
         for (int d = 1; d < 9; ++d) Aw.put(d * nc + t, acc[d]);
+    }
+}
+
+// ------------------------------------------------------------------ float32 set-up
+// The mixed path builds its hierarchy in float32 (a float64 warp instruction
+// costs 64 cycles of its SM sub-partition here, a float32 one under 5).  The
+// V-cycle only needs float32 operators, but in the leakage form: each row's
+// sum s (1 - mu sum p, O(h^2) against O(1) entries) must be accurate, and a
+// sum of rounded float32 entries would lose it.  So s is carried separately
+// and never formed by summing entries:
+//  * a row is (a[9], s); a stored level holds (s, off[8]) and a[DC] = s - sum off;
+//  * interpolation weights come from the rows as in float64, and the defect
+//    of P on the constant vector, delta(g) = (P 1)(g) - 1 at each fine point g,
+//    from identities free of cancellation:
+//      edge point, row collapsed to dC:  w1 + w2 = 1 - s / dC,
+//      cell corner:  sum of its 4 weights = 1 - (s + sum_dir a[dir] delta_dir) / a[DC]
+//    (delta_dir of its four edge neighbours), less the weights towards coarse
+//    points outside the grid (only next to the boundary, where delta is O(1));
+//  * the Galerkin row sum is (P^T A P 1)(t) = sum_f R(t, f) (s_f + sum_g A(f, g) delta(g)),
+//    small terms of one sign in the interior; the Galerkin off-diagonal
+//    entries are accumulated in float32 as in float64.
+
+// Fine level rows from the float32 table, with their row sums.
+struct Src5f {
+    static constexpr bool kFivePoint = true;
+    const IsaacsConsts* K;
+    const uint8_t* code;
+    int side;
+    __device__ __forceinline__ void row(int i, int j, float a[9], float* s) const {
+        const int c = code[(size_t)j * side + i];
+        const float* am = K->amf[c];
+        a[DC] = am[0];
+        a[DW] = i > 0 ? am[1] : 0.0f;
+        a[DE] = i + 1 < side ? am[2] : 0.0f;
+        a[DS] = j > 0 ? am[3] : 0.0f;
+        a[DN] = j + 1 < side ? am[4] : 0.0f;
+        a[DSW] = a[DSE] = a[DNW] = a[DNE] = 0.0f;
+        *s = l0_rowsum_f(K, c, i, j, side);
+    }
+};
+
+// Stored float32 leakage rows [9][n] (row sum, then the off-diagonal entries).
+struct Src9f {
+    static constexpr bool kFivePoint = false;
+    const float* A;
+    int side;
+    size_t n;
+    __device__ __forceinline__ void row(int i, int j, float a[9], float* s) const {
+        const size_t x = (size_t)j * side + i;
+        float d = A[x];
+        *s = d;
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+            a[k] = A[k * n + x];
+            d -= a[k];
+        }
+        a[DC] = d;
+    }
+};
+
+// The same rows promoted to float64 (for the coarsest level's explicit inverse).
+struct Src9fd {
+    const float* A;
+    int side;
+    size_t n;
+    __device__ __forceinline__ void row(int i, int j, double a[9]) const {
+        const size_t x = (size_t)j * side + i;
+        double d = A[x];
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+            a[k] = A[k * n + x];
+            d -= a[k];
+        }
+        a[DC] = d;
+    }
+};
+
+// Edge weights of cell t (as interp_edges_item) and delta (without the
+// outside-the-grid correction) at its x- and y-edge points; delta is indexed
+// like the fine level.
+template <class Src>
+__device__ __forceinline__ void interp_edges_item_f(const Src& src, int sc, unsigned t, float* P,
+                                                    __nv_bfloat16* P16, float* delta) {
+    const int nc1 = sc + 1, sf = 2 * sc + 1;
+    const size_t ncell = (size_t)nc1 * nc1;
+    const int I = (int)(t % (unsigned)nc1), J = (int)(t / (unsigned)nc1);
+    float a[9], s;
+    float wxW = 0, wxE = 0, wyS = 0, wyN = 0;
+    if (J < sc) {          // x-edge point (2I, 2J+1): row collapsed along y
+        src.row(2 * I, 2 * J + 1, a, &s);
+        const float dC = a[DC] + a[DS] + a[DN];
+        float d = -1.0f;
+        if (dC > 0) {
+            wxW = -(a[DW] + a[DSW] + a[DNW]) / dC;
+            wxE = -(a[DE] + a[DSE] + a[DNE]) / dC;
+            d = -s / dC;
+        }
+        delta[(size_t)(2 * J + 1) * sf + 2 * I] = d;
+    }
+    if (I < sc) {          // y-edge point (2I+1, 2J): row collapsed along x
+        src.row(2 * I + 1, 2 * J, a, &s);
+        const float dC = a[DC] + a[DW] + a[DE];
+        float d = -1.0f;
+        if (dC > 0) {
+            wyS = -(a[DS] + a[DSW] + a[DSE]) / dC;
+            wyN = -(a[DN] + a[DNW] + a[DNE]) / dC;
+            d = -s / dC;
+        }
+        delta[(size_t)(2 * J) * sf + 2 * I + 1] = d;
+    }
+    P[PXW * ncell + t] = wxW;
+    P[PXE * ncell + t] = wxE;
+    P[PYS * ncell + t] = wyS;
+    P[PYN * ncell + t] = wyN;
+    if (P16) {
+        P16[PXW * ncell + t] = __float2bfloat16_rn(wxW);
+        P16[PXE * ncell + t] = __float2bfloat16_rn(wxE);
+        P16[PYS * ncell + t] = __float2bfloat16_rn(wyS);
+        P16[PYN * ncell + t] = __float2bfloat16_rn(wyN);
+    }
+}
+
+// Corner weights of cell t (as interp_corners_item), delta at the corner
+// (from its edge neighbours' delta) and delta = 0 at the cell's C point.
+template <class Src>
+__device__ __forceinline__ void interp_corners_item_f(const Src& src, int sc, unsigned t, float* P,
+                                                      __nv_bfloat16* P16, float* delta) {
+    const int nc1 = sc + 1, sf = 2 * sc + 1;
+    const size_t ncell = (size_t)nc1 * nc1;
+    const int I = (int)(t % (unsigned)nc1), J = (int)(t / (unsigned)nc1);
+    float a[9], s;
+    src.row(2 * I, 2 * J, a, &s);
+    const size_t cW = t - 1, cS = t - nc1;
+    const float yS_W = I >= 1 ? P[PYS * ncell + cW] : 0.0f, yN_W = I >= 1 ? P[PYN * ncell + cW] : 0.0f;
+    const float yS_E = I < sc ? P[PYS * ncell + t] : 0.0f, yN_E = I < sc ? P[PYN * ncell + t] : 0.0f;
+    const float xW_S = J >= 1 ? P[PXW * ncell + cS] : 0.0f, xE_S = J >= 1 ? P[PXE * ncell + cS] : 0.0f;
+    const float xW_N = J < sc ? P[PXW * ncell + t] : 0.0f, xE_N = J < sc ? P[PXE * ncell + t] : 0.0f;
+    // delta of the four edge neighbours (2I -+ 1, 2J) and (2I, 2J -+ 1)
+    const float dW = I >= 1 ? delta[(size_t)(2 * J) * sf + 2 * I - 1] : 0.0f;
+    const float dE = I < sc ? delta[(size_t)(2 * J) * sf + 2 * I + 1] : 0.0f;
+    const float dS = J >= 1 ? delta[(size_t)(2 * J - 1) * sf + 2 * I] : 0.0f;
+    const float dN = J < sc ? delta[(size_t)(2 * J + 1) * sf + 2 * I] : 0.0f;
+    float wSW = 0, wSE = 0, wNW = 0, wNE = 0, d = -1.0f;
+    if (a[DC] > 0) {
+        const float inv = 1.0f / a[DC];
+        wSW = -(a[DSW] + a[DW] * yS_W + a[DS] * xW_S) * inv;
+        wSE = -(a[DSE] + a[DE] * yS_E + a[DS] * xE_S) * inv;
+        wNW = -(a[DNW] + a[DW] * yN_W + a[DN] * xW_N) * inv;
+        wNE = -(a[DNE] + a[DE] * yN_E + a[DN] * xE_N) * inv;
+        d = -(s + a[DW] * dW + a[DE] * dE + a[DS] * dS + a[DN] * dN) * inv;
+    }
+    delta[(size_t)(2 * J) * sf + 2 * I] = d;
+    if (I < sc && J < sc) delta[(size_t)(2 * J + 1) * sf + 2 * I + 1] = 0.0f;
+    P[PSW * ncell + t] = wSW;
+    P[PSE * ncell + t] = wSE;
+    P[PNW * ncell + t] = wNW;
+    P[PNE * ncell + t] = wNE;
+    if (P16) {
+        P16[PSW * ncell + t] = __float2bfloat16_rn(wSW);
+        P16[PSE * ncell + t] = __float2bfloat16_rn(wSE);
+        P16[PNW * ncell + t] = __float2bfloat16_rn(wNW);
+        P16[PNE * ncell + t] = __float2bfloat16_rn(wNE);
+    }
+}
+
+// delta(g) = (P 1)(g) - 1 at the fine point (gi, gj) in the grid: the stored
+// value less the weights towards coarse points outside the grid.
+__device__ __forceinline__ float delta_at(const float* P, const float* delta, int sc, int gi,
+                                          int gj) {
+    const int oi = gi & 1, oj = gj & 1;
+    if (oi && oj) return 0.0f;   // C point: interpolates itself
+    const int nc1 = sc + 1, sf = 2 * sc + 1;
+    const size_t ncell = (size_t)nc1 * nc1;
+    const int I = gi >> 1, J = gj >> 1;
+    const size_t c = (size_t)J * nc1 + I;
+    float d = delta[(size_t)gj * sf + gi];
+    if (!oi) {
+        if (oj) {            // x-edge: sources (I - 1, J) and (I, J)
+            if (I == 0) d -= P[PXW * ncell + c];
+            if (I == sc) d -= P[PXE * ncell + c];
+        } else {             // corner: sources (I - 1 or I, J - 1 or J)
+            const bool w = I == 0, e = I == sc, so = J == 0, no = J == sc;
+            if (w || so) d -= P[PSW * ncell + c];
+            if (e || so) d -= P[PSE * ncell + c];
+            if (w || no) d -= P[PNW * ncell + c];
+            if (e || no) d -= P[PNE * ncell + c];
+        }
+    } else {                 // y-edge: sources (I, J - 1) and (I, J)
+        if (J == 0) d -= P[PYS * ncell + c];
+        if (J == sc) d -= P[PYN * ncell + c];
+    }
+    return d;
+}
+
+// Galerkin coarse row t in float32 leakage form: Ac[t] = its row sum from
+// R (s + A delta), Ac[d * nc + t] = its off-diagonal entries (and A16 their
+// bfloat16 copy when given).
+template <class Src>
+__device__ __forceinline__ void rap_item_f(const Src& src, int sc, unsigned t, const float* P,
+                                           const float* delta, float* Ac, __nv_bfloat16* A16) {
+    const unsigned nc = (unsigned)sc * sc;
+    const int I = (int)(t % (unsigned)sc), J = (int)(t / (unsigned)sc);
+    const int sf = 2 * sc + 1;
+    float dl[5][5];
+#pragma unroll
+    for (int qy = -2; qy <= 2; ++qy)
+#pragma unroll
+        for (int qx = -2; qx <= 2; ++qx) {
+            const int gi = 2 * I + 1 + qx, gj = 2 * J + 1 + qy;
+            const bool in = gi >= 0 && gj >= 0 && gi < sf && gj < sf;
+            dl[qy + 2][qx + 2] = in ? delta_at(P, delta, sc, gi, gj) : 0.0f;
+        }
+    float acc[9];
+#pragma unroll
+    for (int d = 0; d < 9; ++d) acc[d] = 0.0f;
+    float rowsum = 0.0f;
+#pragma unroll
+    for (int oy = -1; oy <= 1; ++oy) {
+#pragma unroll
+        for (int ox = -1; ox <= 1; ++ox) {
+            const float R = restrict_weight(P, sc, I, J, ox, oy);
+            float a[9], s;
+            src.row(2 * I + 1 + ox, 2 * J + 1 + oy, a, &s);
+            float inner = s;   // (A (P 1))(f) = s_f + sum_g A(f, g) delta(g)
+#pragma unroll
+            for (int d = 0; d < 9; ++d) {
+                if constexpr (Src::kFivePoint)
+                    if (d >= DSW) continue;
+                const int qx = ox + dir_di(d), qy = oy + dir_dj(d);
+                inner += a[d] * dl[qy + 2][qx + 2];
+                const int gi = 2 * I + 1 + qx, gj = 2 * J + 1 + qy;
+                if (gi < 0 || gj < 0 || gi >= sf || gj >= sf) continue;
+                rap_scatter(P, sc, I, J, qx, qy, R * a[d], acc);
+            }
+            rowsum += R * inner;
+        }
+    }
+    Ac[t] = rowsum;
+#pragma unroll
+    for (int d = 1; d < 9; ++d) Ac[d * nc + t] = acc[d];
+    if (A16) {
+        A16[t] = __float2bfloat16_rn(rowsum);
+#pragma unroll
+        for (int d = 1; d < 9; ++d) A16[d * nc + t] = __float2bfloat16_rn(acc[d]);
     }
 }
 
