@@ -79,6 +79,7 @@ struct IsaacsConsts {
     // Factored Shapley rows: mu w0 (no-drift weight), mu delta (half-drift
     // weight), 0.1 kappa (reward per unit of a - b).
     double w0mu, gmu, c01;
+    float w0mu_f, gmu_f, c01_f, h_f;   // the same and h rounded to float32 (screening)
 };
 
 // Device-side scalars: reductions written by kernels, read by the host once
@@ -115,6 +116,34 @@ struct FastDiv {
         return q;
     }
 };
+
+// Conversions between binary64 and binary32 done on the integer pipe from
+// the IEEE 754 encodings (a float64-pipe conversion costs as much as a float64
+// operation on this part).  Both give exactly the hardware conversions'
+// results; values whose binary32 image is zero, subnormal, infinite or NaN
+// take the hardware conversion.
+// binary64 -> binary32, round to nearest, ties to even.
+__device__ __forceinline__ float f64_to_f32(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    if ((b << 1) == 0) return __uint_as_float((unsigned)(b >> 32));   // signed zero
+    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    if (e <= 0 || e >= 255) return (float)x;
+    const unsigned mant = (unsigned)((b >> 29) & 0x7fffff);
+    const unsigned rest = (unsigned)(b & 0x1fffffff);   // the 29 bits dropped
+    unsigned f = (unsigned)(b >> 32 & 0x80000000u) | ((unsigned)e << 23) | mant;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) ++f;   // may carry into the exponent
+    return __uint_as_float(f);
+}
+
+// binary32 -> binary64 (exact).
+__device__ __forceinline__ double f32_to_f64(float v) {
+    const unsigned b = __float_as_uint(v);
+    const unsigned e = (b >> 23) & 0xff;
+    if ((b & 0x7fffffffu) == 0) return __hiloint2double((int)(b & 0x80000000u), 0);
+    if (e == 0 || e == 255) return (double)v;
+    const unsigned hi = (b & 0x80000000u) | ((e + (1023 - 127)) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)((b & 7u) << 29));
+}
 
 // Largest Isaacs grid side: keeps every level index below 2^28 (FastDiv).
 constexpr int kIsaacsMaxSide = 16383;

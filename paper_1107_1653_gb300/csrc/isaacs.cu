@@ -42,6 +42,17 @@ __device__ __forceinline__ double obstacle_psi(int i, int j, double h) {
     return 0.2 - (x1 * x1 + x2 * x2);
 }
 
+// Maximum of non-negative doubles through their bit patterns (integer ops).
+__device__ __forceinline__ unsigned long long warp_max_bits(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, b, o);
+        b = w > b ? w : b;
+    }
+    return b;
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -89,6 +100,35 @@ __device__ __forceinline__ int reply_b(const double T[4], double A, double D, do
     return (u[bcur] - m > tau) ? first : bcur;
 }
 
+// MIN's reply at fixed a screened in float32: the float32 copies of the u_b
+// are within err of the float64 values the exact path compares (err bounds
+// the float32 rounding of the inputs and of every operation, with a wide
+// margin), so when the smallest float32 u_b beats every other by more than
+// 2 err + tau, the float64 comparisons pick the same index, and with the
+// keep-current rule the reply is that index.  Returns false (undecided)
+// otherwise.  *phi = A_a + min_b u_b in float32.
+__device__ __forceinline__ bool screen_reply(const float Tf[4], float Af, float Df, int a, float err,
+                                             float tauf, int* b_out, float* phi) {
+    float u[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) u[b] = (b == a) ? Df - Af : Tf[b];
+    float m1 = u[0], m2 = INFINITY;
+    int first = 0;
+#pragma unroll
+    for (int b = 1; b < 4; ++b) {
+        if (u[b] < m1) {
+            m2 = m1;
+            m1 = u[b];
+            first = b;
+        } else if (u[b] < m2) {
+            m2 = u[b];
+        }
+    }
+    *b_out = first;
+    *phi = Af + m1;
+    return m2 - m1 > 2.0f * err + tauf;
+}
+
 template <int MODE>
 __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, int variant,
                                  const double* __restrict__ v, const double* __restrict__ r0,
@@ -101,7 +141,8 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
     double res = 0.0;
     int changed = 0, code_changed = 0;
     if (active) {
-        const int i = (int)(x % side), j = (int)(x / side);
+        unsigned iu;
+        const int j = (int)FastDiv((unsigned)side).divmod((unsigned)x, &iu), i = (int)iu;
         const double tau = tau_host >= 0.0
                                ? tau_host
                                : 1e-13 * fmax(1.0, __longlong_as_double((long long)sc->vmax));
@@ -112,47 +153,132 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
         nb.vN = j + 1 < side ? v[x + side] : 0.0;
         nb.vS = j > 0 ? v[x - side] : 0.0;
         const double rx = r0[x];
-        const double g = K->gmu, c = K->c01;
-        const double base = K->w0mu * (nb.vE + nb.vW + nb.vN + nb.vS) + rx;
-        const double D = 2.0 * g * nb.vx;
-        // T_b = g v(x - e_b) - c b for b = +x1, -x1, +x2, -x2
-        const double T[4] = {g * nb.vW, g * nb.vE - c, g * nb.vS - 2.0 * c, g * nb.vN - 3.0 * c};
-        // A_a = g v(x + e_a) + c a
-        const double A[4] = {g * nb.vE, g * nb.vW + c, g * nb.vN + 2.0 * c, g * nb.vS + 3.0 * c};
         const int acur = alpha[x];
         const uint32_t bw = beta[x];
+        const int m1 = variant == 1 ? 5 : 4;
+
+        // ---- float32 screen of every decision this mode takes
+        const float fx = f64_to_f32(nb.vx), fE = f64_to_f32(nb.vE), fW = f64_to_f32(nb.vW),
+                    fN = f64_to_f32(nb.vN), fS = f64_to_f32(nb.vS);
+        const float gf = K->gmu_f, cf = K->c01_f, tauf = f64_to_f32(tau);
+        const float Vm = fmaxf(fmaxf(fabsf(fx), fmaxf(fabsf(fE), fabsf(fW))), fmaxf(fabsf(fN), fabsf(fS)));
+        const float err = 0x1p-18f * (3.0f * gf * Vm + 6.0f * cf);
+        const float Tf[4] = {gf * fW, gf * fE - cf, gf * fS - 2.0f * cf, gf * fN - 3.0f * cf};
+        const float Af[4] = {gf * fE, gf * fW + cf, gf * fN + 2.0f * cf, gf * fS + 3.0f * cf};
+        const float Df = 2.0f * gf * fx;
+        bool sure = true;
         uint32_t bnew = bw;
-        int anew = acur;
+        int anew = acur, amax = acur;
+        int bfirst[4];
         if (MODE == IMP_INNER) {
             if (acur < 4) {
-                const int bc = (bw >> (8 * acur)) & 0xff;
-                double fmin;
-                const int b = reply_b(T, A[acur], D, base, acur, bc, tau, &fmin);
-                if (b != bc) {
-                    changed = 1;
-                    bnew = (bw & ~(0xffu << (8 * acur))) | ((uint32_t)b << (8 * acur));
-                }
+                float phi;
+                // select, not index: a runtime index would put Af in local memory
+                const float Aa = acur == 0 ? Af[0] : acur == 1 ? Af[1] : acur == 2 ? Af[2] : Af[3];
+                sure = screen_reply(Tf, Aa, Df, acur, err, tauf, &bfirst[0], &phi);
+                bnew = (bw & ~(0xffu << (8 * acur))) | ((uint32_t)bfirst[0] << (8 * acur));
             }
         } else {
-            double Fa[5];
+            float G[5];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const int bc = (bw >> (8 * a)) & 0xff;
-                const int b = reply_b(T, A[a], D, base, a, bc, tau, &Fa[a]);
-                bnew = (bnew & ~(0xffu << (8 * a))) | ((uint32_t)b << (8 * a));
+                sure &= screen_reply(Tf, Af[a], Df, a, err, tauf, &bfirst[a], &G[a]);
+                bnew = (bnew & ~(0xffu << (8 * a))) | ((uint32_t)bfirst[a] << (8 * a));
             }
-            const int m1 = variant == 1 ? 5 : 4;
-            if (m1 == 5) Fa[4] = obstacle_psi(i, j, K->h);
-            if (MODE == IMP_OUTER) {
-                double fmax_ = Fa[0];
+            if (MODE == IMP_OUTER && sure) {
+                // F(v; x, a) = base + G_a: base cancels between the four moves,
+                // not against the stop value psi
+                float margin = 4.0f * err + tauf;
+                if (m1 == 5) {
+                    const float S = (fE + fW) + (fN + fS);
+                    const float basef = K->w0mu_f * S + f64_to_f32(rx);
+                    const float x1 = (i + 1) * K->h_f - 0.5f, x2 = (j + 1) * K->h_f - 0.5f;
+                    const float psif = 0.2f - (x1 * x1 + x2 * x2);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) G[a] += basef;
+                    G[4] = psif;
+                    margin += 0x1p-17f * (K->w0mu_f * 4.0f * Vm + fabsf(basef) + fabsf(psif) + 1.0f);
+                }
+                float g1 = G[0], g2 = -INFINITY;
                 int first = 0;
-                for (int a = 1; a < m1; ++a)
-                    if (Fa[a] > fmax_) { fmax_ = Fa[a]; first = a; }
-                anew = (fmax_ - Fa[acur] > tau) ? first : acur;
+                for (int a = 1; a < m1; ++a) {
+                    if (G[a] > g1) {
+                        g2 = g1;
+                        g1 = G[a];
+                        first = a;
+                    } else if (G[a] > g2) {
+                        g2 = G[a];
+                    }
+                }
+                sure = g1 - g2 > margin;
+                amax = first;
+                anew = first;
+            }
+        }
+
+        if (sure) {
+            // float64 only where a value is stored
+            if (MODE == IMP_OUTER) {
+                double fmax_;
+                if (amax == 4) {
+                    fmax_ = obstacle_psi(i, j, K->h);
+                } else {
+                    const double g = K->gmu, c = K->c01;
+                    const double base = K->w0mu * (nb.vE + nb.vW + nb.vN + nb.vS) + rx;
+                    const double T[4] = {g * nb.vW, g * nb.vE - c, g * nb.vS - 2.0 * c, g * nb.vN - 3.0 * c};
+                    const double A[4] = {g * nb.vE, g * nb.vW + c, g * nb.vN + 2.0 * c, g * nb.vS + 3.0 * c};
+                    const int b = bfirst[amax];
+                    const double u = (b == amax) ? 2.0 * g * nb.vx - A[amax] : T[b];
+                    fmax_ = base + A[amax] + u;
+                }
                 changed = anew != acur;
                 res = fabs(fmax_ - nb.vx);
                 if (fv) fv[x] = fmax_;
                 alpha[x] = (uint8_t)anew;
+            } else if (MODE == IMP_INNER) {
+                changed = acur < 4 && bnew != bw;
+            }
+        } else {
+            // the exact float64 path (near-ties within the screen's margin)
+            const double g = K->gmu, c = K->c01;
+            const double base = K->w0mu * (nb.vE + nb.vW + nb.vN + nb.vS) + rx;
+            const double D = 2.0 * g * nb.vx;
+            // T_b = g v(x - e_b) - c b for b = +x1, -x1, +x2, -x2
+            const double T[4] = {g * nb.vW, g * nb.vE - c, g * nb.vS - 2.0 * c, g * nb.vN - 3.0 * c};
+            // A_a = g v(x + e_a) + c a
+            const double A[4] = {g * nb.vE, g * nb.vW + c, g * nb.vN + 2.0 * c, g * nb.vS + 3.0 * c};
+            bnew = bw;
+            anew = acur;
+            if (MODE == IMP_INNER) {
+                if (acur < 4) {
+                    const int bc = (bw >> (8 * acur)) & 0xff;
+                    double fmin;
+                    const int b = reply_b(T, A[acur], D, base, acur, bc, tau, &fmin);
+                    if (b != bc) {
+                        changed = 1;
+                        bnew = (bw & ~(0xffu << (8 * acur))) | ((uint32_t)b << (8 * acur));
+                    }
+                }
+            } else {
+                double Fa[5];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int bc = (bw >> (8 * a)) & 0xff;
+                    const int b = reply_b(T, A[a], D, base, a, bc, tau, &Fa[a]);
+                    bnew = (bnew & ~(0xffu << (8 * a))) | ((uint32_t)b << (8 * a));
+                }
+                if (m1 == 5) Fa[4] = obstacle_psi(i, j, K->h);
+                if (MODE == IMP_OUTER) {
+                    double fmax_ = Fa[0];
+                    int first = 0;
+                    for (int a = 1; a < m1; ++a)
+                        if (Fa[a] > fmax_) { fmax_ = Fa[a]; first = a; }
+                    anew = (fmax_ - Fa[acur] > tau) ? first : acur;
+                    changed = anew != acur;
+                    res = fabs(fmax_ - nb.vx);
+                    if (fv) fv[x] = fmax_;
+                    alpha[x] = (uint8_t)anew;
+                }
             }
         }
         beta[x] = bnew;
@@ -170,15 +296,17 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
         code[x] = (uint8_t)new_code;
         code_changed = new_code != old_code;
     }
-    const double wres = warp_max(res);
-    const double wsq = warp_sum(res * res);
+    const unsigned long long wres = warp_max_bits(res);
     const int wch = warp_isum(changed);
     const int wcc = warp_isum(code_changed);
-    if ((threadIdx.x & 31) == 0) {
-        if (MODE == IMP_OUTER) {
-            atomic_max_nonneg(&sc->res, wres);
+    if (MODE == IMP_OUTER) {
+        const double wsq = warp_sum(res * res);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(&sc->res, wres);
             atomicAdd(&sc->res_sq, wsq);
         }
+    }
+    if ((threadIdx.x & 31) == 0) {
         if (wch) atomicAdd(&sc->changed, wch);
         if (wcc) atomicAdd(&sc->code_changed, wcc);
     }

@@ -97,7 +97,7 @@ __device__ void relax_fine_update(const L0Op<float>& op, const LevelArgs& L, dou
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             if (mine[k]) u[x + k * st] = e[k];
-            v[x + k * st] += (double)e[k];
+            v[x + k * st] += f32_to_f64(e[k]);
         }
     }
     for (; x < n; x += st) {
@@ -110,7 +110,7 @@ __device__ void relax_fine_update(const L0Op<float>& op, const LevelArgs& L, dou
         } else {
             e = u[x];
         }
-        v[x] += (double)e;
+        v[x] += f32_to_f64(e);
     }
 }
 
@@ -488,7 +488,7 @@ __device__ void check_phase(const SolveArgs& a, int slot, size_t gt, size_t gs) 
     const FastDiv dv(side);
     auto finish = [&](unsigned x, int i, int j, double r) {
         if (r32) {
-            const float rf = (float)r;
+            const float rf = f64_to_f32(r);
             r32[x] = rf;
             if (relax0) {
                 if (((i + j) & 1) == 0) e32[x] = rf / opf.diag(i, j);
@@ -533,7 +533,7 @@ __device__ void axpy_phase(const SolveArgs& a, size_t gt, size_t gs) {
     double* __restrict__ v = a.v;
     const size_t n = a.L[0].n;
 #pragma unroll 4
-    for (size_t x = gt; x < n; x += gs) v[x] += (double)e[x];
+    for (size_t x = gt; x < n; x += gs) v[x] += f32_to_f64(e[x]);
 }
 
 // Copies the tail levels' operators and transfers (fixed during one launch)

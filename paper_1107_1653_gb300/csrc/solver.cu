@@ -186,6 +186,10 @@ IsaacsConsts make_isaacs_consts(int side, int variant, int mu_mode) {
     K.w0mu = K.mu * (0.5 / c0);
     K.gmu = K.mu * (h / (2.0 * c0));
     K.c01 = 0.1 * K.kappa;
+    K.w0mu_f = (float)K.w0mu;
+    K.gmu_f = (float)K.gmu;
+    K.c01_f = (float)K.c01;
+    K.h_f = (float)K.h;
     return K;
 }
 
