@@ -120,14 +120,39 @@ struct FastDiv {
 // Conversions between binary64 and binary32 done on the integer pipe from
 // the IEEE 754 encodings (a float64-pipe conversion costs as much as a float64
 // operation on this part).  Both give exactly the hardware conversions'
-// results; values whose binary32 image is zero, subnormal, infinite or NaN
-// take the hardware conversion.
+// results; values whose binary32 image is subnormal, infinite or NaN take the
+// hardware conversion, in a function that is not inlined so that the compiler
+// cannot turn the rare branch into a conversion every lane executes.
+static __device__ __noinline__ float f64_to_f32_hw(double x) { return (float)x; }
+
+// The bit pattern of a double through an opaque move: integer tests on it
+// must stay integer operations (a compiler may otherwise fold them back
+// into float64 compares, which cost as much as float64 arithmetic here).
+__device__ __forceinline__ unsigned long long bits_of(double x) {
+    unsigned long long b;
+    asm("mov.b64 %0, %1;" : "=l"(b) : "d"(x));
+    return b;
+}
+
+__device__ __forceinline__ double from_bits(unsigned long long b) {
+    double x;
+    asm("mov.b64 %0, %1;" : "=d"(x) : "l"(b));
+    return x;
+}
+
+// p[k] if `in`, else +0.0, chosen on the bit pattern: a select between two
+// doubles would otherwise take the float64 pipe.
+__device__ __forceinline__ double load_or_zero(const double* p, size_t k, bool in) {
+    return from_bits(in ? reinterpret_cast<const unsigned long long*>(p)[k] : 0ull);
+}
+static __device__ __noinline__ double f32_to_f64_hw(float v) { return (double)v; }
+
 // binary64 -> binary32, round to nearest, ties to even.
 __device__ __forceinline__ float f64_to_f32(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long b = bits_of(x);
     if ((b << 1) == 0) return __uint_as_float((unsigned)(b >> 32));   // signed zero
     const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
-    if (e <= 0 || e >= 255) return (float)x;
+    if (e <= 0 || e >= 255) return f64_to_f32_hw(x);
     const unsigned mant = (unsigned)((b >> 29) & 0x7fffff);
     const unsigned rest = (unsigned)(b & 0x1fffffff);   // the 29 bits dropped
     unsigned f = (unsigned)(b >> 32 & 0x80000000u) | ((unsigned)e << 23) | mant;
@@ -140,7 +165,7 @@ __device__ __forceinline__ double f32_to_f64(float v) {
     const unsigned b = __float_as_uint(v);
     const unsigned e = (b >> 23) & 0xff;
     if ((b & 0x7fffffffu) == 0) return __hiloint2double((int)(b & 0x80000000u), 0);
-    if (e == 0 || e == 255) return (double)v;
+    if (e == 0 || e == 255) return f32_to_f64_hw(v);
     const unsigned hi = (b & 0x80000000u) | ((e + (1023 - 127)) << 20) | ((b & 0x7fffffu) >> 3);
     return __hiloint2double((int)hi, (int)((b & 7u) << 29));
 }

@@ -44,7 +44,7 @@ __device__ __forceinline__ double obstacle_psi(int i, int j, double h) {
 
 // Maximum of non-negative doubles through their bit patterns (integer ops).
 __device__ __forceinline__ unsigned long long warp_max_bits(double v) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    unsigned long long b = bits_of(v);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long w = __shfl_xor_sync(0xffffffffu, b, o);
@@ -129,12 +129,64 @@ __device__ __forceinline__ bool screen_reply(const float Tf[4], float Af, float 
     return m2 - m1 > 2.0f * err + tauf;
 }
 
+// Keep-current tolerance 1e-13 max(1, |v|_inf) from the reduced |v|_inf.
+__device__ __noinline__ double tau_of_vmax(const DevScalars* sc) {
+    return 1e-13 * fmax(1.0, __longlong_as_double((long long)sc->vmax));
+}
+
+// The exact float64 decisions of one state, for the states whose float32
+// screen was not conclusive (near-ties).  Not inlined: the compiler must not
+// evaluate these float64 rows speculatively for every state.
+template <int MODE>
+__device__ __noinline__ void improve_exact(const IsaacsConsts* __restrict__ K, const Nbr nb,
+                                           double rx, int i, int j, int m1, int acur, uint32_t bw,
+                                           double tau, uint32_t* bnew_out, int* anew_out,
+                                           double* fmax_out) {
+    const double g = K->gmu, c = K->c01;
+    const double base = K->w0mu * (nb.vE + nb.vW + nb.vN + nb.vS) + rx;
+    const double D = 2.0 * g * nb.vx;
+    // T_b = g v(x - e_b) - c b for b = +x1, -x1, +x2, -x2
+    const double T[4] = {g * nb.vW, g * nb.vE - c, g * nb.vS - 2.0 * c, g * nb.vN - 3.0 * c};
+    // A_a = g v(x + e_a) + c a
+    const double A[4] = {g * nb.vE, g * nb.vW + c, g * nb.vN + 2.0 * c, g * nb.vS + 3.0 * c};
+    uint32_t bnew = bw;
+    int anew = acur;
+    if (MODE == IMP_INNER) {
+        if (acur < 4) {
+            const int bc = (bw >> (8 * acur)) & 0xff;
+            double fmin;
+            const int b = reply_b(T, A[acur], D, base, acur, bc, tau, &fmin);
+            bnew = (bw & ~(0xffu << (8 * acur))) | ((uint32_t)b << (8 * acur));
+        }
+    } else {
+        double Fa[5];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int bc = (bw >> (8 * a)) & 0xff;
+            const int b = reply_b(T, A[a], D, base, a, bc, tau, &Fa[a]);
+            bnew = (bnew & ~(0xffu << (8 * a))) | ((uint32_t)b << (8 * a));
+        }
+        if (m1 == 5) Fa[4] = obstacle_psi(i, j, K->h);
+        if (MODE == IMP_OUTER) {
+            double fmax_ = Fa[0];
+            int first = 0;
+            for (int a = 1; a < m1; ++a)
+                if (Fa[a] > fmax_) { fmax_ = Fa[a]; first = a; }
+            anew = (fmax_ - Fa[acur] > tau) ? first : acur;
+            *fmax_out = fmax_;
+        }
+    }
+    *bnew_out = bnew;
+    *anew_out = anew;
+}
+
 template <int MODE>
 __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, int variant,
                                  const double* __restrict__ v, const double* __restrict__ r0,
                                  uint8_t* __restrict__ alpha, uint32_t* __restrict__ beta,
                                  uint8_t* __restrict__ code, double* __restrict__ rhs,
-                                 double* __restrict__ fv, DevScalars* sc, double tau_host) {
+                                 double* __restrict__ fv, DevScalars* sc, double tau_host,
+                                 float tau_host_f, int tau_from_vmax) {
     const size_t n = (size_t)side * side;
     const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = x < n;
@@ -143,15 +195,12 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
     if (active) {
         unsigned iu;
         const int j = (int)FastDiv((unsigned)side).divmod((unsigned)x, &iu), i = (int)iu;
-        const double tau = tau_host >= 0.0
-                               ? tau_host
-                               : 1e-13 * fmax(1.0, __longlong_as_double((long long)sc->vmax));
         Nbr nb;
         nb.vx = v[x];
-        nb.vE = i + 1 < side ? v[x + 1] : 0.0;
-        nb.vW = i > 0 ? v[x - 1] : 0.0;
-        nb.vN = j + 1 < side ? v[x + side] : 0.0;
-        nb.vS = j > 0 ? v[x - side] : 0.0;
+        nb.vE = load_or_zero(v, x + 1, i + 1 < side);
+        nb.vW = load_or_zero(v, x - 1, i > 0);
+        nb.vN = load_or_zero(v, x + side, j + 1 < side);
+        nb.vS = load_or_zero(v, x - side, j > 0);
         const double rx = r0[x];
         const int acur = alpha[x];
         const uint32_t bw = beta[x];
@@ -160,7 +209,8 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
         // ---- float32 screen of every decision this mode takes
         const float fx = f64_to_f32(nb.vx), fE = f64_to_f32(nb.vE), fW = f64_to_f32(nb.vW),
                     fN = f64_to_f32(nb.vN), fS = f64_to_f32(nb.vS);
-        const float gf = K->gmu_f, cf = K->c01_f, tauf = f64_to_f32(tau);
+        const float gf = K->gmu_f, cf = K->c01_f;
+        const float tauf = tau_from_vmax ? f64_to_f32(tau_of_vmax(sc)) : tau_host_f;
         const float Vm = fmaxf(fmaxf(fabsf(fx), fmaxf(fabsf(fE), fabsf(fW))), fmaxf(fabsf(fN), fabsf(fS)));
         const float err = 0x1p-18f * (3.0f * gf * Vm + 6.0f * cf);
         const float Tf[4] = {gf * fW, gf * fE - cf, gf * fS - 2.0f * cf, gf * fN - 3.0f * cf};
@@ -169,7 +219,7 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
         bool sure = true;
         uint32_t bnew = bw;
         int anew = acur, amax = acur;
-        int bfirst[4];
+        int bfirst[4] = {0, 0, 0, 0};
         if (MODE == IMP_INNER) {
             if (acur < 4) {
                 float phi;
@@ -189,6 +239,7 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
                 // F(v; x, a) = base + G_a: base cancels between the four moves,
                 // not against the stop value psi
                 float margin = 4.0f * err + tauf;
+                G[4] = -INFINITY;
                 if (m1 == 5) {
                     const float S = (fE + fW) + (fN + fS);
                     const float basef = K->w0mu_f * S + f64_to_f32(rx);
@@ -201,7 +252,8 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
                 }
                 float g1 = G[0], g2 = -INFINITY;
                 int first = 0;
-                for (int a = 1; a < m1; ++a) {
+#pragma unroll
+                for (int a = 1; a < 5; ++a) {
                     if (G[a] > g1) {
                         g2 = g1;
                         g1 = G[a];
@@ -216,70 +268,35 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
             }
         }
 
+        double fmax_ = 0.0;
         if (sure) {
             // float64 only where a value is stored
             if (MODE == IMP_OUTER) {
-                double fmax_;
                 if (amax == 4) {
                     fmax_ = obstacle_psi(i, j, K->h);
                 } else {
                     const double g = K->gmu, c = K->c01;
                     const double base = K->w0mu * (nb.vE + nb.vW + nb.vN + nb.vS) + rx;
-                    const double T[4] = {g * nb.vW, g * nb.vE - c, g * nb.vS - 2.0 * c, g * nb.vN - 3.0 * c};
-                    const double A[4] = {g * nb.vE, g * nb.vW + c, g * nb.vN + 2.0 * c, g * nb.vS + 3.0 * c};
-                    const int b = bfirst[amax];
-                    const double u = (b == amax) ? 2.0 * g * nb.vx - A[amax] : T[b];
-                    fmax_ = base + A[amax] + u;
+                    const int b = amax == 0 ? bfirst[0] : amax == 1 ? bfirst[1] : amax == 2 ? bfirst[2] : bfirst[3];
+                    const double vb = b == 0 ? nb.vW : b == 1 ? nb.vE : b == 2 ? nb.vS : nb.vN;
+                    const double va = amax == 0 ? nb.vE : amax == 1 ? nb.vW : amax == 2 ? nb.vN : nb.vS;
+                    const double Aa = g * va + c * (double)amax;
+                    // u_b = g v(x - e_b) - c b, or 2 g v(x) - A_a when b == a (as reply_b forms them)
+                    const double u = (b == amax) ? 2.0 * g * nb.vx - Aa : g * vb - c * (double)b;
+                    fmax_ = base + Aa + u;
                 }
-                changed = anew != acur;
-                res = fabs(fmax_ - nb.vx);
-                if (fv) fv[x] = fmax_;
-                alpha[x] = (uint8_t)anew;
-            } else if (MODE == IMP_INNER) {
-                changed = acur < 4 && bnew != bw;
             }
         } else {
-            // the exact float64 path (near-ties within the screen's margin)
-            const double g = K->gmu, c = K->c01;
-            const double base = K->w0mu * (nb.vE + nb.vW + nb.vN + nb.vS) + rx;
-            const double D = 2.0 * g * nb.vx;
-            // T_b = g v(x - e_b) - c b for b = +x1, -x1, +x2, -x2
-            const double T[4] = {g * nb.vW, g * nb.vE - c, g * nb.vS - 2.0 * c, g * nb.vN - 3.0 * c};
-            // A_a = g v(x + e_a) + c a
-            const double A[4] = {g * nb.vE, g * nb.vW + c, g * nb.vN + 2.0 * c, g * nb.vS + 3.0 * c};
-            bnew = bw;
-            anew = acur;
-            if (MODE == IMP_INNER) {
-                if (acur < 4) {
-                    const int bc = (bw >> (8 * acur)) & 0xff;
-                    double fmin;
-                    const int b = reply_b(T, A[acur], D, base, acur, bc, tau, &fmin);
-                    if (b != bc) {
-                        changed = 1;
-                        bnew = (bw & ~(0xffu << (8 * acur))) | ((uint32_t)b << (8 * acur));
-                    }
-                }
-            } else {
-                double Fa[5];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const int bc = (bw >> (8 * a)) & 0xff;
-                    const int b = reply_b(T, A[a], D, base, a, bc, tau, &Fa[a]);
-                    bnew = (bnew & ~(0xffu << (8 * a))) | ((uint32_t)b << (8 * a));
-                }
-                if (m1 == 5) Fa[4] = obstacle_psi(i, j, K->h);
-                if (MODE == IMP_OUTER) {
-                    double fmax_ = Fa[0];
-                    int first = 0;
-                    for (int a = 1; a < m1; ++a)
-                        if (Fa[a] > fmax_) { fmax_ = Fa[a]; first = a; }
-                    anew = (fmax_ - Fa[acur] > tau) ? first : acur;
-                    changed = anew != acur;
-                    res = fabs(fmax_ - nb.vx);
-                    if (fv) fv[x] = fmax_;
-                    alpha[x] = (uint8_t)anew;
-                }
-            }
+            improve_exact<MODE>(K, nb, rx, i, j, m1, acur, bw, tau_from_vmax ? tau_of_vmax(sc) : tau_host,
+                                &bnew, &anew, &fmax_);
+        }
+        if (MODE == IMP_OUTER) {
+            changed = anew != acur;
+            res = fabs(fmax_ - nb.vx);
+            if (fv) fv[x] = fmax_;
+            alpha[x] = (uint8_t)anew;
+        } else if (MODE == IMP_INNER) {
+            changed = bnew != bw;
         }
         beta[x] = bnew;
         // policy-fixed assembly for (alpha, beta(., alpha))
@@ -296,10 +313,10 @@ __global__ void k_isaacs_improve(const IsaacsConsts* __restrict__ K, int side, i
         code[x] = (uint8_t)new_code;
         code_changed = new_code != old_code;
     }
-    const unsigned long long wres = warp_max_bits(res);
     const int wch = warp_isum(changed);
     const int wcc = warp_isum(code_changed);
     if (MODE == IMP_OUTER) {
+        const unsigned long long wres = warp_max_bits(res);
         const double wsq = warp_sum(res * res);
         if ((threadIdx.x & 31) == 0) {
             atomicMax(&sc->res, wres);
@@ -401,13 +418,13 @@ void launch_isaacs_improve(ImproveMode mode, const IsaacsConsts* K, int side, in
     const unsigned g = div_up(n, kBlock);
     switch (mode) {
     case IMP_OUTER:
-        k_isaacs_improve<IMP_OUTER><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc, tau);
+        k_isaacs_improve<IMP_OUTER><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc, tau < 0.0 ? 0.0 : tau, (float)(tau < 0.0 ? 0.0 : tau), tau < 0.0 ? 1 : 0);
         break;
     case IMP_INNER:
-        k_isaacs_improve<IMP_INNER><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc, tau);
+        k_isaacs_improve<IMP_INNER><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc, tau < 0.0 ? 0.0 : tau, (float)(tau < 0.0 ? 0.0 : tau), tau < 0.0 ? 1 : 0);
         break;
     default:
-        k_isaacs_improve<IMP_REPLY><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc, tau);
+        k_isaacs_improve<IMP_REPLY><<<g, kBlock, 0, st>>>(K, side, variant, v, r0, alpha, beta, code, rhs, fv, sc, tau < 0.0 ? 0.0 : tau, (float)(tau < 0.0 ? 0.0 : tau), tau < 0.0 ? 1 : 0);
     }
     GS_CHECK_LAUNCH();
 }

@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_setup(const __grid_constant__
 // bits, so maxima can be taken with integer operations (the float64 pipe is
 // the scarce one).
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
-    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    return bits_of(x) & 0x7fffffffffffffffull;
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {

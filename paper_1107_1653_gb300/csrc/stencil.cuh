@@ -107,14 +107,16 @@ struct L0Op<double> {
     const IsaacsConsts* K;
     const uint8_t* code;
     int side;
+    // Couplings to the boundary multiply +0 instead of being skipped: no
+    // branch or select on doubles (both would take the float64 pipe).
     __device__ __forceinline__ double resid(const double* f, const double* u, int i, int j) const {
         const size_t x = (size_t)j * side + i;
         const double* am = K->am[code[x]];
         double Au = am[0] * u[x];
-        if (i > 0) Au += am[1] * u[x - 1];
-        if (i + 1 < side) Au += am[2] * u[x + 1];
-        if (j > 0) Au += am[3] * u[x - side];
-        if (j + 1 < side) Au += am[4] * u[x + side];
+        Au = fma(am[1], load_or_zero(u, x - 1, i > 0), Au);
+        Au = fma(am[2], load_or_zero(u, x + 1, i + 1 < side), Au);
+        Au = fma(am[3], load_or_zero(u, x - side, j > 0), Au);
+        Au = fma(am[4], load_or_zero(u, x + side, j + 1 < side), Au);
         return f[x] - Au;
     }
     // Gauss-Seidel value of u at (i, j) (neighbours from u; zero: u == 0).
