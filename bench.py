@@ -68,6 +68,12 @@ def mg_cycle_bytes(n: int, prec: str, launches: int, cycles: int) -> float:
     return n * (launches * b["check"] + cycles * (b["cycle"] + b["check"]))
 
 
+# DRAM bytes per k_mg_cycles launch from the committed full capture of the
+# current kernel (profiles/k_mg_cycles_isaacs1023_mixed.md): read + write,
+# with ncu's cache flush before the launch.  Keyed by (side, precision).
+PROFILED_TRAFFIC = {(1023, "mixed"): 45.9e6 + 1.57e6}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -484,7 +490,8 @@ def run_ours(args):
         ach = bpl / avg_s / 1e9
         line["roofline"] = {"kernel": "k_mg_cycles", "bound": "hbm", "achieved": ach,
                             "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                            "peak_source": peak_kind, "traffic": None,
+                            "peak_source": peak_kind,
+                            "traffic": PROFILED_TRAFFIC.get((SIDE, prec)),
                             "launches": tr_n, "avg_us": avg_s * 1e6,
                             "algorithmic_bytes_per_launch": bpl,
                             "note": ("working set fits in L2 (129 MB)" if SIDE <= 1023 else
