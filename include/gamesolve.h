@@ -87,7 +87,8 @@ typedef struct {
                               rebuild); the float64 residual test keeps the solution exact */
     int32_t grid_blocks;   /* cap on the thread blocks of one grid-wide launch (0 = the whole
                               GPU); lets solvers on different streams share the GPU */
-    int32_t reserved1;
+    int32_t cycle_gamma;   /* coarse-grid visits per level visit (Algorithm 3's gamma): 1 V-cycles
+                              (default; 0 reads as 1), 2 W-cycles */
 } gs_options;
 
 /* Statistics of the last gamesolve_solve (the columns of the paper's tables, Sec. 6). */

@@ -37,7 +37,7 @@ class gs_options(ctypes.Structure):
         ("mu_mode", ctypes.c_int32), ("tail_side", ctypes.c_int32),
         ("mem_budget", ctypes.c_uint64), ("stream", ctypes.c_void_p),
         ("pi_rtol", ctypes.c_double), ("setup_reuse", ctypes.c_double),
-        ("grid_blocks", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("grid_blocks", ctypes.c_int32), ("cycle_gamma", ctypes.c_int32),
     ]
 
 

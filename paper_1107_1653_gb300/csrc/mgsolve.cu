@@ -338,6 +338,141 @@ __device__ bool grid_vcycle(const SolveArgs& a, const LevelArgs* tl, const doubl
     return true;
 }
 
+// ------------------------------------------------------------------ W-cycles
+// Algorithm 3 with gamma = 2 (a.gamma): each visit of level l visits level
+// l + 1 twice before prolongating.  The first visit of a level starts from
+// u = 0 (its first colour may then be done by the restriction into it); the
+// second continues from the first visit's u with the same right-hand side.
+// Written as a loop over an explicit stack of visit counts (all threads of the
+// grid, or of block 0 for the tail, follow the same path).
+//
+// One visit of the levels [lbeg, nlev) by thread block 0 on the levels' copies
+// `tl`; `zero`: u of level lbeg is zero at entry (first visit).
+template <typename T, typename W>
+__device__ void block_wcycle(const SolveArgs& a, const LevelArgs* tl, const double* inv, int lbeg,
+                             bool zero) {
+    const size_t s0 = threadIdx.x, st = blockDim.x;
+    const int Lc = a.nlev - 1;
+    const bool staged = lbeg > 0 && lbeg >= a.smem_from;
+    if (staged && zero) {
+        const T* fg = (const T*)a.L[lbeg].f;
+        T* fs = (T*)tl[lbeg].f;
+        T* us = (T*)tl[lbeg].u;
+        for (size_t k = s0; k < tl[lbeg].n; k += st) {
+            fs[k] = fg[k];
+            us[k] = T(0);
+        }
+        __syncthreads();
+    }
+    int visits[kMaxLevels];
+    int l = lbeg;
+    bool z = zero;
+    while (true) {
+        // enter a visit of level l
+        if (l == Lc) {
+            coarse_apply_block<T>(tl[Lc], inv);
+        } else {
+            const int ncol = l == 0 ? 2 : 4;
+            const bool done0 = z && (l > lbeg || (l == 0 && fine_colour0_in_check(a)));
+            for (int k = 0; k < a.nu1; ++k)
+                for (int c = 0; c < ncol; ++c) {
+                    if (done0 && k == 0 && c == 0) continue;
+                    relax_level<T, W>(a, tl[l], l, c, z && k == 0 && c == 0, s0, st);
+                    __syncthreads();
+                }
+            restrict_level<T, W>(a, tl[l], tl[l + 1], l, l + 1 < Lc && a.nu1 > 0, s0, st);
+            __syncthreads();
+            visits[l] = 0;
+            ++l;
+            z = true;
+            continue;
+        }
+        // the visit of level l is complete: return to its parent
+        while (true) {
+            if (l == lbeg) goto out;
+            --l;
+            if (++visits[l] < a.gamma) {   // visit level l + 1 again, from its current u
+                ++l;
+                z = false;
+                break;
+            }
+            const int ncol = l == 0 ? 2 : 4;
+            prolong_phase<T, W>(tl[l], tl[l + 1], s0, st);
+            __syncthreads();
+            for (int k = 0; k < a.nu2; ++k)
+                for (int c = 0; c < ncol; ++c) {
+                    relax_level<T, W>(a, tl[l], l, c, false, s0, st);
+                    __syncthreads();
+                }
+        }
+    }
+out:
+    if (staged) {
+        T* ug = (T*)a.L[lbeg].u;
+        const T* us = (const T*)tl[lbeg].u;
+        for (size_t k = s0; k < tl[lbeg].n; k += st) ug[k] = us[k];
+        __syncthreads();
+    }
+}
+
+// One W-cycle over the whole hierarchy: grid-wide levels [0, a.tail), the tail
+// by block 0 (each visit of level a.tail is one block_wcycle).
+template <typename T, typename W>
+__device__ bool grid_wcycle(const SolveArgs& a, const LevelArgs* tl, const double* inv,
+                            const GridSync& G, size_t gt, size_t gs, bool fine_zero) {
+    const int Lc = a.nlev - 1;
+    int visits[kMaxLevels];
+    int l = 0;
+    bool z = fine_zero;
+    while (true) {
+        if (l == a.tail) {
+            if (blockIdx.x == 0) block_wcycle<T, W>(a, tl, inv, a.tail, l > 0 ? z : fine_zero);
+            if (!G.sync()) return false;
+        } else {
+            const int ncol = l == 0 ? 2 : 4;
+            const bool done0 = z && (l > 0 || fine_colour0_in_check(a));
+            for (int k = 0; k < a.nu1; ++k)
+                for (int c = 0; c < ncol; ++c) {
+                    if (done0 && k == 0 && c == 0) continue;
+                    relax_level<T, W>(a, a.L[l], l, c, z && k == 0 && c == 0, gt, gs);
+                    if (!G.sync()) return false;
+                }
+            restrict_level<T, W>(a, a.L[l], a.L[l + 1], l,
+                                 l + 1 < a.tail && l + 1 < Lc && a.nu1 > 0, gt, gs);
+            if (!G.sync()) return false;
+            visits[l] = 0;
+            ++l;
+            z = true;
+            continue;
+        }
+        while (true) {
+            if (l == 0) return true;
+            --l;
+            if (++visits[l] < a.gamma) {
+                ++l;
+                z = false;
+                break;
+            }
+            const int ncol = l == 0 ? 2 : 4;
+            prolong_phase<T, W>(a.L[l], a.L[l + 1], gt, gs);
+            if (!G.sync()) return false;
+            for (int k = 0; k < a.nu2; ++k)
+                for (int c = 0; c < ncol; ++c) {
+                    if constexpr (sizeof(T) == 4) {
+                        if (l == 0 && k == a.nu2 - 1 && c == ncol - 1) {
+                            relax_fine_update(L0Op<float>{a.K, a.code, a.L[0].side}, a.L[0], a.v, c,
+                                              gt, gs);
+                            if (!G.sync()) return false;
+                            continue;
+                        }
+                    }
+                    relax_level<T, W>(a, a.L[l], l, c, false, gt, gs);
+                    if (!G.sync()) return false;
+                }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ set-up
 // Float32 storage of level l's set-up in the mixed path: the operator the
 // next level's set-up reads (leakage form) and the interpolation weights.
@@ -621,7 +756,9 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_cycles(const __grid_constant_
             a.out->rmax[slot ^ 1] = 0ull;
             a.out->vmax[slot ^ 1] = 0ull;
         }
-        if (!grid_vcycle<T, W>(a, tl, inv, G, gt, gs, a.mixed != 0)) return;
+        const bool ok = a.gamma == 2 ? grid_wcycle<T, W>(a, tl, inv, G, gt, gs, a.mixed != 0)
+                                     : grid_vcycle<T, W>(a, tl, inv, G, gt, gs, a.mixed != 0);
+        if (!ok) return;
         if (a.mixed && (a.tail == 0 || a.nu2 == 0)) {   // not fused into the fine relaxation
             axpy_phase(a, gt, gs);
             if (!G.sync()) return;

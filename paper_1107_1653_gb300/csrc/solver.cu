@@ -327,6 +327,7 @@ bool linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bo
     a.tail = tail_level(s, g);
     a.nu1 = s->opt.nu1;
     a.nu2 = s->opt.nu2;
+    a.gamma = s->opt.cycle_gamma == 2 ? 2 : 1;
     a.max_cycles = s->opt.max_cycles;
     a.mixed = mixed ? 1 : 0;
     a.wbf16 = s->opt.precision == GS_PREC_MIXED_BF16 ? 1 : 0;

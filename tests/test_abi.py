@@ -35,13 +35,14 @@ def test_struct_layouts_match_header(gs):
     # gs_options: 120 bytes, the stream pointer at 88; gs_solve_stats: 48 bytes
     assert ctypes.sizeof(gs.gs_options) == 120 and gs.gs_options.stream.offset == 88
     assert gs.gs_options.grid_blocks.offset == 112
+    assert gs.gs_options.cycle_gamma.offset == 116
     assert gs.gs_options.pi_rtol.offset == 96
     assert ctypes.sizeof(gs.gs_solve_stats) == 48
 
 
 def test_host_side_checks_without_gpu(gs):
     o = gs.default_options()
-    assert o.precision == gs.GS_PREC_FP64 and o.nu1 == 1 and o.nu2 == 1
+    assert o.precision == gs.GS_PREC_FP64 and o.nu1 == 1 and o.nu2 == 1 and o.cycle_gamma == 1
     assert gs.lib.gamesolve_strerror(gs.GS_ENOTCONV).startswith(b"iteration caps")
     # NULL out-pointer and invalid options are rejected before any CUDA call
     assert gs.lib.gamesolve_create(None, None) == gs.GS_EINVAL

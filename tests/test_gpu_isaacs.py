@@ -191,3 +191,40 @@ def test_vcycle_count_size_independent(gs, prec, tail_side):
             _, st = s.policy_solve(alpha, beta)
         assert st["cycles"] <= (20 if prec == "mixed_bf16" else 14), (side, st)
         assert st["res_inf"] < 1e-14
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("side,variant", [(15, 0), (63, 0), (255, 0), (63, 1)])
+def test_wcycle_solve_parity(gs, side, variant, prec):
+    """W-cycles (Algorithm 3 with gamma = 2, the paper's own cycle) reach the
+    oracle's value and policies like V-cycles."""
+    _, ref = oracle_solve(side, variant, 1)
+    with gs.GameSolver(precision=prec, cycle_gamma=2) as s:
+        s.set_isaacs_grid(side, variant, 1)
+        st = s.solve()
+        v = s.get_value()
+        a, b = s.get_policy()
+    assert st["converged"] == 1
+    assert rel_err(v, ref.v) <= TOL[prec], (rel_err(v, ref.v), st)
+    check_policies(a, b, ref, 5 if variant else 4)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("tail_side", [1, 15, 31, 63])
+def test_wcycle_needs_no_more_cycles_than_vcycle(gs, prec, tail_side):
+    """A W-cycle visits every coarse level twice per visit of the level above:
+    per system it needs at most as many cycles as a V-cycle, at every split
+    between grid-wide and single-block levels, and it solves the same system."""
+    rng = np.random.default_rng(13)
+    side = 255
+    alpha = rng.integers(0, 4, size=side * side).astype(np.uint8)
+    beta = rng.integers(0, 4, size=(side * side, 4)).astype(np.uint8)
+    out = {}
+    for gamma in (1, 2):
+        with gs.GameSolver(precision=prec, tail_side=tail_side, cycle_gamma=gamma) as s:
+            s.set_isaacs_grid(side, 0, 1)
+            out[gamma] = s.policy_solve(alpha, beta)
+    (wv, stv), (ww, stw) = out[1], out[2]
+    assert stw["cycles"] <= stv["cycles"], (stv, stw)
+    assert stw["res_inf"] < 1e-14
+    assert rel_err(ww, wv) <= 1e-12
