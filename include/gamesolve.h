@@ -147,6 +147,29 @@ gs_status gamesolve_set_game_batch(gs_solver* s, int32_t count, int32_t m1, int3
                                    const int32_t* col, const double* prob,
                                    const double* reward, const double* mu);
 
+/* Sets the two-sided stopping game on a line of Sec. 6.3 (Eq. (exVI2stop),
+ * discretised): states x_1..x_n, n = 2^k - 1 <= 2047 (the interior points of a
+ * uniform grid of n + 2 points), end values v_left = v(x_0), v_right =
+ * v(x_{n+1}); actions 0 = stop and 1 = continue for both players (m1 = m2 = 2):
+ *   F(v; x, a, 0) = psi2[x]   MIN stops (also when both stop),
+ *   F(v; x, 0, 1) = psi1[x]   MAX stops alone,
+ *   F(v; x, 1, 1) = (v(x-1) + v(x+1)) / 2 + c[x]   both continue (undiscounted,
+ *   the central difference of 0.5 v'' with c = h^2 r).
+ * c, psi1, psi2: n doubles each, host or device, copied; psi1 <= psi2.
+ * gamesolve_solve then runs AMGpi (options.fmg = 0) or FAMGpi from one
+ * interior point (options.fmg = 1, eps_l = options.fmg_c h_l^2; a grid twice
+ * as coarse takes the stop values at its points and 4 c), entirely on the
+ * device in one thread block: every policy-fixed system (tridiagonal) is
+ * solved by a one-dimensional algebraic multigrid (C points at odd positions,
+ * operator-dependent interpolation, Galerkin coarse operators, C/F
+ * relaxation) to the float64 floor.  get_value returns n doubles, get_policy
+ * alpha (n) and beta (2n, beta(x, a) at [2x + a]).
+ * Errors: GS_EINVAL for n not 2^k - 1 in [1, 2047], a missing array, a value
+ * not finite or psi1 > psi2. */
+gs_status gamesolve_set_stopping_line(gs_solver* s, int32_t n, const double* c,
+                                      const double* psi1, const double* psi2, double v_left,
+                                      double v_right);
+
 /* Per-game results of the last solve of a game batch: stats[4g .. 4g+3] =
  * (MAX policy iterations, linear systems, multigrid cycles, converged) and
  * res[g] = |F(v) - v|_inf at the returned value.  Either pointer may be NULL.

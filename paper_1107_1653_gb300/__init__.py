@@ -85,6 +85,8 @@ _SIGS = {
     "gamesolve_set_game_batch": (_S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P,
                                       _P, _P, _P, _P]),
     "gamesolve_get_batch_stats": (_S, [_P, _P, _P]),
+    "gamesolve_set_stopping_line": (_S, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_double,
+                                         ctypes.c_double]),
     "gamesolve_set_isaacs_grid": (_S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P]),
     "gamesolve_set_initial": (_S, [_P, _P, _P, _P]),
     "gamesolve_solve": (_S, [_P, ctypes.POINTER(gs_solve_stats)]),
@@ -204,6 +206,14 @@ class GameSolver:
         _check(lib.gamesolve_set_game(self.h, n, m1, m2, _ptr(row_ptr), _ptr(col), _ptr(prob),
                                       _ptr(reward), mu), "gamesolve_set_game")
         self.n, self.m1, self.count = n, m1, 1
+
+    def set_stopping_line(self, c, psi1, psi2, v_left, v_right):
+        c, psi1, psi2 = _as(c, np.float64), _as(psi1, np.float64), _as(psi2, np.float64)
+        n = len(c)
+        _check(lib.gamesolve_set_stopping_line(self.h, n, _ptr(c), _ptr(psi1), _ptr(psi2),
+                                               float(v_left), float(v_right)),
+               "gamesolve_set_stopping_line")
+        self.n, self.m1, self.count = n, 2, 1
 
     def set_game_batch(self, state_offsets, m1, m2, row_ptr, col, prob, reward, mu):
         off = _as(state_offsets, np.int64)

@@ -141,6 +141,18 @@ gs_status gamesolve_set_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2,
     });
 }
 
+gs_status gamesolve_set_stopping_line(gs_solver* s, int32_t n, const double* c,
+                                      const double* psi1, const double* psi2, double v_left,
+                                      double v_right) {
+    if (!s) return GS_EINVAL;
+    return guarded([&]() -> gs_status {
+        auto P = build_line_problem(s, n, c, psi1, psi2, v_left, v_right);
+        s->prob = std::move(P);
+        reset_initial(s);
+        return GS_OK;
+    });
+}
+
 gs_status gamesolve_set_game_batch(gs_solver* s, int32_t count, int32_t m1, int32_t m2,
                                    const int64_t* state_offsets, const int64_t* row_ptr,
                                    const int32_t* col, const double* prob, const double* reward,
@@ -240,15 +252,20 @@ gs_status gamesolve_solve(gs_solver* s, gs_solve_stats* stats) {
         return GS_ESTATE;
     }
     if (s->prob->kind == 2) return guarded([&]() { return run_games(s, stats); });
+    if (s->prob->kind == 3) return guarded([&]() { return run_line(s, stats); });
     return guarded([&]() { return run_solve(s, stats); });
 }
 
 gs_status gamesolve_get_value(const gs_solver* s, double* v_out, int64_t n) {
     if (!s || !v_out) return GS_EINVAL;
     if (!s->prob) return GS_ESTATE;
-    const bool games = s->prob->kind == 2;
-    const size_t total = games ? (size_t)s->prob->game->n_total : s->prob->grids.back()->n;
-    const double* src = games ? s->prob->game->v : s->prob->grids.back()->v;
+    const int kind = s->prob->kind;
+    const size_t total = kind == 2   ? (size_t)s->prob->game->n_total
+                         : kind == 3 ? (size_t)s->prob->line->n
+                                     : s->prob->grids.back()->n;
+    const double* src = kind == 2   ? s->prob->game->v
+                        : kind == 3 ? s->prob->line->v
+                                    : s->prob->grids.back()->v;
     if (n != (int64_t)total) {
         set_last_error("get_value: n = %lld, problem has %zu states", (long long)n, total);
         return GS_EINVAL;
@@ -264,6 +281,15 @@ gs_status gamesolve_get_policy(const gs_solver* s, uint8_t* alpha, uint8_t* beta
     if (!s) return GS_EINVAL;
     if (!s->prob) return GS_ESTATE;
     gs_solver* sm = const_cast<gs_solver*>(s);
+    if (s->prob->kind == 3) {
+        const LineProblem& L = *s->prob->line;
+        return guarded([&]() -> gs_status {
+            if (alpha) GS_CUDA(cudaMemcpyAsync(alpha, L.alpha, L.n, cudaMemcpyDefault, s->st));
+            if (beta) GS_CUDA(cudaMemcpyAsync(beta, L.beta, 2 * (size_t)L.n, cudaMemcpyDefault, s->st));
+            GS_CUDA(cudaStreamSynchronize(s->st));
+            return GS_OK;
+        });
+    }
     if (s->prob->kind == 2) {
         const GameProblem& G = *s->prob->game;
         return guarded([&]() -> gs_status {

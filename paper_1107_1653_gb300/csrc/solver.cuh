@@ -87,11 +87,22 @@ struct GameProblem {
     }
 };
 
+// The two-sided stopping game on a line (Sec. 6.3) on the device.
+struct LineProblem {
+    int n = 0;
+    double *c = nullptr, *psi1 = nullptr, *psi2 = nullptr;   // per state
+    double v_left = 0, v_right = 0;
+    double *v = nullptr, *res = nullptr;
+    uint8_t *alpha = nullptr, *beta = nullptr;               // beta: 2 per state
+    int* stats = nullptr;                                    // outer, systems, cycles, converged, grids
+};
+
 struct Problem {
     Problem(size_t budget, size_t held, cudaStream_t st) : arena(budget, held, st) {}
     Arena arena;
-    int kind = 0;                                // 1 Isaacs, 2 finite games
+    int kind = 0;                                // 1 Isaacs, 2 finite games, 3 line game
     std::unique_ptr<GameProblem> game;
+    std::unique_ptr<LineProblem> line;
     std::vector<std::unique_ptr<IsaacsGrid>> grids;   // FAMGpi levels, coarse to fine
     double* xi = nullptr;                        // finest-grid noise (when given)
 };
@@ -146,6 +157,10 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
                                             const int32_t* col, const double* prob,
                                             const double* reward, const double* mu);
 gs_status run_games(gs_solver* s, gs_solve_stats* stats);
+std::unique_ptr<Problem> build_line_problem(gs_solver* s, int32_t n, const double* c,
+                                            const double* psi1, const double* psi2, double v_left,
+                                            double v_right);
+gs_status run_line(gs_solver* s, gs_solve_stats* stats);
 gs_status run_solve(gs_solver* s, gs_solve_stats* stats);
 gs_status run_improve(gs_solver* s, const double* v, uint8_t* alpha_out, uint8_t* beta_out,
                       double* fv_out);

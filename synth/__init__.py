@@ -192,3 +192,23 @@ def random_game_parallel(n: int, seed: int, m1: int = 4, m2: int = 4, k: int = 8
             prob[r0 * k:r0 * k + len(p)] = p
             reward[r0:r0 + len(rw)] = rw
     return np.arange(R + 1, dtype=np.int64) * k, col, prob, reward, float(mu)
+
+
+def stopping_line(points: int):
+    """Data of the two-sided stopping game of Sec. 6.3 on a grid of `points`
+    points over [0, 1] (h = 1/(points-1)), in the C-ABI's form for the n =
+    points - 2 interior points: the continuation reward c = h^2 r(x) with
+    r(x) = 0.5 pi^2 cos(pi x), MAX's stop value psi1 = -psi_bar and MIN's
+    psi2 = psi_bar, psi_bar = (2 cos(0.09 pi) + pi (0.18 - 1) sin(0.09 pi)) / 2,
+    and the end values v(0) = psi2, v(1) = psi1.
+
+    Returns (c, psi1, psi2, v_left, v_right).  (Deterministic problem data;
+    the game itself is solved elsewhere.)
+    """
+    m = points - 1
+    h = 1.0 / m
+    x = np.arange(1, m) * h
+    psi_bar = (2.0 * np.cos(0.09 * np.pi) + np.pi * (0.18 - 1.0) * np.sin(0.09 * np.pi)) / 2.0
+    c = h * h * 0.5 * np.pi ** 2 * np.cos(np.pi * x)
+    n = m - 1
+    return c, np.full(n, -psi_bar), np.full(n, psi_bar), float(psi_bar), float(-psi_bar)

@@ -94,3 +94,19 @@ def test_discrete_stopping_regions():
     assert np.array_equal(res.alpha[far], a_ref[far])
     b_at_alpha = res.beta[np.arange(len(x)), res.alpha]
     assert np.array_equal(b_at_alpha[far], b_ref[far, 0])
+
+
+def test_synthetic_line_data_is_the_oracle_game():
+    """The C-ABI's arrays (synth.stopping_line) describe the oracle's game."""
+    import synth
+    points = 33
+    c, p1, p2, vl, vr = synth.stopping_line(points)
+    game = s1.two_stop_game(points)
+    n = game.n
+    assert len(c) == n
+    assert np.allclose(game.rew[:, s1.STOP, s1.CONTINUE], p1, rtol=0, atol=1e-15)
+    assert np.allclose(game.rew[:, s1.CONTINUE, s1.STOP], p2, rtol=0, atol=1e-15)
+    cont = c.copy()
+    cont[0] += 0.5 * vl
+    cont[-1] += 0.5 * vr
+    assert np.allclose(game.rew[:, s1.CONTINUE, s1.CONTINUE], cont, rtol=0, atol=1e-15)
