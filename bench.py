@@ -538,6 +538,59 @@ def run_ours(args):
     return 0
 
 
+def run_line(args):
+    """The two-sided stopping game on a line (Sec. 6.3) at 2049 points: FAMGpi
+    (eps_l = 1e-2 h_l^2, eps = 1e-10, as the paper's table) timed over the
+    steps, flat AMGpi once; the discretisation errors against the exact
+    solution (the paper prints |e|_inf = 1.16e-7, |e|_L2 = 7.40e-8)."""
+    import numpy as np
+    import torch
+    import synth
+    torch.cuda.set_device(0)
+    import paper_1107_1653_gb300 as gs
+    points = 2049
+    c, p1, p2, vl, vr = synth.stopping_line(points)
+    m = points - 1
+    x = np.arange(1, m) / m
+    s9, c9 = np.sin(0.09 * np.pi), np.cos(0.09 * np.pi)
+    psi = (2 * c9 + np.pi * (0.18 - 1) * s9) / 2
+    exact = np.cos(np.pi * x) + np.pi * s9 * x + (psi - c9 - 0.09 * np.pi * s9)
+    exact = np.where(x < 0.09, psi, np.where(x > 0.91, -psi, exact))
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, fmg, steps in (("famgpi", 1, args.steps), ("amgpi", 0, 1)):
+        s = gs.GameSolver(fmg=fmg, fmg_c=1e-2, eps=1e-10, max_inner=100000, max_outer=100000,
+                          stream=stream)
+        s.set_stopping_line(c, p1, p2, vl, vr)
+        for _ in range(args.warmup if fmg else 0):
+            s.solve()
+        ts = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = s.solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        e = s.get_value() - exact
+        s.close()
+        out[name] = {"ms": statistics.mean(ts), "outer": st["outer"], "systems": st["systems"],
+                     "cycles": st["cycles"], "fmg_levels": st["fmg_levels"],
+                     "e_inf": float(np.max(np.abs(e))), "e_l2": float(np.sqrt(np.mean(e * e))),
+                     "res_inf": st["res_inf"]}
+    line = {"metric": "two-sided stopping game (Sec. 6.3) solves/s at 2049 points, FAMGpi",
+            "value": 1000.0 / out["famgpi"]["ms"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["famgpi"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "stopping_line_2049", "points": points},
+            "famgpi": out["famgpi"], "amgpi_flat": out["amgpi"],
+            "speedup_famgpi_vs_flat": out["amgpi"]["ms"] / out["famgpi"]["ms"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,9 +603,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--side", type=int, default=SIDE)
-    ap.add_argument("--workload", default="isaacs", choices=["isaacs", "batch", "serving"],
+    ap.add_argument("--workload", default="isaacs", choices=["isaacs", "batch", "serving", "line"],
                     help="isaacs: the metric's 1023^2 solve (default); batch: 4096 random "
-                         "games; serving: a Poisson request stream")
+                         "games; serving: a Poisson request stream; line: the Sec. 6.3 "
+                         "stopping game at 2049 points, FAMGpi against flat AMGpi")
     ap.add_argument("--games", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--burst", type=int, default=64)
@@ -572,6 +626,8 @@ def main():
         return run_batch(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "line":
+        return run_line(args)
     return run_ours(args)
 
 

@@ -270,7 +270,7 @@ __device__ int line_improve(const LineArgs& A, const LineGrid& G, int mode, cons
         if (mode == 0) {
             const int first = Fa[1] > Fa[0] ? 1 : 0;
             anew = Fa[first] - Fa[acur] > tau ? first : acur;
-            changed = anew != acur;
+            if (anew != acur) changed = 1;
             alpha[j] = (uint8_t)anew;
             rm = fmax(rm, fabs(Fa[first] - v[j]));
         }

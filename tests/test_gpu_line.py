@@ -40,8 +40,9 @@ def gpu_solve(gs, points, fmg, **opts):
     return v, a, b, st
 
 
-@pytest.mark.parametrize("points", [9, 17, 33, 65, 129])
+@pytest.mark.parametrize("points", [9, 17, 33, 65, 129, 2049])
 def test_flat_amgpi_follows_the_oracle(gs, points):
+    """(2049 points: two states per thread of the block.)"""
     game = s1.two_stop_game(points)
     ref = oracle.policy_iteration(game)
     v, a, b, st = gpu_solve(gs, points, fmg=0)
