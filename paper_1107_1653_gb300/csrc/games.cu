@@ -50,6 +50,7 @@ __global__ void k_game_validate(GameTables T, int count, const int64_t* __restri
         }
         if (sum > 1.0 + 1e-12) err |= 8;
         if (!(fabs(T.rew[row]) <= DBL_MAX)) err |= 16;
+        if (k1 - k0 != T.row_ptr[1] - T.row_ptr[0]) err |= 32;   // rows of unequal length (allowed)
         if (err) atomicOr(bad, err);
     }
 }
@@ -57,7 +58,8 @@ __global__ void k_game_validate(GameTables T, int count, const int64_t* __restri
 // Per row: leakage 1 - mu sum_k p_k (float64) and the float32 or bfloat16 copy of p.
 __global__ void k_game_prepare(GameTables T, int count, const int64_t* __restrict__ st_off,
                                const double* __restrict__ mu, double* __restrict__ leak,
-                               float* __restrict__ prob32, __nv_bfloat16* __restrict__ prob16) {
+                               float* __restrict__ leak32, float* __restrict__ prob32,
+                               __nv_bfloat16* __restrict__ prob16) {
     const int64_t R = (int64_t)T.m1 * T.m2;
     const int64_t rows = st_off[count] * R;
     for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
@@ -76,6 +78,7 @@ __global__ void k_game_prepare(GameTables T, int count, const int64_t* __restric
             else prob32[k] = (float)T.prob[k];
         }
         leak[row] = 1.0 - mu[lo] * sum;
+        leak32[row] = (float)leak[row];
     }
 }
 
@@ -114,25 +117,53 @@ __device__ T block_sum(T v, T* red) {
 }
 
 // ------------------------------------------------------------------ one game
+// Transition probability k rounded to float32 (the screen's error bound
+// assumes float32 rounding: with bfloat16 storage it rounds the float64 value).
+__device__ __forceinline__ float prob_at_f(const GameTables& tb, int64_t k) {
+    return tb.prob16 ? f64_to_f32(tb.prob[k]) : tb.prob32[k];
+}
+
 struct Game {
     GameTables T;
     int64_t x0, n, row0;   // first state, states, first row
     double mu;
+    float mu_f;            // mu rounded to float32
     int R;                 // m1 * m2
 };
 
-// F(v; x, a, b) = mu sum_k p_k v(col_k) + r(x, a, b)  (Eq. (ILPI)); v indexed locally.
-__device__ __forceinline__ double row_value(const Game& G, int64_t row, const double* v) {
-    double s = 0.0;
-    for (int64_t k = G.T.row_ptr[row]; k < G.T.row_ptr[row + 1]; ++k)
-        s += G.T.prob[k] * v[G.T.col[k]];
-    return G.mu * s + G.T.rew[row];
+// sum_k p_k v(col_k) over a row, v indexed locally.  Two partial sums: a
+// float64 operation's latency is 64 cycles here.
+__device__ __forceinline__ double row_sum(const Game& G, int64_t row, const double* v) {
+    int64_t k0, k1;
+    row_range(G.T, row, &k0, &k1);
+    double s0 = 0.0, s1 = 0.0;
+    int64_t k = k0;
+    for (; k + 1 < k1; k += 2) {
+        s0 = fma(G.T.prob[k], v[G.T.col[k]], s0);
+        s1 = fma(G.T.prob[k + 1], v[G.T.col[k + 1]], s1);
+    }
+    if (k < k1) s0 = fma(G.T.prob[k], v[G.T.col[k]], s0);
+    return s0 + s1;
 }
 
-// Policy improvement at local state i (modes as for the Isaacs grid).
-// Returns the number of changed policy entries; *res gets |F(v) - v| (outer).
-__device__ int improve_state(const Game& G, const BatchOut& O, int mode, int64_t i, double tau,
-                             const double* v, double* res) {
+// F(v; x, a, b) = mu sum_k p_k v(col_k) + r(x, a, b)  (Eq. (ILPI)).
+__device__ __forceinline__ double row_value(const Game& G, int64_t row, const double* v) {
+    return G.mu * row_sum(G, row, v) + G.T.rew[row];
+}
+
+// The same in float32 from the float32 copies (a screen; |error| <= err_of).
+__device__ __forceinline__ float row_value_f(const Game& G, int64_t row, const float* v32) {
+    int64_t k0, k1;
+    row_range(G.T, row, &k0, &k1);
+    float s = 0.0f;
+    for (int64_t k = k0; k < k1; ++k) s = fmaf(prob_at_f(G.T, k), v32[G.T.col[k]], s);
+    return G.mu_f * s + f64_to_f32(G.T.rew[row]);
+}
+
+// The exact float64 decisions for one state (near-ties of the float32 screen).
+// Not inlined: the compiler must not evaluate these rows for every state.
+__device__ __noinline__ int improve_state_exact(const Game& G, const BatchOut& O, int mode, int64_t i,
+                                                double tau, const double* v, double* res) {
     const int m1 = G.T.m1, m2 = G.T.m2;
     const int64_t x = G.x0 + i;
     const int64_t rb = G.row0 + i * G.R;
@@ -174,6 +205,85 @@ __device__ int improve_state(const Game& G, const BatchOut& O, int mode, int64_t
     return changed;
 }
 
+// Policy improvement at local state i (modes as for the Isaacs grid), screened
+// in float32: every F(v; x, a, b) is first taken from the float32 copies of p
+// and v, within err = 2^-18 (mu |v|_inf + |r|) of its float64 value (float32
+// rounding of the inputs and of at most 10 operations, with a wide margin).
+// A decision whose best candidate beats the second by more than 2 err + tau
+// is the float64 one; otherwise the state takes the exact path.  float64 then
+// only evaluates |F(v) - v| for the chosen row (outer mode).
+// Returns the number of changed policy entries; *res gets |F(v) - v| (outer).
+__device__ int improve_state(const Game& G, const BatchOut& O, int mode, int64_t i, double tau,
+                             float tauf, float vmaxf, const double* v, double* res) {
+    const int m1 = G.T.m1, m2 = G.T.m2;
+    const int64_t x = G.x0 + i;
+    const int64_t rb = G.row0 + i * G.R;
+    const int acur = O.alpha[x];
+    const float* v32 = O.v32 + G.x0;
+    float Fa[8];
+    int bsel[8];
+    bool sure = true;
+    for (int a = 0; a < m1 && sure; ++a) {
+        if (mode == 1 && a != acur) continue;
+        float best = INFINITY, second = INFINITY, rmax = 0.0f;
+        int first = 0;
+        for (int b = 0; b < m2; ++b) {
+            const int64_t row = rb + a * m2 + b;
+            const float F = row_value_f(G, row, v32);
+            rmax = fmaxf(rmax, fabsf(f64_to_f32(G.T.rew[row])));
+            if (F < best) {
+                second = best;
+                best = F;
+                first = b;
+            } else if (F < second) {
+                second = F;
+            }
+        }
+        const float err = 0x1p-18f * (G.mu_f * vmaxf + rmax);
+        sure = m2 == 1 || second - best > 2.0f * err + tauf;
+        Fa[a] = best;
+        bsel[a] = first;
+    }
+    int anew = acur;
+    if (sure && mode == 0) {
+        float g1 = -INFINITY, g2 = -INFINITY;
+        int first = 0;
+        for (int a = 0; a < m1; ++a) {
+            if (Fa[a] > g1) {
+                g2 = g1;
+                g1 = Fa[a];
+                first = a;
+            } else if (Fa[a] > g2) {
+                g2 = Fa[a];
+            }
+        }
+        float rmax = 0.0f;
+        for (int r = 0; r < G.R; ++r) rmax = fmaxf(rmax, fabsf(f64_to_f32(G.T.rew[rb + r])));
+        const float err = 0x1p-18f * (G.mu_f * vmaxf + rmax);
+        sure = m1 == 1 || g1 - g2 > 2.0f * err + tauf;
+        anew = first;
+    }
+    if (!sure) return improve_state_exact(G, O, mode, i, tau, v, res);
+    int changed = 0;
+    for (int a = 0; a < m1; ++a) {
+        if (mode == 1 && a != acur) continue;
+        uint8_t& bref = O.beta[x * m1 + a];
+        if (bref != bsel[a]) {
+            bref = (uint8_t)bsel[a];
+            if (mode == 1) changed = 1;
+        }
+    }
+    const int64_t row = rb + anew * m2 + O.beta[x * m1 + anew];
+    if (mode == 0) {
+        changed = anew != acur;
+        *res = fabs(row_value(G, row, v) - v[i]);
+        O.alpha[x] = (uint8_t)anew;
+    }
+    O.sel[x] = row;
+    O.rhs[x] = G.T.rew[row];
+    return changed;
+}
+
 // Transition probability k in the relaxation's precision.
 template <typename T>
 __device__ __forceinline__ T prob_at(const GameTables& tb, int64_t k) {
@@ -188,26 +298,32 @@ __device__ __forceinline__ void apply_row(const Game& G, const BatchOut& O, int6
                                           T* Ae, T* diag) {
     const int64_t row = O.sel[G.x0 + i];
     const T ei = e[i];
-    const T mu = (T)G.mu;
-    T acc = (T)G.T.leak[row] * ei, off = 0;
-    for (int64_t k = G.T.row_ptr[row]; k < G.T.row_ptr[row + 1]; ++k) {
+    const T mu = sizeof(T) == 4 ? (T)G.mu_f : (T)G.mu;
+    const T leak = sizeof(T) == 4 ? (T)G.T.leak32[row] : (T)G.T.leak[row];
+    T acc = leak * ei, off = 0;
+    int64_t k0, k1;
+    row_range(G.T, row, &k0, &k1);
+    for (int64_t k = k0; k < k1; ++k) {
         const int32_t c = G.T.col[k];
         const T p = prob_at<T>(G.T, k);
         acc += mu * p * (ei - e[c]);
         if (c != i) off += mu * p;
     }
     *Ae = acc;
-    *diag = (T)G.T.leak[row] + off;
+    *diag = leak + off;
 }
 
 // Diagonal of A for the selected row: s_i + mu sum_{k: col_k != i} p_k.
 template <typename T>
 __device__ __forceinline__ T diag_row(const Game& G, const BatchOut& O, int64_t i) {
     const int64_t row = O.sel[G.x0 + i];
+    const T mu = sizeof(T) == 4 ? (T)G.mu_f : (T)G.mu;
     T off = 0;
-    for (int64_t k = G.T.row_ptr[row]; k < G.T.row_ptr[row + 1]; ++k)
-        if (G.T.col[k] != i) off += (T)G.mu * prob_at<T>(G.T, k);
-    return (T)G.T.leak[row] + off;
+    int64_t k0, k1;
+    row_range(G.T, row, &k0, &k1);
+    for (int64_t k = k0; k < k1; ++k)
+        if (G.T.col[k] != i) off += mu * prob_at<T>(G.T, k);
+    return (sizeof(T) == 4 ? (T)G.T.leak32[row] : (T)G.T.leak[row]) + off;
 }
 
 // Execution context of one game's policy iteration: which threads share the
@@ -268,19 +384,20 @@ struct GridCtx {
 // float64 residual rhs - (v - mu M v) -> C.r; returns |r|_inf, sets *vmax.
 template <typename T, class Ctx>
 __device__ double check(const Game& G, const BatchOut& O, const double* v, Ctx& C, double* vmax) {
-    double rm = 0.0, vm = 0.0;
+    // maxima on the bit patterns, conversions on the integer pipe
+    unsigned long long rm = 0, vm = 0;
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
         const int64_t row = O.sel[G.x0 + i];
-        double s = 0.0;
-        for (int64_t k = G.T.row_ptr[row]; k < G.T.row_ptr[row + 1]; ++k)
-            s += G.T.prob[k] * v[G.T.col[k]];
-        const double r = O.rhs[G.x0 + i] - (v[i] - G.mu * s);
-        C.r[i] = (T)r;
-        rm = fmax(rm, fabs(r));
-        vm = fmax(vm, fabs(v[i]));
+        const double r = O.rhs[G.x0 + i] - (v[i] - G.mu * row_sum(G, row, v));
+        if constexpr (sizeof(T) == 4) C.r[i] = f64_to_f32(r);
+        else C.r[i] = r;
+        const unsigned long long rb = bits_of(r) & 0x7fffffffffffffffull;
+        const unsigned long long vb = bits_of(v[i]) & 0x7fffffffffffffffull;
+        rm = rb > rm ? rb : rm;
+        vm = vb > vm ? vb : vm;
     }
-    *vmax = C.max(vm);
-    return C.max(rm);
+    *vmax = C.max(from_bits(vm));
+    return C.max(from_bits(rm));
 }
 
 // One two-level cycle on A e = r from e = 0, then v += e.  Returns false if a
@@ -310,7 +427,8 @@ __device__ bool cycle(const Game& G, const BatchOut& O, double* v, Ctx& C, T asu
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
         T Ae, d;
         apply_row<T>(G, O, i, C.e, &Ae, &d);
-        part += (double)(C.r[i] - Ae);
+        if constexpr (sizeof(T) == 4) part += f32_to_f64(C.r[i] - Ae);
+        else part += (double)(C.r[i] - Ae);
     }
     const double tot = C.sum(part);
     if (C.failed()) return false;
@@ -327,7 +445,14 @@ __device__ bool cycle(const Game& G, const BatchOut& O, double* v, Ctx& C, T asu
         if (!C.sync()) return false;
         T* sw = C.e; C.e = C.t; C.t = sw;
     }
-    for (int64_t i = C.begin(); i < G.n; i += C.stride()) v[i] += (double)C.e[i];
+    float* v32 = O.v32 + G.x0;
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
+        double vi = v[i];
+        if constexpr (sizeof(T) == 4) vi += f32_to_f64(C.e[i]);
+        else vi += C.e[i];
+        v[i] = vi;
+        v32[i] = f64_to_f32(vi);
+    }
     return C.sync();
 }
 
@@ -363,18 +488,23 @@ __device__ bool evaluate(const Game& G, const BatchOut& O, const BatchOpts& P, d
 template <class Ctx>
 __device__ int improve_all(const Game& G, const BatchOut& O, int mode, const double* v, Ctx& C,
                            double* res_out) {
-    double vm = 0.0;
-    for (int64_t i = C.begin(); i < G.n; i += C.stride()) vm = fmax(vm, fabs(v[i]));
-    vm = C.max(vm);
+    unsigned long long vb = 0;
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
+        const unsigned long long b = bits_of(v[i]) & 0x7fffffffffffffffull;
+        vb = b > vb ? b : vb;
+    }
+    const double vm = C.max(from_bits(vb));
     const double tau = 1e-13 * fmax(1.0, vm);
+    const float tauf = f64_to_f32(tau), vmaxf = f64_to_f32(vm);
     int changed = 0;
-    double res = 0.0;
+    unsigned long long rb = 0;
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
         double r = 0.0;
-        changed += improve_state(G, O, mode, i, tau, v, &r);
-        res = fmax(res, r);
+        changed += improve_state(G, O, mode, i, tau, tauf, vmaxf, v, &r);
+        const unsigned long long b = bits_of(r);
+        rb = b > rb ? b : rb;
     }
-    if (res_out) *res_out = C.max(res);
+    if (res_out) *res_out = C.max(from_bits(rb));
     return C.sumi(changed);
 }
 
@@ -389,12 +519,14 @@ __device__ void solve_game(const BatchArgs& B, int g, Ctx& C) {
     G.R = B.T.m1 * B.T.m2;
     G.row0 = G.x0 * G.R;
     G.mu = B.mu[g];
+    G.mu_f = f64_to_f32(G.mu);
     const BatchOut& O = B.out;
     const BatchOpts& P = B.opt;
     double* v = O.v + G.x0;
     const int a0 = P.default_alpha;
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
         v[i] = 0.0;
+        O.v32[G.x0 + i] = 0.0f;
         O.alpha[G.x0 + i] = (uint8_t)(a0 < G.T.m1 ? a0 : 0);
         for (int a = 0; a < G.T.m1; ++a) O.beta[(G.x0 + i) * G.T.m1 + a] = 0;
     }
@@ -487,10 +619,10 @@ void launch_game_validate(const GameTables& T, int count, const int64_t* st_off,
 }
 
 void launch_game_prepare(const GameTables& T, int count, const int64_t* st_off, int64_t rows,
-                         const double* mu, double* leak, float* prob32, __nv_bfloat16* prob16,
-                         cudaStream_t st) {
+                         const double* mu, double* leak, float* leak32, float* prob32,
+                         __nv_bfloat16* prob16, cudaStream_t st) {
     const unsigned g = (unsigned)std::min<int64_t>((rows + 255) / 256, 152 * 32);
-    k_game_prepare<<<std::max(1u, g), 256, 0, st>>>(T, count, st_off, mu, leak, prob32, prob16);
+    k_game_prepare<<<std::max(1u, g), 256, 0, st>>>(T, count, st_off, mu, leak, leak32, prob32, prob16);
     GS_CHECK_LAUNCH();
 }
 

@@ -19,10 +19,25 @@ struct GameTables {
     const __nv_bfloat16* prob16;   // bfloat16 copy (relaxation; null unless chosen)
     const double* rew;        // per row
     const double* leak;       // per row: 1 - mu sum_k p_k
+    const float* leak32;      // the same rounded to float32 (relaxation)
+    int64_t k_uniform;        // > 0: every row has exactly this many entries (row_ptr unused
+                              // by the walks); 0: general CSR
 };
+
+// Entries [k0, k1) of a row.
+__device__ __forceinline__ void row_range(const GameTables& T, int64_t row, int64_t* k0, int64_t* k1) {
+    if (T.k_uniform > 0) {
+        *k0 = row * T.k_uniform;
+        *k1 = *k0 + T.k_uniform;
+    } else {
+        *k0 = T.row_ptr[row];
+        *k1 = T.row_ptr[row + 1];
+    }
+}
 
 struct BatchOut {
     double* v;        // per state (global numbering): value, also the iterate
+    float* v32;       // its float32 rounding, kept beside it (screened improvement)
     uint8_t* alpha;   // per state
     uint8_t* beta;    // per state x m1
     int64_t* sel;     // per state: the selected row of the policy-fixed system
@@ -64,8 +79,8 @@ void launch_game_validate(const GameTables& T, int count, const int64_t* st_off,
 // Writes the leakage per row and the rounded copy of p (float32 into prob32, or
 // bfloat16 into prob16: exactly one of them is non-null).
 void launch_game_prepare(const GameTables& T, int count, const int64_t* st_off, int64_t rows,
-                         const double* mu, double* leak, float* prob32, __nv_bfloat16* prob16,
-                         cudaStream_t st);
+                         const double* mu, double* leak, float* leak32, float* prob32,
+                         __nv_bfloat16* prob16, cudaStream_t st);
 size_t games_smem_bytes(int max_n, bool mixed);
 void launch_games_pi(const BatchArgs& B, bool mixed, cudaStream_t st);
 // Thread blocks for the grid-wide kernel on a game of n states (cap > 0 limits them).

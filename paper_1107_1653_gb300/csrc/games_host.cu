@@ -77,8 +77,10 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
     G->prob32 = ar.alloc<float>(std::max<int64_t>(nnz, 1));
     G->rew = ar.alloc<double>(rows);
     G->leak = ar.alloc<double>(rows);
+    G->leak32 = ar.alloc<float>(rows);
     G->mu = ar.alloc<double>(count);
     G->v = ar.alloc<double>(n_total);
+    G->v32 = ar.alloc<float>(n_total);
     G->alpha = ar.alloc<uint8_t>(n_total);
     G->beta = ar.alloc<uint8_t>(n_total * m1);
     G->sel = ar.alloc<int64_t>(n_total);
@@ -109,13 +111,20 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
     int bad = 0;
     GS_CUDA(cudaMemcpyAsync(&bad, G->queue + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
-    if (bad) {
+    if (bad & 31) {
         set_last_error("set_game: invalid table (%s%s%s%s%s)", bad & 1 ? "row_ptr decreasing " : "",
                        bad & 2 ? "column out of range " : "", bad & 4 ? "probability outside [0,1] " : "",
                        bad & 8 ? "row sum above 1 " : "", bad & 16 ? "reward not finite" : "");
         throw Error{GS_EINVAL};
     }
-    launch_game_prepare(T, count, G->st_off, rows, G->mu, G->leak,
+    // rows of one length let the walks skip row_ptr (the validation flags any other)
+    if (!(bad & 32) && rows > 0) {
+        int64_t rp1 = 0;
+        GS_CUDA(cudaMemcpy(&rp1, row_ptr + 1, sizeof(int64_t), cudaMemcpyDefault));
+        G->k_uniform = rp1 > 0 ? rp1 : 0;
+        T = G->tables();
+    }
+    launch_game_prepare(T, count, G->st_off, rows, G->mu, G->leak, G->leak32,
                         G->prob_bf16 ? nullptr : G->prob32,
                         G->prob_bf16 ? (__nv_bfloat16*)G->prob32 : nullptr, st);
     GS_CUDA(cudaStreamSynchronize(st));
@@ -129,7 +138,7 @@ gs_status run_games(gs_solver* s, gs_solve_stats* stats) {
     const bool mixed = s->opt.precision != GS_PREC_FP64;
     BatchArgs B{};
     B.T = G.tables();
-    B.out = {G.v, G.alpha, G.beta, G.sel, G.rhs, G.gstats, G.gres};
+    B.out = {G.v, G.v32, G.alpha, G.beta, G.sel, G.rhs, G.gstats, G.gres};
     B.opt.max_outer = s->opt.max_outer;
     B.opt.max_inner = s->opt.max_inner;
     B.opt.max_cycles = s->opt.max_cycles;

@@ -73,6 +73,9 @@ struct GameProblem {
     double *prob = nullptr, *rew = nullptr, *leak = nullptr, *mu = nullptr, *v = nullptr,
            *rhs = nullptr, *gres = nullptr;
     float* prob32 = nullptr;   // rounded copy of prob: float32, or bfloat16 in its first half
+    float* leak32 = nullptr;   // float32 copy of leak
+    float* v32 = nullptr;      // float32 copy of v
+    int64_t k_uniform = 0;     // every row has this many entries (0: not uniform)
     bool prob_bf16 = false;
     uint8_t *alpha = nullptr, *beta = nullptr;
     int *gstats = nullptr, *queue = nullptr;
@@ -83,7 +86,7 @@ struct GameProblem {
     std::vector<double> res_h;
     GameTables tables() const {
         return {m1,   m2, row_ptr, col, prob, prob_bf16 ? nullptr : prob32,
-                prob_bf16 ? (const __nv_bfloat16*)prob32 : nullptr, rew, leak};
+                prob_bf16 ? (const __nv_bfloat16*)prob32 : nullptr, rew, leak, leak32, k_uniform};
     }
 };
 
