@@ -563,7 +563,7 @@ __device__ __forceinline__ size_t warp_spread_index() {
 
 // Interpolation weights and Galerkin operators of every level for the current
 // policy codes, then the explicit inverse of the coarsest operator.
-__global__ void __launch_bounds__(kMGThreads) k_mg_setup(const __grid_constant__ SolveArgs a) {
+__global__ void __launch_bounds__(kMGThreads, 2) k_mg_setup(const __grid_constant__ SolveArgs a) {
     extern __shared__ double smem[];
     const GridSync G{a.bar, gridDim.x};
     const size_t gt = warp_spread_index();
@@ -720,9 +720,15 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_cycles(const __grid_constant_
     if (!G.sync()) return;   // set-up complete (and error state shared)
     prof_mark(8000);
     double* inv = a.inv;
-    if (blockIdx.x == 0) stage_tail<T, W>(a, smem_c, tl, &inv);
     int slot = 0;
-    check_phase(a, slot, gt, gs);
+    if (gridDim.x > 1) {
+        // block 0 stages the tail while the others take the first residual check
+        if (blockIdx.x == 0) stage_tail<T, W>(a, smem_c, tl, &inv);
+        else check_phase(a, slot, gt - blockDim.x, gs - blockDim.x);
+    } else {
+        stage_tail<T, W>(a, smem_c, tl, &inv);
+        check_phase(a, slot, gt, gs);
+    }
     if (!G.sync()) return;
     prof_mark(6000);
     double prev = 0.0, res0 = 0.0;
