@@ -107,7 +107,7 @@ typedef struct {
 /* Fills *opt with the defaults: FP64, eps 0, max_outer 1000, max_inner 1000,
  * V(1,1), max_cycles 200, lin_tol 1e-15, coarse_max 9, flat, fmg_side 31,
  * fmg_c 0.1, literal mu, tail_side 31, no memory budget, default stream,
- * pi_rtol 1e-3, setup_reuse 1e-3, grid_blocks 0. */
+ * pi_rtol 1e-2, setup_reuse 1e-2, grid_blocks 0, cycle_gamma 1. */
 void gamesolve_default_options(gs_options* opt);
 
 /* Creates a solver on the current CUDA device.  opt may be NULL (defaults).

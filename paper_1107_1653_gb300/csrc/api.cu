@@ -74,8 +74,8 @@ void gamesolve_default_options(gs_options* o) {
     o->mu_mode = 0;
     o->mem_budget = 0;
     o->stream = nullptr;
-    o->pi_rtol = 1e-3;
-    o->setup_reuse = 1e-3;
+    o->pi_rtol = 1e-2;
+    o->setup_reuse = 1e-2;
     o->cycle_gamma = 1;
 }
 

@@ -381,6 +381,11 @@ bool linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bo
     if (do_setup) {
         g.hier_valid = true;
         g.stale_rows = 0;
+    } else if (rel_tol > 0.0 && s->mgh->out.cycles > 3) {
+        // a reused hierarchy that needs more than 3 cycles for an inexact
+        // evaluation's drop (a fresh one needs 1-2 at rel_tol 1e-2) has gone
+        // stale for the changed rows: rebuild it for the next system
+        g.hier_valid = false;
     }
     cnt.cycles += s->mgh->out.cycles;
     cnt.last_lin_res = s->mgh->out.res;
