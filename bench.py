@@ -68,10 +68,10 @@ def mg_cycle_bytes(n: int, prec: str, launches: int, cycles: int) -> float:
     return n * (launches * b["check"] + cycles * (b["cycle"] + b["check"]))
 
 
-# DRAM bytes per k_mg_cycles launch from the committed full capture of the
-# current kernel (profiles/k_mg_cycles_isaacs1023_mixed.md): read + write,
-# with ncu's cache flush before the launch.  Keyed by (side, precision).
-PROFILED_TRAFFIC = {(1023, "mixed"): 45.9e6 + 1.57e6}
+# DRAM bytes per k_mg_cycles launch from the committed full captures of the
+# current kernel (profiles/k_mg_cycles_isaacs{1023,2047}_mixed.md): read +
+# write, with ncu's cache flush before the launch.  Keyed by (side, precision).
+PROFILED_TRAFFIC = {(1023, "mixed"): 45.9e6 + 1.57e6, (2047, "mixed"): 1110e6 + 342e6}
 
 
 def load_peaks():
