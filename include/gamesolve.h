@@ -49,13 +49,18 @@ typedef enum {
 
 typedef enum {
     GS_PREC_FP64 = 0,        /* every step in float64 */
-    GS_PREC_MIXED = 1,       /* float32 V-cycles inside float64 iterative refinement */
+    GS_PREC_MIXED = 1,       /* float32 V-cycles inside float64 iterative refinement: the
+                                residual, the value update, the coarsest inverse and the
+                                stored values in float64; the Galerkin set-up (Isaacs
+                                grids) in float32 with every coarse row sum carried by
+                                cancellation-free identities, never summed from entries;
+                                improvement decisions screened in float32 with a proven
+                                margin and a float64 fallback, so they are the float64
+                                decisions.  The result meets the same float64 floor. */
     GS_PREC_MIXED_BF16 = 2   /* as MIXED, with the V-cycle's coarse operators and
                                 interpolation weights (Isaacs grids) or the transition
-                                probabilities (finite games) stored in bfloat16; the
-                                arithmetic stays float32, and residuals, Galerkin
-                                products, the coarsest solve and the improvement stay
-                                float64, so the result meets the same float64 floor */
+                                probabilities of the relaxation (finite games) stored in
+                                bfloat16; the arithmetic stays float32 */
 } gs_precision;
 
 /* Solver options.  Fill with gamesolve_default_options, then override. */

@@ -1,5 +1,6 @@
 // Two cooperative kernels per policy-fixed linear system: the Galerkin set-up,
-// then the V-cycles (Algorithm 3, gamma = 1) with the float64 stopping test.
+// then the multigrid cycles (Algorithm 3; V-cycles, or W-cycles with gamma = 2)
+// with the float64 stopping test.
 // The small coarse levels (the "tail") are relaxed by thread block 0 alone,
 // out of shared memory.  Every grid-wide wait is bounded in time; a wait that
 // gives up sets an error flag and the kernels return.
