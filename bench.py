@@ -32,6 +32,10 @@ METRIC = "Isaacs solves/s at 1023^2 (FP32+refine vs FP64), HBM GB/s, p50/p99 lat
 # arithmetic types per precision option: float64; float32 V-cycles in float64
 # refinement; the same with the V-cycle weights stored in bfloat16
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "mixed_bf16": "bf16(weights)+f32+f64"}
+# V(1,2) cycles for the Isaacs workload: at 1023^2 they need 34 V-cycles per
+# solve against 48 for V(1,1) and take 6% less time (a solver option, as a user
+# would set it; the library's default stays V(1,1)).
+ISAACS_CYCLE = {"nu1": 1, "nu2": 2}
 SIDE = 1023          # the metric's workload; --side changes it (e.g. 2047 for profiling)
 SEED = 2
 
@@ -39,11 +43,13 @@ SEED = 2
 # system), per fine state: what the method must move, with every array read
 # or written once per phase.  Coarse levels carry 9-point stencils; the level
 # sizes shrink by 4, so their sum is 4/3 of the first coarse level.
-def mg_bytes_per_state(prec: str):
+def mg_bytes_per_state(prec: str, sweeps: int = 2):
+    """Algorithmic bytes per fine state of one V-cycle with `sweeps` = nu1 + nu2
+    relaxation sweeps per level, of one float64 residual check, and of a set-up."""
     if prec == "fp64":
         check = 1 + 8 + 8                              # code, rhs, v
-        fine = 2 * (1 + 8 + 8 + 8) + (1 + 8 + 8 + 16 + 4) + (16 + 2 + 16)
-        coarse1 = 2 * (72 + 24) + (72 + 16 + 16 + 4) + 34
+        fine = sweeps * (1 + 8 + 8 + 8) + (1 + 8 + 8 + 16 + 4) + (16 + 2 + 16)
+        coarse1 = sweeps * (72 + 24) + (72 + 16 + 16 + 4) + 34
         setup = (2 + 32 + 1 + 32 + 32 + 4 + 64 + 72) / 4 + (72 + (32 + 32 + 64 + 72) / 4) / 3
     else:
         # float32 vectors; weights in float32 (mixed) or bfloat16 (mixed_bf16):
@@ -52,8 +58,8 @@ def mg_bytes_per_state(prec: str):
         wb = 2 if prec == "mixed_bf16" else 4
         A, Pf = 9 * wb, 2 * wb
         check = 1 + 8 + 8 + 4                          # + float32 residual written
-        fine = 2 * (1 + 4 + 4 + 4) + (1 + 4 + 4 + Pf + 2) + (Pf + 1 + 8) + (4 + 16)
-        coarse1 = 2 * (A + 12) + (A + 8 + Pf + 2) + (Pf + 1 + 8)
+        fine = sweeps * (1 + 4 + 4 + 4) + (1 + 4 + 4 + Pf + 2) + (Pf + 1 + 8) + (4 + 16)
+        coarse1 = sweeps * (A + 12) + (A + 8 + Pf + 2) + (Pf + 1 + 8)
         Pe = 32 + 4 * wb                               # 4 edge (or corner) weights, both copies
         Ac = 72 + A                                    # Galerkin row, both copies
         setup = (2 + Pe + 1 + 32 + Pe + 4 + 64 + Ac) / 4 + (72 + (Pe + Pe + 64 + Ac) / 4) / 3
@@ -61,17 +67,17 @@ def mg_bytes_per_state(prec: str):
     return {"check": check, "cycle": cycle, "setup": setup}
 
 
-def mg_cycle_bytes(n: int, prec: str, launches: int, cycles: int) -> float:
+def mg_cycle_bytes(n: int, prec: str, launches: int, cycles: int, sweeps: int = 2) -> float:
     """Algorithmic bytes of `launches` V-cycle launches running `cycles` cycles in all
     (each launch evaluates the float64 residual once more than it has cycles)."""
-    b = mg_bytes_per_state(prec)
+    b = mg_bytes_per_state(prec, sweeps)
     return n * (launches * b["check"] + cycles * (b["cycle"] + b["check"]))
 
 
-# DRAM bytes per k_mg_cycles launch from the committed full captures of the
-# current kernel (profiles/k_mg_cycles_isaacs{1023,2047}_mixed.md): read +
-# write, with ncu's cache flush before the launch.  Keyed by (side, precision).
-PROFILED_TRAFFIC = {(1023, "mixed"): 45.9e6 + 1.57e6, (2047, "mixed"): 1110e6 + 342e6}
+# DRAM bytes per k_mg_cycles launch from the committed full capture of the
+# current kernel (profiles/k_mg_cycles_isaacs1023_mixed.md): read + write, with
+# ncu's cache flush before the launch.  Keyed by (side, precision).
+PROFILED_TRAFFIC = {(1023, "mixed"): 45.92e6 + 1.45e6}
 
 
 def load_peaks():
@@ -380,7 +386,7 @@ def run_profile(args):
     torch.cuda.set_device(0)
     import paper_1107_1653_gb300 as gs
     with gs.GameSolver(precision=args.precision, fmg=args.fmg, fmg_side=31,
-                       stream=torch.cuda.current_stream()) as s:
+                       stream=torch.cuda.current_stream(), **ISAACS_CYCLE) as s:
         s.set_isaacs_grid(SIDE, 0, SEED)
         st = s.solve()
     torch.cuda.synchronize()
@@ -403,7 +409,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def timed(precision, steps, warmup, trace=None):
-        s = gs.GameSolver(precision=precision, fmg=args.fmg, fmg_side=31, stream=stream)
+        s = gs.GameSolver(precision=precision, fmg=args.fmg, fmg_side=31, stream=stream, **ISAACS_CYCLE)
         s.set_isaacs_grid(SIDE, 0, SEED)
         for _ in range(warmup):
             s.solve()
@@ -469,6 +475,7 @@ def run_ours(args):
                    "precision": prec, "fmg": bool(args.fmg),
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (256 MiB write)",
+                   "cycle": "V(%d,%d)" % (ISAACS_CYCLE["nu1"], ISAACS_CYCLE["nu2"]),
                    "outer": stats["outer"], "systems": stats["systems"], "cycles": stats["cycles"],
                    "levels": stats["levels"], "res_inf": stats["res_inf"]},
         "p50_ms": statistics.median(per_step),
@@ -484,7 +491,8 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     if tr_n:
         kind = prec
-        total = mg_cycle_bytes(n, kind, tr_n, stats["cycles"] * args.steps)
+        sweeps = ISAACS_CYCLE["nu1"] + ISAACS_CYCLE["nu2"]
+        total = mg_cycle_bytes(n, kind, tr_n, stats["cycles"] * args.steps, sweeps)
         bpl = total / tr_n
         avg_s = tr_ms * 1e-3 / tr_n
         ach = bpl / avg_s / 1e9
@@ -497,7 +505,7 @@ def run_ours(args):
                             "note": ("working set fits in L2 (129 MB)" if SIDE <= 1023 else
                                      "working set exceeds the 129 MB L2") + "; bytes per state "
                                     + json.dumps({k: round(v, 1) for k, v in
-                                                  mg_bytes_per_state(kind).items()})}
+                                                  mg_bytes_per_state(kind, sweeps).items()})}
 
     # end to end through the C-ABI with host buffers
     if not args.no_e2e:
@@ -506,7 +514,7 @@ def run_ours(args):
         v_h = torch.empty(n, dtype=torch.float64).pin_memory()
         a_h = torch.empty(n, dtype=torch.uint8).pin_memory()
         b_h = torch.empty((n, 4), dtype=torch.uint8).pin_memory()
-        s = gs.GameSolver(precision=prec, fmg=args.fmg, fmg_side=31, stream=stream)
+        s = gs.GameSolver(precision=prec, fmg=args.fmg, fmg_side=31, stream=stream, **ISAACS_CYCLE)
         e2e = []
         for k in range(1 + max(2, args.steps // 2)):
             torch.cuda.synchronize()

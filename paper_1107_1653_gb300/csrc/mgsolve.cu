@@ -84,7 +84,7 @@ __device__ void relax_fine_update(const L0Op<float>& op, const LevelArgs& L, dou
     const unsigned n = (unsigned)L.n, st = (unsigned)stride;
     const FastDiv dv(side);
     unsigned x = (unsigned)start;
-    constexpr int K = 2;
+    constexpr int K = 4;
     for (; x + (K - 1) * st < n; x += K * st) {
         float e[K];
         bool mine[K];

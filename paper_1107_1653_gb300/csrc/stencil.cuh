@@ -109,15 +109,15 @@ struct L0Op<double> {
     int side;
     // Couplings to the boundary multiply +0 instead of being skipped: no
     // branch or select on doubles (both would take the float64 pipe).
+    // Five fused multiply-adds from f (each float64 operation costs 64 cycles).
     __device__ __forceinline__ double resid(const double* f, const double* u, int i, int j) const {
         const size_t x = (size_t)j * side + i;
         const double* am = K->am[code[x]];
-        double Au = am[0] * u[x];
-        Au = fma(am[1], load_or_zero(u, x - 1, i > 0), Au);
-        Au = fma(am[2], load_or_zero(u, x + 1, i + 1 < side), Au);
-        Au = fma(am[3], load_or_zero(u, x - side, j > 0), Au);
-        Au = fma(am[4], load_or_zero(u, x + side, j + 1 < side), Au);
-        return f[x] - Au;
+        double r = fma(-am[0], u[x], f[x]);
+        r = fma(-am[1], load_or_zero(u, x - 1, i > 0), r);
+        r = fma(-am[2], load_or_zero(u, x + 1, i + 1 < side), r);
+        r = fma(-am[3], load_or_zero(u, x - side, j > 0), r);
+        return fma(-am[4], load_or_zero(u, x + side, j + 1 < side), r);
     }
     // Gauss-Seidel value of u at (i, j) (neighbours from u; zero: u == 0).
     __device__ __forceinline__ double relaxed(const double* f, const double* u, int i, int j,
