@@ -39,17 +39,37 @@ ISAACS_CYCLE = {"nu1": 1, "nu2": 2}
 SIDE = 1023          # the metric's workload; --side changes it (e.g. 2047 for profiling)
 SEED = 2
 
+def cycle_sweeps(cycle: dict):
+    """(nu1 + nu2 on the finest level, nu1 + nu2 on the coarse levels) of a cycle option set."""
+    fine = cycle["nu1"] + cycle["nu2"]
+    c1 = cycle.get("nu1_coarse", -1)
+    c2 = cycle.get("nu2_coarse", -1)
+    return fine, (cycle["nu1"] if c1 < 0 else c1) + (cycle["nu2"] if c2 < 0 else c2)
+
+
+def cycle_label(cycle: dict) -> str:
+    """"V(nu1,nu2)", with the coarse levels' sweeps when they differ."""
+    lab = "V(%d,%d)" % (cycle["nu1"], cycle["nu2"])
+    c1, c2 = cycle.get("nu1_coarse", -1), cycle.get("nu2_coarse", -1)
+    if c1 >= 0 or c2 >= 0:
+        lab += ", coarse levels (%d,%d)" % (cycle["nu1"] if c1 < 0 else c1,
+                                            cycle["nu2"] if c2 < 0 else c2)
+    return lab
+
+
 # Algorithmic bytes of the multigrid solve kernel (one launch per linear
 # system), per fine state: what the method must move, with every array read
 # or written once per phase.  Coarse levels carry 9-point stencils; the level
 # sizes shrink by 4, so their sum is 4/3 of the first coarse level.
-def mg_bytes_per_state(prec: str, sweeps: int = 2):
+def mg_bytes_per_state(prec: str, sweeps: int = 2, sweeps_coarse: int = None):
     """Algorithmic bytes per fine state of one V-cycle with `sweeps` = nu1 + nu2
-    relaxation sweeps per level, of one float64 residual check, and of a set-up."""
+    relaxation sweeps on the finest level and `sweeps_coarse` (default: the
+    same) on the coarse ones, of one float64 residual check, and of a set-up."""
+    sc = sweeps if sweeps_coarse is None else sweeps_coarse
     if prec == "fp64":
         check = 1 + 8 + 8                              # code, rhs, v
         fine = sweeps * (1 + 8 + 8 + 8) + (1 + 8 + 8 + 16 + 4) + (16 + 2 + 16)
-        coarse1 = sweeps * (72 + 24) + (72 + 16 + 16 + 4) + 34
+        coarse1 = sc * (72 + 24) + (72 + 16 + 16 + 4) + 34
         setup = (2 + 32 + 1 + 32 + 32 + 4 + 64 + 72) / 4 + (72 + (32 + 32 + 64 + 72) / 4) / 3
     else:
         # float32 vectors; weights in float32 (mixed) or bfloat16 (mixed_bf16):
@@ -59,7 +79,7 @@ def mg_bytes_per_state(prec: str, sweeps: int = 2):
         A, Pf = 9 * wb, 2 * wb
         check = 1 + 8 + 8 + 4                          # + float32 residual written
         fine = sweeps * (1 + 4 + 4 + 4) + (1 + 4 + 4 + Pf + 2) + (Pf + 1 + 8) + (4 + 16)
-        coarse1 = sweeps * (A + 12) + (A + 8 + Pf + 2) + (Pf + 1 + 8)
+        coarse1 = sc * (A + 12) + (A + 8 + Pf + 2) + (Pf + 1 + 8)
         Pe = 32 + 4 * wb                               # 4 edge (or corner) weights, both copies
         Ac = 72 + A                                    # Galerkin row, both copies
         setup = (2 + Pe + 1 + 32 + Pe + 4 + 64 + Ac) / 4 + (72 + (Pe + Pe + 64 + Ac) / 4) / 3
@@ -67,17 +87,18 @@ def mg_bytes_per_state(prec: str, sweeps: int = 2):
     return {"check": check, "cycle": cycle, "setup": setup}
 
 
-def mg_cycle_bytes(n: int, prec: str, launches: int, cycles: int, sweeps: int = 2) -> float:
+def mg_cycle_bytes(n: int, prec: str, launches: int, cycles: int, sweeps: int = 2,
+                   sweeps_coarse: int = None) -> float:
     """Algorithmic bytes of `launches` V-cycle launches running `cycles` cycles in all
     (each launch evaluates the float64 residual once more than it has cycles)."""
-    b = mg_bytes_per_state(prec, sweeps)
+    b = mg_bytes_per_state(prec, sweeps, sweeps_coarse)
     return n * (launches * b["check"] + cycles * (b["cycle"] + b["check"]))
 
 
-# DRAM bytes per k_mg_cycles launch from the committed full capture of the
-# current kernel (profiles/k_mg_cycles_isaacs1023_mixed.md): read + write, with
-# ncu's cache flush before the launch.  Keyed by (side, precision).
-PROFILED_TRAFFIC = {(1023, "mixed"): 45.92e6 + 1.45e6}
+# DRAM bytes per k_mg_cycles launch from the committed capture of the current
+# kernel (profiles/k_mg_cycles_isaacs1023_mixed.md): read + write, with ncu's
+# cache flush before the launch.  Keyed by (side, precision).
+PROFILED_TRAFFIC = {(1023, "mixed"): 45.91e6 + 0.95e6}
 
 
 def load_peaks():
@@ -475,7 +496,7 @@ def run_ours(args):
                    "precision": prec, "fmg": bool(args.fmg),
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (256 MiB write)",
-                   "cycle": "V(%d,%d)" % (ISAACS_CYCLE["nu1"], ISAACS_CYCLE["nu2"]),
+                   "cycle": cycle_label(ISAACS_CYCLE),
                    "outer": stats["outer"], "systems": stats["systems"], "cycles": stats["cycles"],
                    "levels": stats["levels"], "res_inf": stats["res_inf"]},
         "p50_ms": statistics.median(per_step),
@@ -491,8 +512,8 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     if tr_n:
         kind = prec
-        sweeps = ISAACS_CYCLE["nu1"] + ISAACS_CYCLE["nu2"]
-        total = mg_cycle_bytes(n, kind, tr_n, stats["cycles"] * args.steps, sweeps)
+        sweeps, sweeps_c = cycle_sweeps(ISAACS_CYCLE)
+        total = mg_cycle_bytes(n, kind, tr_n, stats["cycles"] * args.steps, sweeps, sweeps_c)
         bpl = total / tr_n
         avg_s = tr_ms * 1e-3 / tr_n
         ach = bpl / avg_s / 1e9
@@ -505,7 +526,8 @@ def run_ours(args):
                             "note": ("working set fits in L2 (129 MB)" if SIDE <= 1023 else
                                      "working set exceeds the 129 MB L2") + "; bytes per state "
                                     + json.dumps({k: round(v, 1) for k, v in
-                                                  mg_bytes_per_state(kind, sweeps).items()})}
+                                                  mg_bytes_per_state(kind, sweeps,
+                                                                     sweeps_c).items()})}
 
     # end to end through the C-ABI with host buffers
     if not args.no_e2e:

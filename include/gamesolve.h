@@ -94,6 +94,10 @@ typedef struct {
                               GPU); lets solvers on different streams share the GPU */
     int32_t cycle_gamma;   /* coarse-grid visits per level visit (Algorithm 3's gamma): 1 V-cycles
                               (default; 0 reads as 1), 2 W-cycles */
+    int32_t nu1_coarse;    /* pre-sweeps on the coarse levels of an Isaacs grid's hierarchy
+                              (-1, the default: nu1) */
+    int32_t nu2_coarse;    /* post-sweeps on those levels (-1, the default: nu2); the two
+                              together must be >= 1 */
 } gs_options;
 
 /* Statistics of the last gamesolve_solve (the columns of the paper's tables, Sec. 6). */
@@ -112,7 +116,8 @@ typedef struct {
 /* Fills *opt with the defaults: FP64, eps 0, max_outer 1000, max_inner 1000,
  * V(1,1), max_cycles 200, lin_tol 1e-15, coarse_max 9, flat, fmg_side 31,
  * fmg_c 0.1, literal mu, tail_side 31, no memory budget, default stream,
- * pi_rtol 1e-2, setup_reuse 1e-2, grid_blocks 0, cycle_gamma 1. */
+ * pi_rtol 1e-2, setup_reuse 1e-2, grid_blocks 0, cycle_gamma 1, nu1_coarse and
+ * nu2_coarse -1 (as on the finest level). */
 void gamesolve_default_options(gs_options* opt);
 
 /* Creates a solver on the current CUDA device.  opt may be NULL (defaults).

@@ -38,6 +38,7 @@ class gs_options(ctypes.Structure):
         ("mem_budget", ctypes.c_uint64), ("stream", ctypes.c_void_p),
         ("pi_rtol", ctypes.c_double), ("setup_reuse", ctypes.c_double),
         ("grid_blocks", ctypes.c_int32), ("cycle_gamma", ctypes.c_int32),
+        ("nu1_coarse", ctypes.c_int32), ("nu2_coarse", ctypes.c_int32),
     ]
 
 

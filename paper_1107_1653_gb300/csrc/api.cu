@@ -77,6 +77,8 @@ void gamesolve_default_options(gs_options* o) {
     o->pi_rtol = 1e-2;
     o->setup_reuse = 1e-2;
     o->cycle_gamma = 1;
+    o->nu1_coarse = -1;
+    o->nu2_coarse = -1;
 }
 
 gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
@@ -93,7 +95,9 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
         o.coarse_max < 1 || o.coarse_max > 64 || o.tail_side < 0 || !(o.eps >= 0) || !(o.fmg_c > 0) ||
         (o.fmg && !is_pow2m1(o.fmg_side)) || o.mu_mode < 0 || o.mu_mode > 1 ||
         !(o.pi_rtol >= 0.0 && o.pi_rtol < 1.0) || !(o.setup_reuse >= 0.0 && o.setup_reuse <= 1.0) ||
-        o.grid_blocks < 0 || o.cycle_gamma < 0 || o.cycle_gamma > 2) {
+        o.grid_blocks < 0 || o.cycle_gamma < 0 || o.cycle_gamma > 2 || o.nu1_coarse < -1 ||
+        o.nu2_coarse < -1 ||
+        (o.nu1_coarse < 0 ? o.nu1 : o.nu1_coarse) + (o.nu2_coarse < 0 ? o.nu2 : o.nu2_coarse) < 1) {
         set_last_error("create: invalid option value");
         return GS_EINVAL;
     }

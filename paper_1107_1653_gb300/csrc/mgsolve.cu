@@ -213,6 +213,11 @@ __device__ void restrict_level(const SolveArgs& a, const LevelArgs& L, const Lev
     else restrict_with<T, W>(L9Op<T, W>{(const W*)L.A, L.n, L.side}, L, C, fuse, start, stride);
 }
 
+// Relaxation sweeps on level l before and after its coarse-grid correction
+// (Algorithm 3's nu1, nu2): the finest level's counts, or the coarse levels'.
+__device__ __forceinline__ int sweeps_pre(const SolveArgs& a, int l) { return l == 0 ? a.nu1 : a.nu1c; }
+__device__ __forceinline__ int sweeps_post(const SolveArgs& a, int l) { return l == 0 ? a.nu2 : a.nu2c; }
+
 // Whether the residual check already relaxed the fine level's first colour
 // from the zero start (mixed path: the correction starts from zero).
 __device__ __forceinline__ bool fine_colour0_in_check(const SolveArgs& a) {
@@ -260,13 +265,13 @@ __device__ void block_vcycle(const SolveArgs& a, const LevelArgs* tl, const doub
         // first colour from the zero start already done by the restriction into
         // this level, or (fine level) by the residual check
         const bool done0 = z && (l > lbeg || (l == 0 && fine_colour0_in_check(a)));
-        for (int k = 0; k < a.nu1; ++k)
+        for (int k = 0; k < sweeps_pre(a, l); ++k)
             for (int c = 0; c < ncol; ++c) {
                 if (done0 && k == 0 && c == 0) continue;
                 relax_level<T, W>(a, tl[l], l, c, z && k == 0 && c == 0, s0, st);
                 __syncthreads();
             }
-        restrict_level<T, W>(a, tl[l], tl[l + 1], l, l + 1 < Lc && a.nu1 > 0, s0, st);
+        restrict_level<T, W>(a, tl[l], tl[l + 1], l, l + 1 < Lc && sweeps_pre(a, l + 1) > 0, s0, st);
         __syncthreads();
     }
     coarse_apply_block<T>(tl[Lc], inv);
@@ -274,7 +279,7 @@ __device__ void block_vcycle(const SolveArgs& a, const LevelArgs* tl, const doub
         const int ncol = l == 0 ? 2 : 4;
         prolong_phase<T, W>(tl[l], tl[l + 1], s0, st);
         __syncthreads();
-        for (int k = 0; k < a.nu2; ++k)
+        for (int k = 0; k < sweeps_post(a, l); ++k)
             for (int c = 0; c < ncol; ++c) {
                 relax_level<T, W>(a, tl[l], l, c, false, s0, st);
                 __syncthreads();
@@ -300,7 +305,7 @@ __device__ bool grid_vcycle(const SolveArgs& a, const LevelArgs* tl, const doubl
         // first colour from the zero start already done by the restriction into
         // this level, or (fine level) by the residual check
         const bool done0 = z && (l > 0 || fine_colour0_in_check(a));
-        for (int k = 0; k < a.nu1; ++k)
+        for (int k = 0; k < sweeps_pre(a, l); ++k)
             for (int c = 0; c < ncol; ++c) {
                 if (done0 && k == 0 && c == 0) continue;
                 relax_level<T, W>(a, a.L[l], l, c, z && k == 0 && c == 0, gt, gs);
@@ -308,8 +313,8 @@ __device__ bool grid_vcycle(const SolveArgs& a, const LevelArgs* tl, const doubl
                 prof_mark(1000 + 10 * l + c);
             }
         // the block relaxes level a.tail from its own staged copy: no fusion into it
-        restrict_level<T, W>(a, a.L[l], a.L[l + 1], l, l + 1 < a.tail && l + 1 < Lc && a.nu1 > 0,
-                             gt, gs);
+        restrict_level<T, W>(a, a.L[l], a.L[l + 1], l,
+                             l + 1 < a.tail && l + 1 < Lc && sweeps_pre(a, l + 1) > 0, gt, gs);
         if (!G.sync()) return false;
         prof_mark(2000 + 10 * l);
     }
@@ -321,10 +326,10 @@ __device__ bool grid_vcycle(const SolveArgs& a, const LevelArgs* tl, const doubl
         prolong_phase<T, W>(a.L[l], a.L[l + 1], gt, gs);
         if (!G.sync()) return false;
         prof_mark(3000 + 10 * l);
-        for (int k = 0; k < a.nu2; ++k)
+        for (int k = 0; k < sweeps_post(a, l); ++k)
             for (int c = 0; c < ncol; ++c) {
                 if constexpr (sizeof(T) == 4) {
-                    if (l == 0 && k == a.nu2 - 1 && c == ncol - 1) {
+                    if (l == 0 && k == sweeps_post(a, l) - 1 && c == ncol - 1) {
                         relax_fine_update(L0Op<float>{a.K, a.code, a.L[0].side}, a.L[0], a.v, c, gt, gs);
                         if (!G.sync()) return false;
                         prof_mark(1000 + 10 * l + c);
@@ -375,13 +380,13 @@ __device__ void block_wcycle(const SolveArgs& a, const LevelArgs* tl, const doub
         } else {
             const int ncol = l == 0 ? 2 : 4;
             const bool done0 = z && (l > lbeg || (l == 0 && fine_colour0_in_check(a)));
-            for (int k = 0; k < a.nu1; ++k)
+            for (int k = 0; k < sweeps_pre(a, l); ++k)
                 for (int c = 0; c < ncol; ++c) {
                     if (done0 && k == 0 && c == 0) continue;
                     relax_level<T, W>(a, tl[l], l, c, z && k == 0 && c == 0, s0, st);
                     __syncthreads();
                 }
-            restrict_level<T, W>(a, tl[l], tl[l + 1], l, l + 1 < Lc && a.nu1 > 0, s0, st);
+            restrict_level<T, W>(a, tl[l], tl[l + 1], l, l + 1 < Lc && sweeps_pre(a, l + 1) > 0, s0, st);
             __syncthreads();
             visits[l] = 0;
             ++l;
@@ -400,7 +405,7 @@ __device__ void block_wcycle(const SolveArgs& a, const LevelArgs* tl, const doub
             const int ncol = l == 0 ? 2 : 4;
             prolong_phase<T, W>(tl[l], tl[l + 1], s0, st);
             __syncthreads();
-            for (int k = 0; k < a.nu2; ++k)
+            for (int k = 0; k < sweeps_post(a, l); ++k)
                 for (int c = 0; c < ncol; ++c) {
                     relax_level<T, W>(a, tl[l], l, c, false, s0, st);
                     __syncthreads();
@@ -432,14 +437,14 @@ __device__ bool grid_wcycle(const SolveArgs& a, const LevelArgs* tl, const doubl
         } else {
             const int ncol = l == 0 ? 2 : 4;
             const bool done0 = z && (l > 0 || fine_colour0_in_check(a));
-            for (int k = 0; k < a.nu1; ++k)
+            for (int k = 0; k < sweeps_pre(a, l); ++k)
                 for (int c = 0; c < ncol; ++c) {
                     if (done0 && k == 0 && c == 0) continue;
                     relax_level<T, W>(a, a.L[l], l, c, z && k == 0 && c == 0, gt, gs);
                     if (!G.sync()) return false;
                 }
             restrict_level<T, W>(a, a.L[l], a.L[l + 1], l,
-                                 l + 1 < a.tail && l + 1 < Lc && a.nu1 > 0, gt, gs);
+                                 l + 1 < a.tail && l + 1 < Lc && sweeps_pre(a, l + 1) > 0, gt, gs);
             if (!G.sync()) return false;
             visits[l] = 0;
             ++l;
@@ -457,10 +462,10 @@ __device__ bool grid_wcycle(const SolveArgs& a, const LevelArgs* tl, const doubl
             const int ncol = l == 0 ? 2 : 4;
             prolong_phase<T, W>(a.L[l], a.L[l + 1], gt, gs);
             if (!G.sync()) return false;
-            for (int k = 0; k < a.nu2; ++k)
+            for (int k = 0; k < sweeps_post(a, l); ++k)
                 for (int c = 0; c < ncol; ++c) {
                     if constexpr (sizeof(T) == 4) {
-                        if (l == 0 && k == a.nu2 - 1 && c == ncol - 1) {
+                        if (l == 0 && k == sweeps_post(a, l) - 1 && c == ncol - 1) {
                             relax_fine_update(L0Op<float>{a.K, a.code, a.L[0].side}, a.L[0], a.v, c,
                                               gt, gs);
                             if (!G.sync()) return false;

@@ -47,6 +47,7 @@ struct SolveArgs {
     int tail;        // levels >= tail are relaxed by thread block 0 alone
     int smem_from;   // levels >= smem_from (>= max(tail, 1)) live in block 0's shared memory
     int nu1, nu2, max_cycles;
+    int nu1c, nu2c;  // sweeps on the coarse levels (l >= 1)
     int gamma;       // coarse visits per level visit: 1 V-cycle, 2 W-cycle
     int mixed;       // float32 V-cycles on the float64 residual (iterative refinement)
     int wbf16;       // mixed path with bfloat16 storage of the V-cycle operators and weights

@@ -327,6 +327,8 @@ bool linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bo
     a.tail = tail_level(s, g);
     a.nu1 = s->opt.nu1;
     a.nu2 = s->opt.nu2;
+    a.nu1c = s->opt.nu1_coarse < 0 ? a.nu1 : s->opt.nu1_coarse;
+    a.nu2c = s->opt.nu2_coarse < 0 ? a.nu2 : s->opt.nu2_coarse;
     a.gamma = s->opt.cycle_gamma == 2 ? 2 : 1;
     a.max_cycles = s->opt.max_cycles;
     a.mixed = mixed ? 1 : 0;

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+from bench import ISAACS_CYCLE
 from oracle.isaacs import isaacs_game
 
 pytestmark = pytest.mark.gpu
@@ -23,10 +24,13 @@ def reference():
     return game, oracle.policy_iteration(game)
 
 
-@pytest.mark.parametrize("prec,fmg", [("fp64", 0), ("mixed", 0), ("mixed", 1), ("mixed_bf16", 0)])
-def test_isaacs_1023_parity(gs, reference, prec, fmg):
+@pytest.mark.parametrize("prec,fmg,cycle", [("fp64", 0, {}), ("mixed", 0, {}), ("mixed", 1, {}),
+                                            ("mixed_bf16", 0, {}), ("mixed", 0, ISAACS_CYCLE),
+                                            ("fp64", 0, ISAACS_CYCLE)])
+def test_isaacs_1023_parity(gs, reference, prec, fmg, cycle):
+    """The default V(1,1) cycles and the benchmark's cycle options."""
     game, ref = reference
-    with gs.GameSolver(precision=prec, fmg=fmg, fmg_side=31) as s:
+    with gs.GameSolver(precision=prec, fmg=fmg, fmg_side=31, **cycle) as s:
         s.set_isaacs_grid(SIDE, 0, SEED)
         st = s.solve()
         v = s.get_value()

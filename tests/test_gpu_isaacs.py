@@ -209,6 +209,26 @@ def test_wcycle_solve_parity(gs, side, variant, prec):
     check_policies(a, b, ref, 5 if variant else 4)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
+@pytest.mark.parametrize("sweeps", [(1, 2, 0, 1), (1, 2, 1, 0), (1, 2, 1, 1), (2, 1, 0, 2)])
+@pytest.mark.parametrize("side,variant,tail", [(63, 0, 15), (255, 0, 31), (255, 0, 63), (63, 1, 31)])
+def test_coarse_sweeps_solve_parity(gs, side, variant, tail, sweeps, prec):
+    """Other sweep counts on the coarse levels than on the finest (Algorithm 3
+    leaves nu1, nu2 free per level) reach the oracle's value and policies, on
+    the grid-wide levels and on the single-block tail."""
+    nu1, nu2, c1, c2 = sweeps
+    _, ref = oracle_solve(side, variant, 1)
+    with gs.GameSolver(precision=prec, nu1=nu1, nu2=nu2, nu1_coarse=c1, nu2_coarse=c2,
+                       tail_side=tail) as s:
+        s.set_isaacs_grid(side, variant, 1)
+        st = s.solve()
+        v = s.get_value()
+        a, b = s.get_policy()
+    assert st["converged"] == 1
+    assert rel_err(v, ref.v) <= TOL[prec], (rel_err(v, ref.v), st)
+    check_policies(a, b, ref, 5 if variant else 4)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("tail_side", [1, 15, 31, 63])
 def test_wcycle_needs_no_more_cycles_than_vcycle(gs, prec, tail_side):

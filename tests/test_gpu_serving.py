@@ -64,6 +64,43 @@ def test_results_alone_equal_in_the_mix(gs):
     assert overlap > 0          # the requests' work did overlap
 
 
+def test_full_size_requests_alone_equal_in_the_mix(gs):
+    """The serving workload's largest requests: Isaacs grids up to 1023 x 1023
+    (plain and obstacle) and the largest and smallest games of its pool
+    (937,562 and 63,437 states, tables borrowed from device memory as the
+    benchmark serves them), four slots."""
+    import os
+
+    import torch
+    games = []
+    for n, seed in ((937_562, 5007), (63_437, 5000)):
+        rp, col, prob, rew, mu = synth.random_game_parallel(n, seed, workers=os.cpu_count() or 1)
+        games.append((n, (rp, col, prob, rew, mu)))
+    reqs = [("isaacs", 1023, 0, 5), ("isaacs", 1023, 1, 6), ("isaacs", 511, 0, 7),
+            ("isaacs", 63, 0, 8)] + [("game", n, t) for n, t in games]
+    ref = [alone(gs, r) for r in reqs]
+    dev = {n: tuple(torch.from_numpy(x).cuda() for x in t[:4]) + (t[4],) for n, t in games}
+    with gs.GameServer(slots=4, precision="mixed") as srv:
+        tickets = []
+        for r in reqs:
+            if r[0] == "isaacs":
+                tickets.append(srv.submit_isaacs(r[1], r[2], r[3]))
+            else:
+                rp, col, prob, rew, mu = dev[r[1]]
+                tickets.append(srv.submit_game(r[1], 4, 4, rp, col, prob, rew, mu, borrow=True))
+        infos = [srv.wait(t) for t in tickets]
+        out = [srv.result(t) for t in tickets]
+    torch.cuda.synchronize()
+    for i, (r, (v, a, b), (v0, a0, b0), info) in enumerate(zip(reqs, out, ref, infos)):
+        assert info["state"] == 2 and info["status"] == gs.GS_OK, i
+        assert info["stats"]["converged"] == 1, i
+        if r[0] == "isaacs":
+            assert np.array_equal(v, v0), i
+            assert np.array_equal(a, a0) and np.array_equal(b, b0), i
+        else:
+            assert np.max(np.abs(v - v0)) <= 1e-12 * np.max(np.abs(v0)), i
+
+
 def test_memory_budget_serialises(gs):
     reqs = [("isaacs", 127, 0, 7 + k) for k in range(4)]
     with gs.GameServer(slots=4, mem_budget=1 << 20) as srv:   # below any one request
