@@ -270,6 +270,7 @@ def run_batch(args):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) * 1e-3)
     gst, gres = s.batch_stats()
+    shape = s.batch_shape()
     sec = statistics.mean(times)
     n_tot = int(off[-1])
     nnz = len(col)
@@ -301,6 +302,7 @@ def run_batch(args):
         "data": "synthetic",
         "config": {"workload": "random_games_batch4096", "games": count, "states": n_tot,
                    "nnz": nnz, "seed": seed, "precision": args.precision,
+                   "threads_per_game": shape, "order": "largest game first",
                    "l2": "flushed between steps (256 MiB write)",
                    "outer_max": int(gst[:, 0].max()), "systems": int(gst[:, 1].sum()),
                    "cycles": int(gst[:, 2].sum()), "converged": int(gst[:, 3].min()),

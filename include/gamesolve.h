@@ -98,6 +98,10 @@ typedef struct {
                               (-1, the default: nu1) */
     int32_t nu2_coarse;    /* post-sweeps on those levels (-1, the default: nu2); the two
                               together must be >= 1 */
+    int32_t game_threads;  /* threads per game of a batch of finite games: 256 or 512, or 0
+                              (default): 512, autotuned for batches of >= 1024 games (the
+                              first solve times both on a sample; the choice is kept for the
+                              process per precision, largest game, actions and row length) */
 } gs_options;
 
 /* Statistics of the last gamesolve_solve (the columns of the paper's tables, Sec. 6). */
@@ -117,7 +121,7 @@ typedef struct {
  * V(1,1), max_cycles 200, lin_tol 1e-15, coarse_max 9, flat, fmg_side 31,
  * fmg_c 0.1, literal mu, tail_side 31, no memory budget, default stream,
  * pi_rtol 1e-2, setup_reuse 1e-2, grid_blocks 0, cycle_gamma 1, nu1_coarse and
- * nu2_coarse -1 (as on the finest level). */
+ * nu2_coarse -1 (as on the finest level), game_threads 0 (autotuned). */
 void gamesolve_default_options(gs_options* opt);
 
 /* Creates a solver on the current CUDA device.  opt may be NULL (defaults).
@@ -185,6 +189,11 @@ gs_status gamesolve_set_stopping_line(gs_solver* s, int32_t n, const double* c,
  * res[g] = |F(v) - v|_inf at the returned value.  Either pointer may be NULL.
  * Errors: GS_ESTATE when no solved batch is held. */
 gs_status gamesolve_get_batch_stats(const gs_solver* s, int32_t* stats, double* res);
+
+/* Threads per game the last solve of a game batch ran with (256 or 512; 0 for
+ * a single large game run on the whole grid).  Games are taken largest first.
+ * Errors: GS_EINVAL (NULL argument), GS_ESTATE when no solved batch is held. */
+gs_status gamesolve_get_batch_shape(const gs_solver* s, int32_t* threads);
 
 /* Sets the finite-difference Isaacs game on the unit square (Sec. 3.3, the
  * upwind scheme (decent) with the centred scheme (centre), scaled to the form

@@ -39,6 +39,7 @@ class gs_options(ctypes.Structure):
         ("pi_rtol", ctypes.c_double), ("setup_reuse", ctypes.c_double),
         ("grid_blocks", ctypes.c_int32), ("cycle_gamma", ctypes.c_int32),
         ("nu1_coarse", ctypes.c_int32), ("nu2_coarse", ctypes.c_int32),
+        ("game_threads", ctypes.c_int32),
     ]
 
 
@@ -86,6 +87,7 @@ _SIGS = {
     "gamesolve_set_game_batch": (_S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P,
                                       _P, _P, _P, _P]),
     "gamesolve_get_batch_stats": (_S, [_P, _P, _P]),
+    "gamesolve_get_batch_shape": (_S, [_P, _P]),
     "gamesolve_set_stopping_line": (_S, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_double,
                                          ctypes.c_double]),
     "gamesolve_set_isaacs_grid": (_S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P]),
@@ -232,6 +234,11 @@ class GameSolver:
         _check(lib.gamesolve_get_batch_stats(self.h, _ptr(st), _ptr(res)),
                "gamesolve_get_batch_stats")
         return st, res
+
+    def batch_shape(self):
+        t = ctypes.c_int32()
+        _check(lib.gamesolve_get_batch_shape(self.h, ctypes.byref(t)), "gamesolve_get_batch_shape")
+        return t.value
 
     def set_initial(self, v0=None, alpha0=None, beta0=None):
         v0, alpha0, beta0 = _as(v0, np.float64), _as(alpha0, np.uint8), _as(beta0, np.uint8)

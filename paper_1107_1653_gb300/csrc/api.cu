@@ -79,6 +79,7 @@ void gamesolve_default_options(gs_options* o) {
     o->cycle_gamma = 1;
     o->nu1_coarse = -1;
     o->nu2_coarse = -1;
+    o->game_threads = 0;
 }
 
 gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
@@ -97,6 +98,7 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
         !(o.pi_rtol >= 0.0 && o.pi_rtol < 1.0) || !(o.setup_reuse >= 0.0 && o.setup_reuse <= 1.0) ||
         o.grid_blocks < 0 || o.cycle_gamma < 0 || o.cycle_gamma > 2 || o.nu1_coarse < -1 ||
         o.nu2_coarse < -1 ||
+        (o.game_threads != 0 && o.game_threads != 256 && o.game_threads != 512) ||
         (o.nu1_coarse < 0 ? o.nu1 : o.nu1_coarse) + (o.nu2_coarse < 0 ? o.nu2 : o.nu2_coarse) < 1) {
         set_last_error("create: invalid option value");
         return GS_EINVAL;
@@ -187,6 +189,16 @@ gs_status gamesolve_get_batch_stats(const gs_solver* s, int32_t* stats, double* 
     }
     if (stats) std::memcpy(stats, G.stats_h.data(), sizeof(int32_t) * 4 * G.count);
     if (res) std::memcpy(res, G.res_h.data(), sizeof(double) * G.count);
+    return GS_OK;
+}
+
+gs_status gamesolve_get_batch_shape(const gs_solver* s, int32_t* threads) {
+    if (!s || !threads) return GS_EINVAL;
+    if (!s->prob || s->prob->kind != 2 || s->prob->game->stats_h.empty()) {
+        set_last_error("get_batch_shape: no solved game batch held");
+        return GS_ESTATE;
+    }
+    *threads = s->prob->game->shape;
     return GS_OK;
 }
 

@@ -570,18 +570,23 @@ __device__ void solve_game(const BatchArgs& B, int g, Ctx& C) {
     C.sync();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_games_pi(const __grid_constant__ BatchArgs B) {
+// One thread block of NT threads per game; blocks take games from the queue
+// in the order B.order gives (512 / NT blocks per SM fit the registers).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_games_pi(const __grid_constant__ BatchArgs B) {
     extern __shared__ __align__(16) char smem[];
     __shared__ int s_game;
     __shared__ double red_d[32];
     __shared__ int red_i[32];
     while (true) {
-        if (threadIdx.x == 0) s_game = atomicAdd(B.queue, 1);
+        if (threadIdx.x == 0) {
+            const int q = atomicAdd(B.queue, 1);
+            s_game = q < B.count ? B.order[q] : -1;
+        }
         __syncthreads();
         const int g = s_game;
         __syncthreads();
-        if (g >= B.count) break;
+        if (g < 0) break;
         BlockCtx<T> C;
         C.r = (T*)smem;
         C.e = C.r + B.max_n;
@@ -654,17 +659,21 @@ size_t games_smem_bytes(int max_n, bool mixed) {
     return (size_t)3 * max_n * (mixed ? sizeof(float) : sizeof(double));
 }
 
-void launch_games_pi(const BatchArgs& B, bool mixed, cudaStream_t st) {
+void launch_games_pi(const BatchArgs& B, bool mixed, int threads, cudaStream_t st) {
     const size_t smem = games_smem_bytes(B.max_n, mixed);
-    const void* fn = mixed ? (const void*)k_games_pi<float> : (const void*)k_games_pi<double>;
+    const void* fn = threads == 256 ? (mixed ? (const void*)k_games_pi<float, 256>
+                                             : (const void*)k_games_pi<double, 256>)
+                                    : (mixed ? (const void*)k_games_pi<float, 512>
+                                             : (const void*)k_games_pi<double, 512>);
+    const int nt = threads == 256 ? 256 : 512;
     GS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, sms = 0;
     GS_CUDA(cudaGetDevice(&dev));
     GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
+    GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
     const int blocks = std::max(1, std::min(B.count, std::max(1, per_sm) * sms));
     void* args[] = {(void*)&B};
-    GS_CUDA(cudaLaunchKernel(fn, dim3(blocks), dim3(kThreads), args, smem, st));
+    GS_CUDA(cudaLaunchKernel(fn, dim3(blocks), dim3(nt), args, smem, st));
     note_launches(1);
 }
 

@@ -60,6 +60,7 @@ struct BatchArgs {
     const int64_t* st_off;  // count + 1 state offsets
     const double* mu;       // per game
     int* queue;             // work counter (zeroed before the launch)
+    const int* order;       // queue position -> game, `count` entries (one-block kernel)
 };
 
 // Work vectors of the grid-wide single-game kernel (global memory).
@@ -82,7 +83,12 @@ void launch_game_prepare(const GameTables& T, int count, const int64_t* st_off, 
                          const double* mu, double* leak, float* leak32, float* prob32,
                          __nv_bfloat16* prob16, cudaStream_t st);
 size_t games_smem_bytes(int max_n, bool mixed);
-void launch_games_pi(const BatchArgs& B, bool mixed, cudaStream_t st);
+// Threads per game of the one-block kernel's instantiations.
+constexpr int kBatchShapes[2] = {256, 512};
+// Batches of at least this many games autotune the shape on a sample of this many.
+constexpr int kAutotuneMinGames = 1024;
+constexpr int kAutotuneSample = 608;
+void launch_games_pi(const BatchArgs& B, bool mixed, int threads, cudaStream_t st);
 // Thread blocks for the grid-wide kernel on a game of n states (cap > 0 limits them).
 int game_grid_blocks(int64_t n, int cap);
 void launch_game_pi_grid(const BatchArgs& B, const GridWork& W, int blocks, bool mixed,

@@ -4,6 +4,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <tuple>
 
 #include "games.cuh"
 #include "solver.cuh"
@@ -88,6 +92,20 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
     G->gstats = ar.alloc<int>(4 * (size_t)count);
     G->gres = ar.alloc<double>(count);
     G->queue = ar.alloc<int>(2);
+    // largest games first, so that no large game starts as the batch drains;
+    // the autotuning sample takes every k-th game of that order (the same mix)
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return off[a + 1] - off[a] > off[b + 1] - off[b];
+    });
+    const int stride = count >= kAutotuneMinGames ? count / kAutotuneSample : 1;
+    std::vector<int> sample;
+    for (int q = 0; q < count && (int)sample.size() < kAutotuneSample; q += stride)
+        sample.push_back(order[q]);
+    G->order = ar.alloc<int>(count);
+    G->sample = ar.alloc<int>(sample.size());
+    G->n_sample = (int)sample.size();
     if (grid) {
         G->grid = true;
         G->wr = ar.alloc<double>(n_total);
@@ -106,6 +124,9 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
     GS_CUDA(cudaMemcpyAsync(G->rew, reward, sizeof(double) * rows, cudaMemcpyDefault, st));
     GS_CUDA(cudaMemcpyAsync(G->mu, mu_h.data(), sizeof(double) * count, cudaMemcpyHostToDevice, st));
     GS_CUDA(cudaMemsetAsync(G->queue, 0, 2 * sizeof(int), st));
+    GS_CUDA(cudaMemcpyAsync(G->order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(G->sample, sample.data(), sizeof(int) * sample.size(),
+                            cudaMemcpyHostToDevice, st));
     GameTables T = G->tables();
     launch_game_validate(T, count, G->st_off, rows, G->queue + 1, st);
     int bad = 0;
@@ -132,6 +153,61 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
     return P;
 }
 
+namespace {
+
+// Block-shape autotuner of the one-block batch kernel.  Games are latency
+// bound, so the better shape (fewer threads per game and more games in flight,
+// or the reverse) depends on the games' sizes, the precision and the shared
+// memory each game takes.  The first solve of a large batch times every shape
+// on a sample of it (every k-th game, largest first) and keeps the faster; the
+// choice is cached per (precision, largest game rounded up to a power of two,
+// actions, row length) for the process.
+using ShapeKey = std::tuple<int, int, int, int, int64_t>;
+std::mutex g_shape_mu;
+std::map<ShapeKey, int> g_shapes;
+
+int tuned_shape(gs_solver* s, GameProblem& G, const BatchArgs& B, bool mixed) {
+    if (s->opt.game_threads > 0) return s->opt.game_threads;
+    if (G.count < kAutotuneMinGames) return 512;
+    int pow2 = 1;
+    while (pow2 < G.max_n) pow2 <<= 1;
+    const ShapeKey key{s->opt.precision, pow2, G.m1, G.m2, G.k_uniform};
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        auto it = g_shapes.find(key);
+        if (it != g_shapes.end()) return it->second;
+    }
+    cudaStream_t st = s->st;
+    BatchArgs T = B;
+    T.count = G.n_sample;
+    T.order = G.sample;
+    cudaEvent_t e0, e1;
+    GS_CUDA(cudaEventCreate(&e0));
+    GS_CUDA(cudaEventCreate(&e1));
+    int best = 512;
+    float best_ms = 0.0f;
+    for (int shape : kBatchShapes) {
+        GS_CUDA(cudaMemsetAsync(G.queue, 0, sizeof(int), st));
+        GS_CUDA(cudaEventRecord(e0, st));
+        launch_games_pi(T, mixed, shape, st);
+        GS_CUDA(cudaEventRecord(e1, st));
+        GS_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        GS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (best_ms == 0.0f || ms < best_ms) {
+            best = shape;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shapes[key] = best;
+    return best;
+}
+
+}  // namespace
+
 gs_status run_games(gs_solver* s, gs_solve_stats* stats) {
     GameProblem& G = *s->prob->game;
     cudaStream_t st = s->st;
@@ -153,6 +229,9 @@ gs_status run_games(gs_solver* s, gs_solve_stats* stats) {
     B.st_off = G.st_off;
     B.mu = G.mu;
     B.queue = G.queue;
+    B.order = G.order;
+    const int shape = G.grid ? 0 : tuned_shape(s, G, B, mixed);
+    G.shape = shape;
     cudaEvent_t e0, e1;
     GS_CUDA(cudaEventCreate(&e0));
     GS_CUDA(cudaEventCreate(&e1));
@@ -164,7 +243,7 @@ gs_status run_games(gs_solver* s, gs_solve_stats* stats) {
         const int blocks = std::min(game_grid_blocks(G.n_total, s->opt.grid_blocks), 152 * 64);
         launch_game_pi_grid(B, W, blocks, mixed, st);
     } else {
-        launch_games_pi(B, mixed, st);
+        launch_games_pi(B, mixed, shape, st);
     }
     GS_CUDA(cudaEventRecord(e1, st));
     G.stats_h.resize(4 * (size_t)G.count);

@@ -79,6 +79,10 @@ struct GameProblem {
     bool prob_bf16 = false;
     uint8_t *alpha = nullptr, *beta = nullptr;
     int *gstats = nullptr, *queue = nullptr;
+    int* order = nullptr;                  // games largest first (the queue's order)
+    int* sample = nullptr;                 // every k-th entry of order (shape autotuning)
+    int n_sample = 0;
+    int shape = 0;                         // threads per game of the last solve (0: grid)
     bool grid = false;                     // one large game on the whole grid
     double *wr = nullptr, *we = nullptr, *wt = nullptr, *part = nullptr;
     GridBarrier* bar = nullptr;

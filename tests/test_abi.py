@@ -32,11 +32,12 @@ def test_every_declared_symbol_is_exported(gs):
 
 
 def test_struct_layouts_match_header(gs):
-    # gs_options: 128 bytes, the stream pointer at 88; gs_solve_stats: 48 bytes
-    assert ctypes.sizeof(gs.gs_options) == 128 and gs.gs_options.stream.offset == 88
+    # gs_options: 136 bytes, the stream pointer at 88; gs_solve_stats: 48 bytes
+    assert ctypes.sizeof(gs.gs_options) == 136 and gs.gs_options.stream.offset == 88
     assert gs.gs_options.grid_blocks.offset == 112
     assert gs.gs_options.cycle_gamma.offset == 116
     assert gs.gs_options.nu1_coarse.offset == 120 and gs.gs_options.nu2_coarse.offset == 124
+    assert gs.gs_options.game_threads.offset == 128
     assert gs.gs_options.pi_rtol.offset == 96
     assert ctypes.sizeof(gs.gs_solve_stats) == 48
 
@@ -44,12 +45,13 @@ def test_struct_layouts_match_header(gs):
 def test_host_side_checks_without_gpu(gs):
     o = gs.default_options()
     assert o.precision == gs.GS_PREC_FP64 and o.nu1 == 1 and o.nu2 == 1 and o.cycle_gamma == 1
-    assert o.nu1_coarse == -1 and o.nu2_coarse == -1
+    assert o.nu1_coarse == -1 and o.nu2_coarse == -1 and o.game_threads == 0
     assert gs.lib.gamesolve_strerror(gs.GS_ENOTCONV).startswith(b"iteration caps")
     # NULL out-pointer and invalid options are rejected before any CUDA call
     assert gs.lib.gamesolve_create(None, None) == gs.GS_EINVAL
     h = ctypes.c_void_p()
-    for kw in ({"coarse_max": 0}, {"nu1_coarse": -2}, {"nu1_coarse": 0, "nu2_coarse": 0}):
+    for kw in ({"coarse_max": 0}, {"nu1_coarse": -2}, {"nu1_coarse": 0, "nu2_coarse": 0},
+               {"game_threads": 384}):
         bad = gs.default_options(**kw)
         assert gs.lib.gamesolve_create(ctypes.byref(h), ctypes.byref(bad)) == gs.GS_EINVAL, kw
     assert gs.lib.gamesolve_solve(None, None) == gs.GS_EINVAL

@@ -131,6 +131,52 @@ def test_game_batch(gs, prec):
         assert gres[g] <= 1e-9
 
 
+@pytest.mark.parametrize("threads", [256, 512])
+def test_game_batch_shapes(gs, threads):
+    """Both block shapes of the batch kernel, forced, solve every game."""
+    sizes = synth.batch_game_sizes(24, 5, nmin=256, nmax=1500)
+    (off, rp, col, prob, rew, mu), parts = batch(sizes, 5)
+    with gs.GameSolver(precision="mixed", game_threads=threads) as s:
+        s.set_game_batch(off, 4, 4, rp, col, prob, rew, mu)
+        st = s.solve()
+        v = s.get_value()
+        a, b = s.get_policy()
+        gst, _ = s.batch_stats()
+        assert s.batch_shape() == threads
+    assert st["converged"] == 1 and np.all(gst[:, 3] == 1)
+    for g, n in enumerate(sizes):
+        x0, x1 = off[g], off[g + 1]
+        _, ref = oracle_of(int(n), 4, 4, *parts[g])
+        assert check(v[x0:x1], a[x0:x1], b[x0:x1], ref) <= TOL["mixed"], g
+
+
+def test_batch_shape_autotuned(gs):
+    """A batch of >= 1024 games autotunes its block shape on a sample; the
+    result agrees with the other shape's and, on sampled games, the oracle's."""
+    sizes = synth.batch_game_sizes(1100, 6, nmin=64, nmax=400)
+    (off, rp, col, prob, rew, mu), parts = batch(sizes, 6)
+    with gs.GameSolver(precision="mixed") as s:
+        s.set_game_batch(off, 4, 4, rp, col, prob, rew, mu)
+        st = s.solve()
+        v = s.get_value()
+        a, b = s.get_policy()
+        shape = s.batch_shape()
+    assert shape in (256, 512)
+    assert st["converged"] == 1
+    other = 512 if shape == 256 else 256
+    with gs.GameSolver(precision="mixed", game_threads=other) as s:
+        s.set_game_batch(off, 4, 4, rp, col, prob, rew, mu)
+        s.solve()
+        w = s.get_value()
+    for g in range(len(sizes)):
+        x0, x1 = off[g], off[g + 1]
+        assert np.max(np.abs(v[x0:x1] - w[x0:x1])) <= 1e-11 * np.max(np.abs(w[x0:x1])), g
+    for g in np.random.default_rng(6).choice(len(sizes), 6, replace=False):
+        x0, x1 = off[g], off[g + 1]
+        _, ref = oracle_of(int(sizes[g]), 4, 4, *parts[g])
+        assert check(v[x0:x1], a[x0:x1], b[x0:x1], ref) <= TOL["mixed"], g
+
+
 def test_game_validation(gs):
     n = 50
     rp, col, prob, rew, mu = synth.random_game(n, 1)
