@@ -5,12 +5,12 @@ with these stored oracle outputs at a seeded sample of states: the oracle
 takes minutes to an hour per workload, too long to run beside the GPU.
 Calls only oracle/ (and the seeded input generators of synth/).
 
-    python tests/golden/make_fullsize_samples.py isaacs2047    # ~1 h, ~12 GB
+    python tests/golden/make_fullsize_samples.py isaacs2047_seed3   # ~16 min, ~12 GB
     python tests/golden/make_fullsize_samples.py obstacle1023
     python tests/golden/make_fullsize_samples.py batch4096
 
-* isaacs2047: Algorithm 2 with Algorithm 1 inside (sparse LU) on the plain
-  2047 x 2047 Isaacs game, seed 2, from the default start.
+* isaacs2047_seed2, isaacs2047_seed3: Algorithm 2 with Algorithm 1 inside
+  (sparse LU) on the plain 2047 x 2047 Isaacs game, from the default start.
 * obstacle1023: the obstacle variant at 1023 x 1023, seed 2.  The oracle runs
   its own FAMGpi (Algorithm 4, from 31 x 31, eps_l = 0.01 h_l^2) with eps = 0
   on the finest level, so the last policy iteration runs until MAX's policy
@@ -68,17 +68,17 @@ def write(name, header, body):
         fh.writelines(body)
 
 
-def isaacs2047():
+def isaacs2047(seed: int):
     t0 = time.time()
-    res = oracle.policy_iteration(isaacs_game(2047, 0, seed=2))
+    res = oracle.policy_iteration(isaacs_game(2047, 0, seed=seed))
     idx = sample_states(res.v.size, SAMPLES, 2047)
-    write("isaacs2047_plain_seed2_samples.txt",
+    write(f"isaacs2047_plain_seed{seed}_samples.txt",
           ["FP64 oracle, Algorithm 2 with Algorithm 1 inside (sparse LU), plain Isaacs game",
-           "2047 x 2047, seed 2; written by make_fullsize_samples.py isaacs2047",
+           f"2047 x 2047, seed {seed}; written by make_fullsize_samples.py isaacs2047_seed{seed}",
            "columns: state v alpha beta(x,0..m1-1) gap_max gap_min(x,0..m1-1)",
            f"outer {res.outer} systems {res.systems} residual {res.residual:.3e}"],
           [f"vmax {np.max(np.abs(res.v)):.17e}\n"] + rows(res, idx))
-    print(f"isaacs2047: outer {res.outer} systems {res.systems} residual {res.residual:.2e} "
+    print(f"isaacs2047 seed {seed}: outer {res.outer} systems {res.systems} residual {res.residual:.2e} "
           f"in {time.time() - t0:.0f} s")
 
 
@@ -125,6 +125,7 @@ def batch4096():
 
 
 if __name__ == "__main__":
-    jobs = {"isaacs2047": isaacs2047, "obstacle1023": obstacle1023, "batch4096": batch4096}
+    jobs = {"isaacs2047_seed2": lambda: isaacs2047(2), "isaacs2047_seed3": lambda: isaacs2047(3),
+            "obstacle1023": obstacle1023, "batch4096": batch4096}
     for name in sys.argv[1:] or list(jobs):
         jobs[name]()

@@ -64,6 +64,7 @@ def test_batch_fixture_is_the_oracles():
 
 
 @pytest.mark.parametrize("name", ["isaacs2047_plain_seed2_samples.txt",
+                                  "isaacs2047_plain_seed3_samples.txt",
                                   "isaacs1023_obstacle_seed2_samples.txt"])
 def test_grid_fixtures_are_well_formed(name):
     vmax, (idx, v, a, b, gmax, gmin) = load_grid_samples(name)

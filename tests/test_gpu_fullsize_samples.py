@@ -9,7 +9,8 @@ for the Isaacs grids; one persistent launch over the whole 4096-game batch).
 Bars: value to 1e-10 relative to max |v*| (float64 path), 1e-9 (mixed and
 bfloat16-storage paths); policies bit-exact wherever the oracle's gap exceeds
 1e-8.  Beyond the sample, the float64 and mixed solutions of the 2047 x 2047
-game agree at every state within the mixed bar.
+game agree at every state within the mixed bar.  The 2047 x 2047 game is
+checked at seeds 2 and 3.
 """
 import os
 
@@ -66,30 +67,28 @@ def check_sample(v, a, b, vmax, sample, tol):
     return err
 
 
-@pytest.fixture(scope="module")
-def isaacs2047():
-    return load_grid_samples("isaacs2047_plain_seed2_samples.txt")
-
-
-@pytest.fixture(scope="module")
-def fp64_2047(gs):
+@pytest.fixture(scope="module", params=[2, 3])
+def case2047(request, gs):
+    """(seed, stored oracle sample, float64 GPU solve) of the 2047 x 2047 game."""
+    seed = request.param
+    vmax, sample = load_grid_samples(f"isaacs2047_plain_seed{seed}_samples.txt")
     with gs.GameSolver(precision="fp64", **CYCLE) as s:
-        s.set_isaacs_grid(2047, 0, 2)
+        s.set_isaacs_grid(2047, 0, seed)
         st = s.solve()
-        return st, s.get_value()
+        v64 = s.get_value()
+    return seed, vmax, sample, st, v64
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
-def test_isaacs_2047_sampled_parity(gs, isaacs2047, fp64_2047, prec):
-    vmax, sample = isaacs2047
+def test_isaacs_2047_sampled_parity(gs, case2047, prec):
+    seed, vmax, sample, st64, v64 = case2047
     with gs.GameSolver(precision=prec, **CYCLE) as s:
-        s.set_isaacs_grid(2047, 0, 2)
+        s.set_isaacs_grid(2047, 0, seed)
         st = s.solve()
         v = s.get_value()
         a, b = s.get_policy()
     assert st["converged"] == 1
     check_sample(v, a, b, vmax, sample, TOL[prec])
-    st64, v64 = fp64_2047
     assert st64["converged"] == 1
     # every state, not only the sample: mixed against float64 on the device
     assert np.max(np.abs(v - v64)) / vmax <= TOL[prec]
