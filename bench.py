@@ -195,6 +195,36 @@ def oracle_sample(systems_per_solve: int, outer_per_solve: int):
     return t_solve, t1 - t0, t2 - t1
 
 
+def _oracle_batch_game(args):
+    """Worker (module level for a spawn pool): seconds the oracle takes to solve
+    game g of the random batch (policy iteration, fixed-point evaluation)."""
+    n, seed, g = args
+    import oracle
+    import synth
+    from oracle.game import game_from_csr
+    rp, col, prob, rew, mu = synth.random_game(n, synth.batch_game_seed(seed, g))
+    game = game_from_csr(n, 4, 4, rp, col, prob, rew, mu)
+    t0 = time.perf_counter()
+    oracle.policy_iteration(game, solver="fixed_point")
+    return time.perf_counter() - t0
+
+
+def oracle_batch_sample(sizes, seed: int, games: int = 48, workers: int = 0):
+    """The oracle on a seeded sample of the batch's games, one game per process
+    over the host's cores.  Returns (games/s, cores, seconds of CPU work)."""
+    import multiprocessing as mp
+    import numpy as np
+    workers = workers or os.cpu_count() or 1
+    pick = np.random.default_rng(seed + 1).choice(len(sizes), size=min(games, len(sizes)),
+                                                  replace=False)
+    tasks = [(int(sizes[g]), seed, int(g)) for g in pick]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        t0 = time.perf_counter()
+        per_game = pool.map(_oracle_batch_game, tasks, chunksize=1)
+        wall = time.perf_counter() - t0
+    return len(tasks) / wall, workers, float(sum(per_game))
+
+
 # Policy iterations the FP64 oracle needs for this workload (1023^2, seed 2),
 # counted by a full oracle run (tests/golden/oracle_counts_1023.txt).
 def oracle_counts():
@@ -314,6 +344,13 @@ def run_batch(args):
                 "h2d_bytes_per_step": int(rp.nbytes + col.nbytes + prob.nbytes + rew.nbytes),
                 "d2h_bytes_per_step": int(v_h.nbytes + a_h.nbytes + b_h.nbytes)},
     }
+    if not args.no_cpu_baseline:
+        g_s, cores, cpu_s = oracle_batch_sample(sizes, seed)
+        line["cpu_baseline"] = {
+            "value": g_s, "unit": "games/s", "cores": cores, "kind": "oracle",
+            "sample": f"48 games drawn from the batch, one per process on {cores} host cores "
+                      f"({cpu_s:.0f} s of CPU work); policy iteration with the fixed-point "
+                      f"policy evaluation to 1e-14"}
     print(json.dumps(line), flush=True)
     return 0
 
