@@ -154,7 +154,8 @@ gs_status gamesolve_set_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2,
  * state index within the row's own game.  Values, policies and statistics are
  * read back concatenated in the same state order.  In a batch of two or more
  * games each game must have at most 16384 states (mixed precision) or 8192
- * (float64).
+ * (float64).  Thread blocks take the games largest first; the first solve of
+ * a batch of at least 1024 games picks the block shape (options.game_threads).
  * Errors: as gamesolve_set_game, per row and per game. */
 gs_status gamesolve_set_game_batch(gs_solver* s, int32_t count, int32_t m1, int32_t m2,
                                    const int64_t* state_offsets, const int64_t* row_ptr,
