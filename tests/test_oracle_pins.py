@@ -333,3 +333,90 @@ def test_random_game_structure():
     # roughly uniform successor marginal
     counts = np.bincount(col, minlength=n)
     assert counts.min() > 0.6 * counts.mean() and counts.max() < 1.4 * counts.mean()
+
+
+# ----------------------------------------------------------------- fixed-point evaluation
+@pytest.mark.parametrize("n,seed", [(300, 11), (1000, 12), (2000, 13)])
+def test_fixed_point_evaluation_matches_dense_solve(n, seed):
+    """The fixed-policy iteration w <- mu M w + r (Eq. (LSPI) as a fixed point)
+    stops on its step size; at mu = 0.99 that step bounds the error by
+    mu/(1 - mu) times itself, so the result must sit within about 1e-12 of
+    the LAPACK solution of the same system.  Random policies, random games."""
+    rp, col, prob, rew, mu = synth.random_game(n, seed)
+    game = game_from_csr(n, 4, 4, rp, col, prob, rew, mu)
+    rng = np.random.default_rng(seed)
+    alpha = rng.integers(0, 4, n).astype(np.uint8)
+    beta = rng.integers(0, 4, (n, 4)).astype(np.uint8)
+    A, r = oracle.policy_system(game, alpha, beta)
+    w_dense = oracle.solve_policy_system(A, r, "dense")
+    w_fp = oracle.solve_policy_system(A, r, "fixed_point")
+    scale = np.max(np.abs(w_dense))
+    assert np.max(np.abs(w_fp - w_dense)) <= 1e-12 * scale
+    # and the dense solution is the fixed point: w = mu M w + r row by row
+    M = (sp_identity(n) - A)
+    assert np.max(np.abs(M @ w_dense + r - w_dense)) <= 1e-13 * scale
+
+
+def sp_identity(n):
+    import scipy.sparse as sp
+    return sp.identity(n, format="csr")
+
+
+def test_fixed_point_evaluation_substochastic_rows():
+    """Rows that lose mass (stop actions, the Dirichlet boundary) change the
+    fixed point: a two-state chain worked by hand.  State 0 moves to 1 with
+    p = 1/2 (the rest leaves), state 1 stays with p = 1/4; r = (1, 2),
+    mu = 0.8: w1 = 2 / (1 - 0.2) = 2.5, w0 = 1 + 0.4 * 2.5 = 2."""
+    game = game_from_csr(2, 1, 1, np.array([0, 1, 2]), np.array([1, 1], np.int32),
+                         np.array([0.5, 0.25]), np.array([1.0, 2.0]), 0.8)
+    A, r = oracle.policy_system(game, np.zeros(2, np.uint8), np.zeros((2, 1), np.uint8))
+    w = oracle.solve_policy_system(A, r, "fixed_point")
+    assert abs(w[1] - 2.5) <= 1e-13 and abs(w[0] - 2.0) <= 1e-13
+
+
+@pytest.mark.parametrize("mu", [0.5, 0.9, 0.99])
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_pi_with_fixed_point_evaluation_matches_brute_force(n, mu):
+    """Whole policy iteration with the fixed-point policy evaluation (the one
+    used for random games above 2000 states) against enumeration."""
+    p, r = tiny_dense_game(5000 * n + int(100 * mu), n, 2, 2)
+    vstar, V = brute_force(p, r, mu)
+    res = oracle.policy_iteration(dense_to_game(p, r, mu), solver="fixed_point")
+    assert res.converged
+    # stopping on a 1e-14 step at mu = 0.99 leaves at most ~1e-12 relative
+    assert np.max(np.abs(res.v - vstar)) <= 2e-12 * max(1.0, np.max(np.abs(vstar)))
+    a = res.alpha.astype(int)
+    assert np.allclose(V[tuple(a.tolist())], vstar, atol=1e-11)
+
+
+# ----------------------------------------------------------------- gaps and rewards
+def test_gap_hand_example():
+    """Best minus second best over the last axis: for MAX the two largest,
+    for MIN the two smallest; a tie gives 0; one action gives inf."""
+    from oracle.game import _gap
+    vals = np.array([[3.0, 1.0, 2.0], [5.0, 5.0, 0.0], [-1.0, 4.0, 0.5]])
+    assert _gap(vals, True).tolist() == [1.0, 0.0, 3.5]
+    assert _gap(vals, False).tolist() == [1.0, 5.0, 1.5]
+    assert np.all(np.isinf(_gap(np.zeros((4, 1)), True)))
+    # the PI result's gaps are those of F(v; x, a) over a and F(v; x, a, b) over b
+    p, r = tiny_dense_game(31, 3, 2, 2)
+    res = oracle.policy_iteration(dense_to_game(p, r, 0.9))
+    q = 0.9 * np.einsum("xaby,y->xab", p, res.v) + r
+    fa = q.min(axis=2)
+    assert np.allclose(res.gap_max, np.abs(fa[:, 0] - fa[:, 1]), atol=1e-15)
+    assert np.allclose(res.gap_min, np.abs(q[:, :, 0] - q[:, :, 1]), atol=1e-15)
+
+
+def test_config_reward_hand_values():
+    """r(x, a, b) = sin(pi x1) sin(pi x2) + 0.1 (a - b) + xi at hand-computed
+    points: x = (1/2, 1/4), a = 3, b = 1, xi = 0.01 gives sqrt(2)/2 + 0.21;
+    x = (1/6, 1/2), a = b = 2, xi = -0.05 gives 1/2 - 0.05."""
+    from oracle.isaacs import config_reward
+    assert abs(config_reward(0.5, 0.25, 3, 1, 0.01) - (np.sqrt(2) / 2 + 0.21)) <= 2e-16
+    assert abs(config_reward(1 / 6, 0.5, 2, 2, -0.05) - 0.45) <= 2e-16
+    assert abs(config_reward(0.5, 0.5, 0, 3, 0.0) - 0.7) <= 2e-16
+    # the oracle's game carries (1 - mu) r with 1 - mu = h^2 / (1 + h^2)
+    g = isaacs_game(3, 0, xi=np.zeros(9))
+    h = 0.25
+    x = 4                                       # centre point (1/2, 1/2)
+    assert abs(g.rew[x, 1, 3] - h * h / (1 + h * h) * (1.0 - 0.2)) <= 1e-17
