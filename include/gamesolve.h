@@ -102,6 +102,12 @@ typedef struct {
                               (default): 512, autotuned for batches of >= 1024 games (the
                               first solve times both on a sample; the choice is kept for the
                               process per precision, largest game, actions and row length) */
+    int32_t cycle_kernel;  /* Isaacs grids' V-cycles: 0 tiled where they apply (each
+                              thread block runs a whole smoothing leg of a tile of a level in
+                              shared memory, with a halo recomputed by its neighbours: about
+                              two grid-wide barriers per level and cycle); 1 one grid-wide
+                              phase per relaxation colour (default).  Same arithmetic per point.
+                              W-cycles always take the latter. */
 } gs_options;
 
 /* Statistics of the last gamesolve_solve (the columns of the paper's tables, Sec. 6). */
@@ -121,7 +127,8 @@ typedef struct {
  * V(1,1), max_cycles 200, lin_tol 1e-15, coarse_max 9, flat, fmg_side 31,
  * fmg_c 0.1, literal mu, tail_side 31, no memory budget, default stream,
  * pi_rtol 1e-2, setup_reuse 1e-2, grid_blocks 0, cycle_gamma 1, nu1_coarse and
- * nu2_coarse -1 (as on the finest level), game_threads 0 (autotuned). */
+ * nu2_coarse -1 (as on the finest level), game_threads 0 (autotuned),
+ * cycle_kernel 1 (one phase per colour). */
 void gamesolve_default_options(gs_options* opt);
 
 /* Creates a solver on the current CUDA device.  opt may be NULL (defaults).
@@ -224,7 +231,10 @@ gs_status gamesolve_set_initial(gs_solver* s, const double* v0,
 
 /* Runs AMGpi (or FAMGpi if options.fmg) from the current initial data.
  * stats may be NULL.  Returns GS_ENOTCONV when a cap was reached (the best
- * iterate is kept and readable), GS_ESTATE when no problem is set. */
+ * iterate is kept and readable): max_outer, or max_cycles in any policy
+ * evaluation (an evaluation that stops short of the float64 floor ends the
+ * iteration, since no policy decision may rest on it; under FAMGpi the finer
+ * levels are then not run).  GS_ESTATE when no problem is set. */
 gs_status gamesolve_solve(gs_solver* s, gs_solve_stats* stats);
 
 /* Copies the value v (n doubles) to v_out (host or device). */
@@ -245,10 +255,58 @@ gs_status gamesolve_improve(gs_solver* s, const double* v, uint8_t* alpha_out,
 /* Solves the policy-fixed system (I - mu M^{alpha beta}) w = r^{alpha beta}
  * of Eq. (LSPI) for the given policies (alpha: n bytes, beta: n*m1 bytes) with
  * the solver's multigrid method and precision, from the initial guess w0
- * (NULL = 0).  Writes w (n doubles).  stats (may be NULL) gets cycles and the
- * final |b - A w|_inf in res_inf. */
+ * (NULL = 0).  Writes w (n doubles).  stats (may be NULL) gets cycles, the
+ * final |b - A w|_inf in res_inf and converged.  Returns GS_ENOTCONV (w
+ * holds the last iterate) when options.max_cycles is reached before the
+ * float64 floor. */
 gs_status gamesolve_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* beta,
                                  const double* w0, double* w_out, gs_solve_stats* stats);
+
+/* The two interpolations of FAMGpi (Algorithm 4, Sec. 5.2) from an Isaacs
+ * grid of side side_c to the grid of side 2 side_c + 1 whose points include
+ * it (coarse point (P, Q), 1-based, is fine point (2P, 2Q)):
+ *  - value interpolation I: a fine point that is a coarse point keeps its
+ *    value; any other takes the mean of v over its coarse neighbours N(x) at
+ *    distance <= the coarse step, boundary neighbours counting with their
+ *    Dirichlet value 0 (2 neighbours on a cell edge, 4 at a cell centre);
+ *  - strategy interpolation U: coarse points keep alpha and beta(., a); a new
+ *    fine point copies those of the interior member of N(x) with the lowest
+ *    row-major index.
+ * variant 0 (m1 = 4) or 1 (obstacle, m1 = 5).  Inputs: v_c (n_c doubles),
+ * alpha_c (n_c bytes), beta_c (n_c*m1 bytes, beta(x, a) at [x*m1 + a]), n_c =
+ * side_c^2; outputs (any may be NULL): v_f, alpha_f, beta_f likewise on the
+ * fine grid.  Host or device pointers; the call allocates its own device
+ * buffers and runs on `stream` (NULL = legacy default), returning when done.
+ * Errors: GS_EINVAL for side_c outside [1, 8191], variant not 0/1, a missing
+ * input or an action out of range. */
+gs_status gamesolve_fmg_interpolate(int32_t side_c, int32_t variant, const double* v_c,
+                                    const uint8_t* alpha_c, const uint8_t* beta_c, double* v_f,
+                                    uint8_t* alpha_f, uint8_t* beta_f, void* stream);
+
+/* Iteration counts per level of the last gamesolve_solve of an Isaacs grid
+ * (the per-level columns of the paper's FAMGpi tables, Sec. 6): for level k,
+ * coarsest first, stats[3k .. 3k+2] = (grid side, MAX policy iterations,
+ * linear systems solved).  A flat solve has one level.  At most cap levels
+ * are written; *levels (may be NULL) receives the number of levels.
+ * Errors: GS_EINVAL (bad arguments), GS_ESTATE (no solved Isaacs grid). */
+gs_status gamesolve_get_level_stats(const gs_solver* s, int32_t* stats, int32_t cap,
+                                    int32_t* levels);
+
+/* Self-test of the bounded grid-wide barrier (failure detection; the paper has
+ * no counterpart).  Every cooperative kernel of the library synchronises its
+ * thread blocks with a barrier whose waits give up after a time limit (2 s in
+ * the solvers), raise an error flag that releases the other waiters, and make
+ * the call return GS_ETIMEOUT instead of hanging the GPU.  This call runs that
+ * barrier alone: a cooperative launch of `blocks` blocks (clamped to what can
+ * be resident at once) passes it `rounds` times with each wait limited to
+ * limit_ns nanoseconds (1e3 .. 1e8).  absent_block in [0, blocks) names a
+ * block that returns without ever arriving, so the others' first wait runs out
+ * (-1: every block arrives).  *passed (may be NULL) receives the number of
+ * barrier passages completed, summed over blocks.  Returns GS_ETIMEOUT when a
+ * wait gave up (the context stays usable), GS_OK when every round completed,
+ * GS_EINVAL for arguments out of range. */
+gs_status gamesolve_selftest_barrier(int32_t blocks, int32_t absent_block, uint64_t limit_ns,
+                                     int32_t rounds, void* stream, int32_t* passed);
 
 /* Kernel classes that gamesolve_trace can time (diagnostics). */
 typedef enum {
@@ -283,9 +341,12 @@ uint64_t gamesolve_kernel_launches(void);
  * 2.5 MiB file-scope device array that every GPU loading the library holds
  * until the process exits.
  *  - side must be 2^k - 1 and at most 127 (GS_EINVAL beyond that).
- *  - alpha (n bytes), beta (n*m1 bytes), w0 (n doubles, NULL = start from 0),
- *    xi (n doubles, NULL = SplitMix64 stream `seed`) and the output w (n
- *    doubles) must be device memory of the current device (GS_EINVAL otherwise).
+ *  - alpha (n bytes), beta (n*m1 bytes), w0 (n doubles, NULL = start from 0;
+ *    w0 == w is allowed and starts from w's contents), xi (n doubles, NULL =
+ *    SplitMix64 stream `seed`) and the output w (n doubles) must be device
+ *    memory of the current device, or managed memory (GS_EINVAL otherwise).
+ *  - Returns GS_ENOTCONV (w holds the last iterate, stats->converged = 0)
+ *    when the default cycle cap is reached before the float64 floor.
  *  - The first call on a device looks the array's device address up
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture.

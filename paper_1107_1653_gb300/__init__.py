@@ -40,6 +40,7 @@ class gs_options(ctypes.Structure):
         ("grid_blocks", ctypes.c_int32), ("cycle_gamma", ctypes.c_int32),
         ("nu1_coarse", ctypes.c_int32), ("nu2_coarse", ctypes.c_int32),
         ("game_threads", ctypes.c_int32),
+        ("cycle_kernel", ctypes.c_int32),
     ]
 
 
@@ -100,6 +101,11 @@ _SIGS = {
     "gamesolve_isaacs_policy_solve_static": (_S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                                   _P, _P, _P, _P, _P, ctypes.c_int32, _P,
                                                   ctypes.POINTER(gs_solve_stats)]),
+    "gamesolve_fmg_interpolate": (_S, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P, _P,
+                                       _P]),
+    "gamesolve_get_level_stats": (_S, [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "gamesolve_selftest_barrier": (_S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32)]),
     "gamesolve_trace": (_S, [_P, ctypes.c_int32]),
     "gamesolve_trace_read": (_S, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "gamesolve_kernel_launches": (ctypes.c_uint64, []),
@@ -282,13 +288,25 @@ class GameSolver:
                "gamesolve_trace_read")
         return ms.value, cnt.value
 
-    def policy_solve(self, alpha, beta, w0=None):
+    def level_stats(self):
+        """Per FAMGpi level (coarsest first): (side, MAX iterations, linear systems)."""
+        out = np.zeros((32, 3), np.int32)
+        nl = ctypes.c_int32()
+        _check(lib.gamesolve_get_level_stats(self.h, _ptr(out), 32, ctypes.byref(nl)),
+               "gamesolve_get_level_stats")
+        return [tuple(int(x) for x in row) for row in out[:nl.value]]
+
+    def policy_solve(self, alpha, beta, w0=None, allow_notconv=False):
         alpha, beta, w0 = _as(alpha, np.uint8), _as(beta, np.uint8), _as(w0, np.float64)
         w = np.empty(self.n, np.float64)
         st = gs_solve_stats()
-        _check(lib.gamesolve_policy_solve(self.h, _ptr(alpha), _ptr(beta), _ptr(w0), _ptr(w),
-                                          ctypes.byref(st)), "gamesolve_policy_solve")
-        return w, st.as_dict()
+        allow = (GS_OK, GS_ENOTCONV) if allow_notconv else (GS_OK,)
+        code = _check(lib.gamesolve_policy_solve(self.h, _ptr(alpha), _ptr(beta), _ptr(w0),
+                                                 _ptr(w), ctypes.byref(st)),
+                      "gamesolve_policy_solve", allow)
+        d = st.as_dict()
+        d["status"] = code
+        return w, d
 
 
 class GameServer:
@@ -365,6 +383,21 @@ class GameServer:
         _check(lib.gamesolve_server_result(self.h, ticket, _ptr(v), n, _ptr(a), _ptr(b)),
                "gamesolve_server_result", (GS_OK, GS_ENOTCONV))
         return v, a, b
+
+
+def fmg_interpolate(side_c, variant, v_c, alpha_c, beta_c):
+    """FAMGpi's value and strategy interpolations (Sec. 5.2) to side 2 side_c + 1."""
+    m1 = 5 if variant == 1 else 4
+    v_c, alpha_c = _as(v_c, np.float64), _as(alpha_c, np.uint8)
+    beta_c = _as(beta_c, np.uint8)
+    sf = 2 * side_c + 1
+    v = np.empty(sf * sf, np.float64)
+    a = np.empty(sf * sf, np.uint8)
+    b = np.empty((sf * sf, m1), np.uint8)
+    _check(lib.gamesolve_fmg_interpolate(side_c, variant, _ptr(v_c), _ptr(alpha_c), _ptr(beta_c),
+                                         _ptr(v), _ptr(a), _ptr(b), None),
+           "gamesolve_fmg_interpolate")
+    return v, a, b
 
 
 def exported_symbols():

@@ -80,6 +80,7 @@ void gamesolve_default_options(gs_options* o) {
     o->nu1_coarse = -1;
     o->nu2_coarse = -1;
     o->game_threads = 0;
+    o->cycle_kernel = 1;
 }
 
 gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
@@ -99,6 +100,7 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
         o.grid_blocks < 0 || o.cycle_gamma < 0 || o.cycle_gamma > 2 || o.nu1_coarse < -1 ||
         o.nu2_coarse < -1 ||
         (o.game_threads != 0 && o.game_threads != 256 && o.game_threads != 512) ||
+        o.cycle_kernel < 0 || o.cycle_kernel > 1 ||
         (o.nu1_coarse < 0 ? o.nu1 : o.nu1_coarse) + (o.nu2_coarse < 0 ? o.nu2 : o.nu2_coarse) < 1) {
         set_last_error("create: invalid option value");
         return GS_EINVAL;
@@ -345,6 +347,34 @@ gs_status gamesolve_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8
         return GS_EINVAL;
     }
     return guarded([&]() { return run_policy_solve(s, alpha, beta, w0, w_out, stats); });
+}
+
+gs_status gamesolve_fmg_interpolate(int32_t side_c, int32_t variant, const double* v_c,
+                                    const uint8_t* alpha_c, const uint8_t* beta_c, double* v_f,
+                                    uint8_t* alpha_f, uint8_t* beta_f, void* stream) {
+    if (side_c < 1 || side_c > 8191 || (variant != 0 && variant != 1) || !v_c || !alpha_c ||
+        !beta_c) {
+        set_last_error("fmg_interpolate: invalid argument");
+        return GS_EINVAL;
+    }
+    return guarded([&]() {
+        return run_fmg_interpolate(side_c, variant, v_c, alpha_c, beta_c, v_f, alpha_f, beta_f,
+                                   (cudaStream_t)stream);
+    });
+}
+
+gs_status gamesolve_get_level_stats(const gs_solver* s, int32_t* stats, int32_t cap,
+                                    int32_t* levels) {
+    if (!s || cap < 0 || (cap > 0 && !stats)) return GS_EINVAL;
+    if (!s->prob || s->prob->kind != 1 || s->level_stats.empty()) {
+        set_last_error("get_level_stats: no solved Isaacs grid");
+        return GS_ESTATE;
+    }
+    const int nl = (int)s->level_stats.size() / 3;
+    if (levels) *levels = nl;
+    for (int k = 0; k < nl && k < cap; ++k)
+        for (int j = 0; j < 3; ++j) stats[3 * k + j] = s->level_stats[3 * k + j];
+    return GS_OK;
 }
 
 gs_status gamesolve_trace(gs_solver* s, int32_t kernel_class) {

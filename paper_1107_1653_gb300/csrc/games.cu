@@ -456,11 +456,14 @@ __device__ bool cycle(const Game& G, const BatchOut& O, double* v, Ctx& C, T asu
     return C.sync();
 }
 
-// Policy evaluation: cycles until the float64 floor / tolerance (exact) or a
-// residual drop by rel_tol (inexact).  Returns true when exact.
+// Why a policy evaluation stopped.
+enum { kEvalExact = 0, kEvalInexact = 1, kEvalCapped = 2 };
+
+// Policy evaluation: cycles until the float64 floor / tolerance (kEvalExact),
+// a residual drop by rel_tol (kEvalInexact) or max_cycles (kEvalCapped).
 template <typename T, class Ctx>
-__device__ bool evaluate(const Game& G, const BatchOut& O, const BatchOpts& P, double* v, Ctx& C,
-                         double rel_tol, int* cycles) {
+__device__ int evaluate(const Game& G, const BatchOut& O, const BatchOpts& P, double* v, Ctx& C,
+                        double rel_tol, int* cycles) {
     double part = 0.0;
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) part += G.T.leak[O.sel[G.x0 + i]];
     const T asum = (T)C.sum(part);
@@ -470,16 +473,16 @@ __device__ bool evaluate(const Game& G, const BatchOut& O, const BatchOpts& P, d
     double prev = res;
     int slow = 0;
     for (int cyc = 0;; ++cyc) {
-        if (C.failed()) return true;
-        if (res <= P.lin_tol * fmax(vm, 1e-300) || res == 0.0) return true;
+        if (C.failed()) return kEvalExact;   // a barrier gave up: the caller leaves
+        if (res <= P.lin_tol * fmax(vm, 1e-300) || res == 0.0) return kEvalExact;
         if (cyc > 0) {
             slow = res > 0.5 * prev ? slow + 1 : 0;
-            if (slow >= 2 && res < 1e-12 * fmax(vm, 1e-300)) return true;
-            if (res <= rel_tol * res0) return false;
+            if (slow >= 2 && res < 1e-12 * fmax(vm, 1e-300)) return kEvalExact;
+            if (res <= rel_tol * res0) return kEvalInexact;
             prev = fmin(prev, res);
         }
-        if (cyc >= P.max_cycles) return true;
-        if (!cycle<T>(G, O, v, C, asum, P.nu1, P.nu2)) return true;
+        if (cyc >= P.max_cycles) return kEvalCapped;
+        if (!cycle<T>(G, O, v, C, asum, P.nu1, P.nu2)) return kEvalExact;
         ++*cycles;
         res = check<T>(G, O, v, C, &vm);
     }
@@ -534,17 +537,23 @@ __device__ void solve_game(const BatchArgs& B, int g, Ctx& C) {
     improve_all(G, O, 2, v, C, (double*)nullptr);   // MIN's first reply, assembly
     if (!C.sync()) return;
     int outer = 0, systems = 0, cycles = 0, converged = 0;
+    bool capped = false;   // an evaluation stopped at max_cycles: no decision may rest on it
     double res = 0.0;
     while (true) {
         for (int j = 0; j < P.max_inner; ++j) {
-            const bool exact = evaluate<T>(G, O, P, v, C, P.pi_rtol, &cycles);
+            const int why = evaluate<T>(G, O, P, v, C, P.pi_rtol, &cycles);
             ++systems;
             if (!C.sync()) return;
+            if (why == kEvalCapped) {
+                capped = true;
+                break;
+            }
             if (improve_all(G, O, 1, v, C, (double*)nullptr) != 0) continue;
             if (!C.sync()) return;
-            if (!exact) {
-                evaluate<T>(G, O, P, v, C, 0.0, &cycles);
+            if (why == kEvalInexact) {
+                if (evaluate<T>(G, O, P, v, C, 0.0, &cycles) == kEvalCapped) capped = true;
                 if (!C.sync()) return;
+                if (capped) break;
                 if (improve_all(G, O, 1, v, C, (double*)nullptr) != 0) continue;
                 if (!C.sync()) return;
             }
@@ -554,6 +563,7 @@ __device__ void solve_game(const BatchArgs& B, int g, Ctx& C) {
         if (!C.sync()) return;
         const int ach = improve_all(G, O, 0, v, C, &res);
         if (!C.sync()) return;
+        if (capped) break;   // unconverged; v is the best iterate, res its residual
         if (res <= P.eps || ach == 0) {
             converged = 1;
             break;

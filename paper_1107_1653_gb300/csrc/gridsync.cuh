@@ -30,6 +30,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 struct GridSync {
     GridBarrier* b;
     unsigned nb;
+    unsigned long long limit_ns = kBarrierTimeoutNs;   // how long one wait may last
     __device__ bool sync() const {
         __shared__ int s_ok;
         __syncthreads();
@@ -43,7 +44,7 @@ struct GridSync {
                 const unsigned long long t0 = global_ns();
                 while (((old ^ *word) & 0x80000000u) == 0) {
                     if (*(volatile int*)&b->error) { ok = 0; break; }
-                    if (global_ns() - t0 > kBarrierTimeoutNs) {
+                    if (global_ns() - t0 > limit_ns) {
                         atomicExch(&b->error, 1);
                         ok = 0;
                         break;

@@ -4,6 +4,7 @@
 // The small coarse levels (the "tail") are relaxed by thread block 0 alone,
 // out of shared memory.  Every grid-wide wait is bounded in time; a wait that
 // gives up sets an error flag and the kernels return.
+#include <algorithm>
 #include <mutex>
 
 #include "gridsync.cuh"
@@ -783,12 +784,709 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_cycles(const __grid_constant_
     }
 }
 
+// ------------------------------------------------------------------ tiled V-cycle
+// The same V-cycle (Algorithm 3, gamma = 1) with far fewer grid-wide barriers.
+// A grid-wide level is cut into tiles, one thread block per tile at a time.
+// A tile stages its points plus a halo in shared memory and runs a whole leg
+// of the cycle there:
+//  - down, coarse level l: the pre-smoothing colours, the residual and the
+//    restriction into level l + 1 (with that level's first colour);
+//  - up, coarse level l: the prolongation from level l + 1 and every
+//    post-smoothing colour;
+//  - the finest level, one phase per cycle: prolongation, post-smoothing,
+//    the float64 update v += e (mixed path), the float64 residual of the
+//    stopping test, then the next cycle's pre-smoothing and restriction
+//    (discarded when the test stops the solve).
+// Each colour update leaves the values it computed exact on a region one
+// point narrower on every side that faces another tile (a point's new value
+// needs its neighbours' current ones), so the halo is as deep as the updates
+// a leg makes; the tile's own points are exact at the end and only they are
+// written back.  Every point is computed by the same arithmetic as in the
+// phase-per-colour kernel above; the halo points are recomputed by the
+// neighbouring tiles.  One grid-wide barrier per leg remains (about 2 per
+// level and cycle instead of 13 at V(1,2)); thread block 0 keeps the tail
+// levels in its shared memory and takes no tiles.
+
+// Tile k of a level of side sf whose next coarser level has side sc: the
+// coarser points [I0, I1) x [J0, J1) it restricts to, the points of this level
+// it owns ([2 I0, 2 I1) per direction, plus the last point 2 sc for the last
+// tile) and the staged region: [2 I0 - H, 2 I1 + 1 + H) clipped to the level.
+struct Tile {
+    int I0, I1, J0, J1;
+    int ox0, ox1, oy0, oy1;
+    int gx0, gx1, gy0, gy1;
+    int w, h;
+    __device__ __forceinline__ int loc(int i, int j) const { return (j - gy0) * w + (i - gx0); }
+};
+
+__device__ __forceinline__ Tile make_tile(int k, int tc, int sc, int sf, int H) {
+    const int ntx = (sc + tc - 1) / tc;
+    Tile t;
+    const int ty = k / ntx, tx = k - ty * ntx;
+    t.I0 = tx * tc;
+    t.I1 = min(sc, t.I0 + tc);
+    t.J0 = ty * tc;
+    t.J1 = min(sc, t.J0 + tc);
+    t.ox0 = 2 * t.I0;
+    t.ox1 = t.I1 == sc ? sf : 2 * t.I1;
+    t.oy0 = 2 * t.J0;
+    t.oy1 = t.J1 == sc ? sf : 2 * t.J1;
+    t.gx0 = max(0, 2 * t.I0 - H);
+    t.gx1 = min(sf, 2 * t.I1 + 1 + H);
+    t.gy0 = max(0, 2 * t.J0 - H);
+    t.gy1 = min(sf, 2 * t.J1 + 1 + H);
+    t.w = t.gx1 - t.gx0;
+    t.h = t.gy1 - t.gy0;
+    return t;
+}
+
+__device__ __forceinline__ int tile_count(int tc, int sc) {
+    const int nt = (sc + tc - 1) / tc;
+    return nt * nt;
+}
+
+// Rectangle on which the staged values are still exact.
+struct Valid {
+    int x0, x1, y0, y1;
+    // One colour update: sides that face another tile lose one point.
+    __device__ __forceinline__ void shrink(int side) {
+        if (x0 > 0) ++x0;
+        if (x1 < side) --x1;
+        if (y0 > 0) ++y0;
+        if (y1 < side) --y1;
+    }
+};
+
+// Calls f(i, j) for the points i = px, j = py (mod 2) of the rectangle,
+// spread over the block's threads.
+template <class F>
+__device__ __forceinline__ void for_sublattice(const Valid& r, int px, int py, F&& f) {
+    const int i0 = r.x0 + ((r.x0 ^ px) & 1), j0 = r.y0 + ((r.y0 ^ py) & 1);
+    const int nx = (r.x1 - i0 + 1) >> 1, ny = (r.y1 - j0 + 1) >> 1;
+    if (nx <= 0 || ny <= 0) return;
+    const FastDiv dv((unsigned)nx);
+    for (unsigned t = threadIdx.x; t < (unsigned)(nx * ny); t += blockDim.x) {
+        unsigned rr;
+        const int q = (int)dv.divmod(t, &rr);
+        f(i0 + 2 * (int)rr, j0 + 2 * q);
+    }
+}
+
+// Points with (i + j) = c (mod 2) of the rectangle (the fine level's colours).
+template <class F>
+__device__ __forceinline__ void for_redblack(const Valid& r, int c, F&& f) {
+    for_sublattice(r, c, 0, f);
+    for_sublattice(r, c ^ 1, 1, f);
+}
+
+template <class F>
+__device__ __forceinline__ void for_rect(int x0, int x1, int y0, int y1, F&& f) {
+    const int nx = x1 - x0, ny = y1 - y0;
+    if (nx <= 0 || ny <= 0) return;
+    const FastDiv dv((unsigned)nx);
+    for (unsigned t = threadIdx.x; t < (unsigned)(nx * ny); t += blockDim.x) {
+        unsigned rr;
+        const int q = (int)dv.divmod(t, &rr);
+        f(x0 + (int)rr, y0 + q);
+    }
+}
+
+// Shared-memory forms of the level operators (same arithmetic as L0Op / L9Op).
+struct TFine32 {
+    const IsaacsConsts* K;
+    const uint8_t* code;   // staged codes
+    int side, w;
+    __device__ __forceinline__ float relaxed(const float* f, const float* u, int k, int i, int j) const {
+        const int c = code[k];
+        const float* am = K->amf[c];
+        float diag = l0_rowsum_f(K, c, i, j, side), s = f[k];
+        if (i > 0) { diag -= am[1]; s -= am[1] * u[k - 1]; }
+        if (i + 1 < side) { diag -= am[2]; s -= am[2] * u[k + 1]; }
+        if (j > 0) { diag -= am[3]; s -= am[3] * u[k - w]; }
+        if (j + 1 < side) { diag -= am[4]; s -= am[4] * u[k + w]; }
+        return s / diag;
+    }
+    __device__ __forceinline__ float diag(int k, int i, int j) const {
+        const int c = code[k];
+        const float* am = K->amf[c];
+        float d = l0_rowsum_f(K, c, i, j, side);
+        if (i > 0) d -= am[1];
+        if (i + 1 < side) d -= am[2];
+        if (j > 0) d -= am[3];
+        if (j + 1 < side) d -= am[4];
+        return d;
+    }
+    __device__ __forceinline__ float resid(const float* f, const float* u, int k, int i, int j) const {
+        const int c = code[k];
+        const float* am = K->amf[c];
+        const float ux = u[k];
+        float Au = l0_rowsum_f(K, c, i, j, side) * ux;
+        if (i > 0) Au += am[1] * (u[k - 1] - ux);
+        if (i + 1 < side) Au += am[2] * (u[k + 1] - ux);
+        if (j > 0) Au += am[3] * (u[k - w] - ux);
+        if (j + 1 < side) Au += am[4] * (u[k + w] - ux);
+        return f[k] - Au;
+    }
+};
+
+struct TFine64 {
+    const IsaacsConsts* K;
+    const uint8_t* code;
+    int side, w;
+    // fx - (A v)(i, j): five fused multiply-adds, boundary couplings times +0
+    __device__ __forceinline__ double resid(double fx, const double* v, int k, int i, int j) const {
+        const double* am = K->am[code[k]];
+        double r = fma(-am[0], v[k], fx);
+        r = fma(-am[1], load_or_zero(v, (size_t)(k - 1), i > 0), r);
+        r = fma(-am[2], load_or_zero(v, (size_t)(k + 1), i + 1 < side), r);
+        r = fma(-am[3], load_or_zero(v, (size_t)(k - w), j > 0), r);
+        return fma(-am[4], load_or_zero(v, (size_t)(k + w), j + 1 < side), r);
+    }
+    __device__ __forceinline__ double relaxed(const double* f, const double* u, int k, int i, int j) const {
+        const double* am = K->am[code[k]];
+        double s = f[k];
+        if (i > 0) s -= am[1] * u[k - 1];
+        if (i + 1 < side) s -= am[2] * u[k + 1];
+        if (j > 0) s -= am[3] * u[k - w];
+        if (j + 1 < side) s -= am[4] * u[k + w];
+        return s / am[0];
+    }
+};
+
+// 9-point level in shared memory: A[d * wh + k] in the cycle's type (float32
+// rows in leakage form: row sum in slot 0).
+template <typename T>
+struct T9 {
+    const T* A;
+    int side, w, wh;
+    __device__ __forceinline__ T resid(const T* f, const T* u, int k, int i, int j) const {
+        const T ux = u[k];
+        T Au = A[k] * ux;
+#pragma unroll
+        for (int d = 1; d < 9; ++d) {
+            const int gi = i + dir_di(d), gj = j + dir_dj(d);
+            const bool in = gi >= 0 && gj >= 0 && gi < side && gj < side;
+            const T ud = in ? u[k + dir_di(d) + dir_dj(d) * w] : T(0);
+            if constexpr (sizeof(T) == 8) Au += A[d * wh + k] * ud;
+            else Au += A[d * wh + k] * (ud - ux);
+        }
+        return f[k] - Au;
+    }
+    __device__ __forceinline__ T relaxed(const T* f, const T* u, int k, int i, int j) const {
+        T s = f[k];
+        T diag = A[k];
+#pragma unroll
+        for (int d = 1; d < 9; ++d) {
+            const T a = A[d * wh + k];
+            if constexpr (sizeof(T) == 4) diag -= a;
+            const int gi = i + dir_di(d), gj = j + dir_dj(d);
+            if (gi < 0 || gj < 0 || gi >= side || gj >= side) continue;
+            s -= a * u[k + dir_di(d) + dir_dj(d) * w];
+        }
+        return s / diag;
+    }
+};
+
+// Correction of level l at its point (i, j) from level l + 1 (u_c of side sc,
+// weights P of the cells (I, J) in [0, sc]^2): the prolongation P u_c.
+template <typename T, typename W>
+__device__ __forceinline__ T prolonged(const W* Pw, const T* uc, int sc, int i, int j) {
+    const int nc1 = sc + 1;
+    const size_t ncell = (size_t)nc1 * nc1;
+    auto P = [&](int k, size_t c) -> T { return (T)wval(Pw[k * ncell + c]); };
+    auto U = [&](int p, int q) -> T {
+        return (p < 0 || q < 0 || p >= sc || q >= sc) ? T(0) : uc[(size_t)q * sc + p];
+    };
+    if (!(i & 1)) {
+        const int I = i >> 1;
+        if (!(j & 1)) {   // cell corner (2I, 2J)
+            const int J = j >> 1;
+            const size_t t = (size_t)J * nc1 + I;
+            return P(PSW, t) * U(I - 1, J - 1) + P(PSE, t) * U(I, J - 1) + P(PNW, t) * U(I - 1, J) +
+                   P(PNE, t) * U(I, J);
+        }
+        const int J = j >> 1;   // x-edge (2I, 2J + 1)
+        const size_t t = (size_t)J * nc1 + I;
+        return P(PXW, t) * U(I - 1, J) + P(PXE, t) * U(I, J);
+    }
+    const int I = i >> 1;
+    if (!(j & 1)) {   // y-edge (2I + 1, 2J)
+        const int J = j >> 1;
+        const size_t t = (size_t)J * nc1 + I;
+        return P(PYS, t) * U(I, J - 1) + P(PYN, t) * U(I, J);
+    }
+    return U(I, j >> 1);   // C point (2I + 1, 2J + 1)
+}
+
+// Restriction of the staged residuals r (rows of width rw from fine point
+// (2 I0, 2 J0)) into the tile's points of level l + 1: f_c = R r.  The next
+// level's first colour (f_c / diag at its C points) is formed by whoever
+// stages f_c; zero_uc clears u_c instead (level l + 1 is the tail, relaxed by
+// block 0 from u_c = 0).
+template <typename T, typename W>
+__device__ void tile_restrict(const Tile& t, const T* r, int rw, const LevelArgs& L,
+                              const LevelArgs& C, bool zero_uc) {
+    const W* P = (const W*)L.P;
+    const int sc = L.sc;
+    T* fc = (T*)C.f;
+    T* uc = (T*)C.u;
+    for_rect(t.I0, t.I1, t.J0, t.J1, [&](int I, int J) {
+        T acc = 0;
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+            for (int di = -1; di <= 1; ++di)
+                acc += (T)restrict_weight(P, sc, I, J, di, dj) *
+                       r[(2 * (J - t.J0) + 1 + dj) * rw + 2 * (I - t.I0) + 1 + di];
+        const size_t x = (size_t)J * sc + I;
+        fc[x] = acc;
+        if (zero_uc) uc[x] = T(0);
+    });
+}
+
+// Diagonal of a staged 9-point row, as L9Op::diag forms it.
+template <typename T>
+__device__ __forceinline__ T diag9(const T* A, int wh, int q) {
+    T d = A[q];
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 1; k < 9; ++k) d -= A[k * wh + q];
+    }
+    return d;
+}
+
+// Down leg of a coarse level l (1 <= l < tail): pre-smoothing (the first
+// colour was done by the restriction into l), residual, restriction.
+template <typename T, typename W>
+__device__ void tile_down(const SolveArgs& a, int l, char* smem, int worker, int nworkers) {
+    const LevelArgs& L = a.L[l];
+    const LevelArgs& C = a.L[l + 1];
+    const int sf = L.side, sc = L.sc, nu = a.nu1c;
+    const int K1 = nu > 0 ? 4 * nu - 1 : 0;
+    const int H = 1 + K1;
+    const bool zero_uc = l + 1 == a.tail;
+    const int ntiles = tile_count(a.tcc, sc);
+    const W* gA = (const W*)L.A;
+    T* gu = (T*)L.u;
+    const T* gf = (const T*)L.f;
+    for (int k = worker; k < ntiles; k += nworkers) {
+        const Tile t = make_tile(k, a.tcc, sc, sf, H);
+        const int wh = t.w * t.h;
+        T* A = (T*)smem;
+        T* u = A + 9 * wh;
+        T* f = u + wh;
+        T* r = f + wh;   // residuals at fine points [2 I0, 2 I1] x [2 J0, 2 J1]
+        for_rect(t.gx0, t.gx1, t.gy0, t.gy1, [&](int i, int j) {
+            const size_t x = (size_t)j * sf + i;
+            const int q = t.loc(i, j);
+            f[q] = gf[x];
+#pragma unroll
+            for (int d = 0; d < 9; ++d) A[d * wh + q] = (T)wval(gA[d * L.n + x]);
+            // u from the zero start, the first colour (C points) relaxed: f / diag
+            u[q] = nu > 0 && (i & j & 1) ? f[q] / diag9(A, wh, q) : T(0);
+        });
+        __syncthreads();
+        const T9<T> op{A, sf, t.w, wh};
+        Valid v{t.gx0, t.gx1, t.gy0, t.gy1};
+        for (int s = 0; s < nu; ++s)
+            for (int c = 0; c < 4; ++c) {
+                if (s == 0 && c == 0) continue;   // done by the restriction into this level
+                v.shrink(sf);
+                for_sublattice(v, colour_ox(c), colour_oy(c), [&](int i, int j) {
+                    const int q = t.loc(i, j);
+                    u[q] = op.relaxed(f, u, q, i, j);
+                });
+                __syncthreads();
+            }
+        const int rx1 = min(sf, 2 * t.I1 + 1), ry1 = min(sf, 2 * t.J1 + 1);
+        const int rw = 2 * (t.I1 - t.I0) + 1;
+        for_rect(t.ox0, rx1, t.oy0, ry1, [&](int i, int j) {
+            r[(j - t.oy0) * rw + (i - t.ox0)] = op.resid(f, u, t.loc(i, j), i, j);
+        });
+        __syncthreads();
+        tile_restrict<T, W>(t, r, rw, L, C, zero_uc);
+        for_rect(t.ox0, t.ox1, t.oy0, t.oy1, [&](int i, int j) { gu[(size_t)j * sf + i] = u[t.loc(i, j)]; });
+        __syncthreads();
+    }
+}
+
+// Up leg of a coarse level l: prolongation from l + 1, post-smoothing.
+template <typename T, typename W>
+__device__ void tile_up(const SolveArgs& a, int l, char* smem, int worker, int nworkers) {
+    const LevelArgs& L = a.L[l];
+    const LevelArgs& C = a.L[l + 1];
+    const int sf = L.side, sc = L.sc, nu = a.nu2c;
+    const int H = 4 * nu;
+    const int ntiles = tile_count(a.tcc, sc);
+    const W* gA = (const W*)L.A;
+    const W* gP = (const W*)L.P;
+    const T* guc = (const T*)(l + 1 == a.tail ? C.u : C.u2);
+    const T* gu = (const T*)L.u;   // after the pre-smoothing
+    T* gu2 = (T*)L.u2;             // after the post-smoothing (other tiles still read gu)
+    const T* gf = (const T*)L.f;
+    for (int k = worker; k < ntiles; k += nworkers) {
+        const Tile t = make_tile(k, a.tcc, sc, sf, H);
+        const int wh = t.w * t.h;
+        T* A = (T*)smem;
+        T* u = A + 9 * wh;
+        T* f = u + wh;
+        for_rect(t.gx0, t.gx1, t.gy0, t.gy1, [&](int i, int j) {
+            const size_t x = (size_t)j * sf + i;
+            const int q = t.loc(i, j);
+            u[q] = gu[x] + prolonged<T, W>(gP, guc, sc, i, j);
+            f[q] = gf[x];
+#pragma unroll
+            for (int d = 0; d < 9; ++d) A[d * wh + q] = (T)wval(gA[d * L.n + x]);
+        });
+        __syncthreads();
+        const T9<T> op{A, sf, t.w, wh};
+        Valid v{t.gx0, t.gx1, t.gy0, t.gy1};
+        for (int s = 0; s < nu; ++s)
+            for (int c = 0; c < 4; ++c) {
+                v.shrink(sf);
+                for_sublattice(v, colour_ox(c), colour_oy(c), [&](int i, int j) {
+                    const int q = t.loc(i, j);
+                    u[q] = op.relaxed(f, u, q, i, j);
+                });
+                __syncthreads();
+            }
+        for_rect(t.ox0, t.ox1, t.oy0, t.oy1, [&](int i, int j) { gu2[(size_t)j * sf + i] = u[t.loc(i, j)]; });
+        __syncthreads();
+    }
+}
+
+// Buffers of the finest level's phase: what it reads and what it writes.
+// Other tiles stage their halos from the inputs while a tile writes its own
+// points, so outputs never alias inputs (the kernel swaps them each cycle).
+struct FineBufs {
+    const double* v_in;
+    const void* e_in;   // mixed: correction e after the pre-smoothing
+    const void* r_in;   // mixed: its right-hand side (float64 residual, rounded)
+    double* v_out;      // mixed: v + e after the post-smoothing; float64: v after it
+    void* e_out;        // mixed: next correction after the pre-smoothing
+    void* r_out;
+    double* v_pre;      // float64: v after the next pre-smoothing
+};
+
+// The finest level's phase, mixed path (float32 correction e of the float64
+// value v).  full: prolongation, post-smoothing and v += e first (else the
+// launch's first residual evaluation, e = 0).  Then the float64 residual
+// r = rhs - A v with |r|_inf, |v|_inf into out slot `slot`, r rounded to
+// float32 as the correction's right-hand side, the pre-smoothing from e = 0
+// (first colour e = r / diag) and the restriction into level 1.
+template <typename W>
+__device__ void tile_fine_mixed(const SolveArgs& a, bool full, int slot, const FineBufs& B,
+                                char* smem, int worker, int nworkers) {
+    const LevelArgs& L = a.L[0];
+    const LevelArgs& C = a.L[1];
+    const int sf = L.side, sc = L.sc;
+    const int K2 = full ? 2 * a.nu2 : 0;
+    const int K1 = a.nu1 > 0 ? 2 * a.nu1 - 1 : 0;
+    const int H = 2 + K1 + K2;
+    const bool zero_uc = a.tail == 1;
+    const int ntiles = tile_count(a.tc0, sc);
+    const W* gP = (const W*)L.P;
+    const float* guc = (const float*)(a.tail == 1 ? C.u : C.u2);
+    const float* ge = (const float*)B.e_in;
+    const float* gr = (const float*)B.r_in;
+    float* ge_out = (float*)B.e_out;
+    float* gr_out = (float*)B.r_out;
+    unsigned long long rm = 0, vm = 0;
+    for (int k = worker; k < ntiles; k += nworkers) {
+        const Tile t = make_tile(k, a.tc0, sc, sf, H);
+        const int wh = t.w * t.h;
+        double* v = (double*)smem;
+        float* e = (float*)(v + wh);
+        float* f = e + wh;
+        uint8_t* code = (uint8_t*)(f + wh);
+        for_rect(t.gx0, t.gx1, t.gy0, t.gy1, [&](int i, int j) {
+            const size_t x = (size_t)j * sf + i;
+            const int q = t.loc(i, j);
+            code[q] = a.code[x];
+            v[q] = B.v_in[x];
+            if (full) {
+                e[q] = ge[x] + prolonged<float, W>(gP, guc, sc, i, j);
+                f[q] = gr[x];
+            }
+        });
+        __syncthreads();
+        const TFine32 op{a.K, code, sf, t.w};
+        Valid vr{t.gx0, t.gx1, t.gy0, t.gy1};
+        if (full) {
+            for (int s = 0; s < a.nu2; ++s)
+                for (int c = 0; c < 2; ++c) {
+                    vr.shrink(sf);
+                    for_redblack(vr, c, [&](int i, int j) {
+                        const int q = t.loc(i, j);
+                        e[q] = op.relaxed(f, e, q, i, j);
+                    });
+                    __syncthreads();
+                }
+            for_rect(vr.x0, vr.x1, vr.y0, vr.y1, [&](int i, int j) {
+                const int q = t.loc(i, j);
+                v[q] += f32_to_f64(e[q]);
+            });
+            __syncthreads();
+        }
+        // float64 residual of the stopping test on a region one narrower
+        vr.shrink(sf);
+        const TFine64 op64{a.K, code, sf, t.w};
+        const bool relax0 = a.nu1 > 0;
+        for_rect(vr.x0, vr.x1, vr.y0, vr.y1, [&](int i, int j) {
+            const int q = t.loc(i, j);
+            const double r = op64.resid(a.rhs[(size_t)j * sf + i], v, q, i, j);
+            const float rf = f64_to_f32(r);
+            f[q] = rf;
+            if (i >= t.ox0 && i < t.ox1 && j >= t.oy0 && j < t.oy1) {
+                rm = max(rm, abs_bits(r));
+                vm = max(vm, abs_bits(v[q]));
+            }
+            e[q] = relax0 && ((i + j) & 1) == 0 ? rf / op.diag(q, i, j) : 0.0f;
+        });
+        __syncthreads();
+        // pre-smoothing: the first colour was the pointwise e = r / diag
+        for (int s = 0; s < a.nu1; ++s)
+            for (int c = 0; c < 2; ++c) {
+                if (s == 0 && c == 0) continue;
+                vr.shrink(sf);
+                for_redblack(vr, c, [&](int i, int j) {
+                    const int q = t.loc(i, j);
+                    e[q] = op.relaxed(f, e, q, i, j);
+                });
+                __syncthreads();
+            }
+        // residuals of the correction at fine points [2 I0, 2 I1] x [2 J0, 2 J1]
+        const int rx1 = min(sf, 2 * t.I1 + 1), ry1 = min(sf, 2 * t.J1 + 1);
+        const int rw = 2 * (t.I1 - t.I0) + 1;
+        float* r = (float*)(code + ((wh + 15) & ~15));
+        for_rect(t.ox0, rx1, t.oy0, ry1, [&](int i, int j) {
+            r[(j - t.oy0) * rw + (i - t.ox0)] = op.resid(f, e, t.loc(i, j), i, j);
+        });
+        // the tile's own points
+        for_rect(t.ox0, t.ox1, t.oy0, t.oy1, [&](int i, int j) {
+            const size_t x = (size_t)j * sf + i;
+            const int q = t.loc(i, j);
+            if (full) B.v_out[x] = v[q];
+            ge_out[x] = e[q];
+            gr_out[x] = f[q];
+        });
+        __syncthreads();
+        tile_restrict<float, W>(t, r, rw, L, C, zero_uc);
+        __syncthreads();
+    }
+    rm = warp_max_u64(rm);
+    vm = warp_max_u64(vm);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&a.out->rmax[slot], rm);
+        atomicMax(&a.out->vmax[slot], vm);
+    }
+}
+
+// The finest level's phase, float64 path (the cycle relaxes v itself,
+// right-hand side rhs): full: prolongation and post-smoothing, the result to
+// v_out; the residual of the stopping test at the tile's own points; the
+// pre-smoothing (to v_pre) and the restriction.
+__device__ void tile_fine_fp64(const SolveArgs& a, bool full, int slot, const FineBufs& B,
+                               char* smem, int worker, int nworkers) {
+    const LevelArgs& L = a.L[0];
+    const LevelArgs& C = a.L[1];
+    const int sf = L.side, sc = L.sc;
+    const int K2 = full ? 2 * a.nu2 : 0;
+    const int K1 = 2 * a.nu1;
+    const int H = 1 + K1 + K2;
+    const bool zero_uc = a.tail == 1;
+    const int ntiles = tile_count(a.tc0, sc);
+    const double* gP = (const double*)L.P;
+    const double* guc = (const double*)(a.tail == 1 ? C.u : C.u2);
+    unsigned long long rm = 0, vm = 0;
+    for (int k = worker; k < ntiles; k += nworkers) {
+        const Tile t = make_tile(k, a.tc0, sc, sf, H);
+        const int wh = t.w * t.h;
+        double* v = (double*)smem;
+        double* f = v + wh;
+        uint8_t* code = (uint8_t*)(f + wh);
+        for_rect(t.gx0, t.gx1, t.gy0, t.gy1, [&](int i, int j) {
+            const size_t x = (size_t)j * sf + i;
+            const int q = t.loc(i, j);
+            code[q] = a.code[x];
+            v[q] = full ? B.v_in[x] + prolonged<double, double>(gP, guc, sc, i, j) : B.v_in[x];
+            f[q] = a.rhs[x];
+        });
+        __syncthreads();
+        const TFine64 op{a.K, code, sf, t.w};
+        Valid vr{t.gx0, t.gx1, t.gy0, t.gy1};
+        for (int s = 0; s < (full ? a.nu2 : 0); ++s)
+            for (int c = 0; c < 2; ++c) {
+                vr.shrink(sf);
+                for_redblack(vr, c, [&](int i, int j) {
+                    const int q = t.loc(i, j);
+                    v[q] = op.relaxed(f, v, q, i, j);
+                });
+                __syncthreads();
+            }
+        for_rect(t.ox0, t.ox1, t.oy0, t.oy1, [&](int i, int j) {
+            const int q = t.loc(i, j);
+            rm = max(rm, abs_bits(op.resid(f[q], v, q, i, j)));
+            vm = max(vm, abs_bits(v[q]));
+            if (full) B.v_out[(size_t)j * sf + i] = v[q];
+        });
+        __syncthreads();
+        for (int s = 0; s < a.nu1; ++s)
+            for (int c = 0; c < 2; ++c) {
+                vr.shrink(sf);
+                for_redblack(vr, c, [&](int i, int j) {
+                    const int q = t.loc(i, j);
+                    v[q] = op.relaxed(f, v, q, i, j);
+                });
+                __syncthreads();
+            }
+        const int rx1 = min(sf, 2 * t.I1 + 1), ry1 = min(sf, 2 * t.J1 + 1);
+        const int rw = 2 * (t.I1 - t.I0) + 1;
+        double* r = (double*)(code + ((wh + 15) & ~15));
+        for_rect(t.ox0, rx1, t.oy0, ry1, [&](int i, int j) {
+            const int q = t.loc(i, j);
+            r[(j - t.oy0) * rw + (i - t.ox0)] = op.resid(f[q], v, q, i, j);
+        });
+        for_rect(t.ox0, t.ox1, t.oy0, t.oy1,
+                 [&](int i, int j) { B.v_pre[(size_t)j * sf + i] = v[t.loc(i, j)]; });
+        __syncthreads();
+        tile_restrict<double, double>(t, r, rw, L, C, zero_uc);
+        __syncthreads();
+    }
+    rm = warp_max_u64(rm);
+    vm = warp_max_u64(vm);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&a.out->rmax[slot], rm);
+        atomicMax(&a.out->vmax[slot], vm);
+    }
+}
+
+template <typename T, typename W>
+__device__ __forceinline__ void tile_fine(const SolveArgs& a, bool full, int slot, const FineBufs& B,
+                                          char* smem, int worker, int nworkers) {
+    if constexpr (sizeof(T) == 4) tile_fine_mixed<W>(a, full, slot, B, smem, worker, nworkers);
+    else tile_fine_fp64(a, full, slot, B, smem, worker, nworkers);
+}
+
+// Buffers of the finest level's phase for set `cur` (see FineBufs).
+// Mixed: the sets (v, e, r) = (a.v, L0.u, L0.f) and (a.v2, a.e2, a.r2); the
+// first phase reads v from set 0 and writes e, r there; a full phase reads
+// set cur and writes set cur ^ 1.  Float64: a.v always receives the result
+// after the post-smoothing; the pre-smoothed v alternates between a.v2 and
+// a.v3 (cur), the first phase reading a.v.
+template <typename T>
+__device__ __forceinline__ FineBufs fine_bufs(const SolveArgs& a, bool full, int cur) {
+    FineBufs B{};
+    if constexpr (sizeof(T) == 4) {
+        double* vs[2] = {a.v, a.v2};
+        void* es[2] = {a.L[0].u, a.e2};
+        void* rs[2] = {a.L[0].f, a.r2};
+        const int in = cur, out = full ? cur ^ 1 : cur;
+        B.v_in = vs[in];
+        B.e_in = es[in];
+        B.r_in = rs[in];
+        B.v_out = vs[out];
+        B.e_out = es[out];
+        B.r_out = rs[out];
+    } else {
+        double* ys[2] = {a.v2, a.v3};
+        B.v_in = full ? ys[cur] : a.v;
+        B.v_out = a.v;
+        B.v_pre = full ? ys[cur ^ 1] : ys[0];
+    }
+    return B;
+}
+
+// V-cycles with tiled grid-wide levels; block 0 stages and runs the tail.
+template <typename T, typename W>
+__global__ void __launch_bounds__(kMGThreads, 2) k_mg_cycles_tiled(const __grid_constant__ SolveArgs a) {
+    extern __shared__ __align__(16) char smem_t[];
+    __shared__ LevelArgs tl[kMaxLevels];
+    const GridSync G{a.bar, gridDim.x};
+    const int worker = (int)blockIdx.x - 1, nworkers = (int)gridDim.x - 1;
+    if (!G.sync()) return;   // set-up complete (and error state shared)
+    prof_mark(8000);
+    double* inv = a.inv;
+    int slot = 0, cur = 0;
+    // block 0 stages the tail while the others take the first residual check
+    // with the first cycle's pre-smoothing and restriction
+    if (blockIdx.x == 0) stage_tail<T, W>(a, smem_t, tl, &inv);
+    else tile_fine<T, W>(a, false, slot, fine_bufs<T>(a, false, cur), smem_t, worker, nworkers);
+    if (!G.sync()) return;
+    prof_mark(6000);
+    double prev = 0.0, res0 = 0.0;
+    int slow = 0;
+    for (int cycles = 0;; ++cycles) {
+        const double res = __longlong_as_double((long long)__ldcg(&a.out->rmax[slot]));
+        const double vm = __longlong_as_double((long long)__ldcg(&a.out->vmax[slot]));
+        if (cycles == 0) res0 = res;
+        int reason = 0;
+        if (res <= a.lin_tol * fmax(vm, 1e-300) || res == 0.0) reason = 1;
+        if (cycles > 0) {
+            slow = res > 0.5 * prev ? slow + 1 : 0;
+            if (!reason && slow >= 2 && res < 1e-12 * fmax(vm, 1e-300)) reason = 1;
+            if (!reason && res <= a.rel_tol * res0) reason = 2;
+            prev = fmin(prev, res);
+        } else {
+            prev = res;
+        }
+        if (!reason && cycles >= a.max_cycles) reason = 3;
+        if (reason) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                a.out->cycles = cycles;
+                a.out->reason = reason;
+                a.out->res = res;
+                a.out->vmax_final = vm;
+            }
+            if constexpr (sizeof(T) == 4) {
+                // the last value went to the second set: copy it home
+                if (cur == 1) {
+                    const size_t n = a.L[0].n;
+                    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+                         x += (size_t)gridDim.x * blockDim.x)
+                        a.v[x] = a.v2[x];
+                }
+            }
+            return;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.out->rmax[slot ^ 1] = 0ull;
+            a.out->vmax[slot ^ 1] = 0ull;
+        }
+        for (int l = 1; l < a.tail; ++l) {
+            if (worker >= 0) tile_down<T, W>(a, l, smem_t, worker, nworkers);
+            if (!G.sync()) return;
+            prof_mark(2000 + 10 * l);
+        }
+        if (blockIdx.x == 0) block_vcycle<T, W>(a, tl, inv, a.tail, true);
+        if (!G.sync()) return;
+        prof_mark(4000);
+        for (int l = a.tail - 1; l >= 1; --l) {
+            if (worker >= 0) tile_up<T, W>(a, l, smem_t, worker, nworkers);
+            if (!G.sync()) return;
+            prof_mark(3000 + 10 * l);
+        }
+        slot ^= 1;
+        if (worker >= 0) tile_fine<T, W>(a, true, slot, fine_bufs<T>(a, true, cur), smem_t, worker, nworkers);
+        cur ^= 1;
+        if (!G.sync()) return;
+        prof_mark(6000);
+    }
+}
+
 // ------------------------------------------------------------------ launch
 struct Occupancy {
     int sms = 0;
     int setup_per_sm = 0;
     int cyc_per_sm[3] = {0, 0, 0};   // float32, float64, float32 on bfloat16 weights
 };
+
+// The tiled cycle kernel of a precision kind (0 float32, 1 float64, 2 bfloat16 weights).
+const void* tiled_kernel(int kind) {
+    return kind == 1   ? (const void*)k_mg_cycles_tiled<double, double>
+           : kind == 2 ? (const void*)k_mg_cycles_tiled<float, __nv_bfloat16>
+                       : (const void*)k_mg_cycles_tiled<float, float>;
+}
 
 Occupancy& occupancy() {
     static Occupancy o;
@@ -807,6 +1505,9 @@ Occupancy& occupancy() {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, big));
         GS_CUDA(cudaFuncSetAttribute(k_mg_cycles<float, __nv_bfloat16>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+        for (int kind = 0; kind < 3; ++kind)
+            GS_CUDA(cudaFuncSetAttribute(tiled_kernel(kind), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTiledSmemMax));
         GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.setup_per_sm, k_mg_setup, kMGThreads,
                                                               64 * 128 * 8));
         GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.cyc_per_sm[0], k_mg_cycles<float, float>,
@@ -829,7 +1530,45 @@ int grid_blocks(const SolveArgs& a, int per_sm, int sms) {
     return (int)std::max<size_t>(1, std::min(want, cap));
 }
 
+// Tiles of the largest tiled phase (the grid needs one more block: block 0 runs the tail).
+int tiled_max_tiles(const SolveArgs& a) {
+    auto tiles = [](int tc, int sc) {
+        const int nt = (sc + tc - 1) / tc;
+        return nt * nt;
+    };
+    int m = tiles(a.tc0, a.L[0].sc);
+    for (int l = 1; l < a.tail; ++l) m = std::max(m, tiles(a.tcc, a.L[l].sc));
+    return m;
+}
+
 }  // namespace
+
+size_t tiled_smem_bytes(const SolveArgs& a) {
+    const size_t T = a.mixed ? 4 : 8;
+    auto side = [](int tc, int sc, int sf, int H) {
+        return (size_t)std::min(sf, 2 * std::min(tc, sc) + 1 + 2 * H);
+    };
+    auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+    size_t need = tail_smem_bytes(a);
+    {   // finest level
+        const LevelArgs& L = a.L[0];
+        const int K1 = a.mixed ? (a.nu1 > 0 ? 2 * a.nu1 - 1 : 0) : 2 * a.nu1;
+        const int H = (a.mixed ? 2 : 1) + K1 + 2 * a.nu2;
+        const size_t w = side(a.tc0, L.sc, L.side, H), wh = w * w;
+        const size_t rw = 2 * (size_t)std::min(a.tc0, L.sc) + 1;
+        need = std::max(need, 16 * wh + r16(wh) + rw * rw * T);
+    }
+    for (int l = 1; l < a.tail; ++l) {
+        const LevelArgs& L = a.L[l];
+        const int K1 = a.nu1c > 0 ? 4 * a.nu1c - 1 : 0;
+        const size_t wd = side(a.tcc, L.sc, L.side, 1 + K1);
+        const size_t rw = 2 * (size_t)std::min(a.tcc, L.sc) + 1;
+        need = std::max(need, 11 * T * wd * wd + rw * rw * T);
+        const size_t wu = side(a.tcc, L.sc, L.side, 4 * a.nu2c);
+        need = std::max(need, 11 * T * wu * wu);
+    }
+    return need;
+}
 
 size_t tail_smem_bytes(const SolveArgs& a) {
     const int elem = a.mixed ? 4 : 8;
@@ -877,6 +1616,20 @@ void launch_mg_setup(const SolveArgs& a, cudaStream_t st) {
 void launch_mg_cycles(const SolveArgs& a, cudaStream_t st) {
     const Occupancy& o = occupancy();
     void* args[] = {(void*)&a};
+    if (a.tiled) {
+        const int kind = !a.mixed ? 1 : a.wbf16 ? 2 : 0;
+        const size_t smem = tiled_smem_bytes(a);
+        int per_sm = 0;
+        GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tiled_kernel(kind), kMGThreads,
+                                                              smem));
+        int nb = std::min(std::max(1, per_sm) * o.sms, 1 + tiled_max_tiles(a));
+        if (a.max_blocks > 0) nb = std::min(nb, a.max_blocks);
+        nb = std::max(nb, 2);
+        GS_CUDA(cudaLaunchCooperativeKernel(tiled_kernel(kind), dim3(nb), dim3(kMGThreads), args, smem,
+                                            st));
+        note_launches(1);
+        return;
+    }
     const size_t smem = tail_smem_bytes(a);
     const int kind = !a.mixed ? 1 : a.wbf16 ? 2 : 0;
     const void* fn = kind == 1   ? (const void*)k_mg_cycles<double, double>

@@ -26,6 +26,7 @@ struct LevelArgs {
                          // the first half of the same buffer)
     double* P64;         // interpolation weights (written by the set-up)
     float* P32;          // their rounded copy (float32, or bfloat16 likewise)
+    void* u2;            // tiled cycles: u after the post-smoothing (levels >= 1)
 };
 
 
@@ -55,6 +56,12 @@ struct SolveArgs {
     int max_blocks;  // cap on the grid (0 = whole GPU)
     double lin_tol;
     double rel_tol;  // also stop once the residual fell by this factor (0: floor only)
+    int tiled;       // V-cycles with tiled grid-wide levels (k_mg_cycles_tiled)
+    int tc0, tcc;    // tile sides, in points of the next coarser level: finest, coarse levels
+    double* v2;      // tiled cycles, finest level: second value buffer
+    double* v3;      // float64 path: third value buffer
+    void* e2;        // mixed path: second correction buffer
+    void* r2;        // mixed path: second right-hand-side buffer
     double* inv;     // inverse of the coarsest operator (n_L x n_L)
     int* inv_status;
     GridBarrier* bar;
@@ -70,5 +77,10 @@ void launch_mg_cycles(const SolveArgs& a, cudaStream_t st);
 
 // Shared memory the tail levels >= a.smem_from need.
 size_t tail_smem_bytes(const SolveArgs& a);
+
+// Largest dynamic shared memory a tiled cycle launch may take, and what one
+// needs (the tail's and the largest tile's, whichever is more).
+constexpr int kTiledSmemMax = 110 * 1024;
+size_t tiled_smem_bytes(const SolveArgs& a);
 
 }  // namespace gs

@@ -75,13 +75,21 @@ private:
     size_t off_ = 0;
 };
 
+// Device memory of the current device, or managed memory.
 bool is_device_pointer(const void* p) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.device == dev;
 }
 
 gs_status static_solve(int32_t side, int32_t variant, uint64_t seed, const double* xi,
@@ -141,6 +149,10 @@ gs_status static_solve(int32_t side, int32_t variant, uint64_t seed, const doubl
         L.u32 = cv.take<float>(L.n);
         L.f32 = cv.take<float>(L.n);
         L.r32 = cv.take<float>(L.n);
+        if (l == 0) {
+            L.w64 = cv.take<double>(L.n);
+            L.w32 = cv.take<float>(L.n);
+        }
         if (l + 1 < g.lv.size()) {
             const size_t sc = (size_t)(L.side - 1) / 2;
             L.P64 = cv.take<double>(8 * (sc + 1) * (sc + 1));
@@ -169,12 +181,13 @@ gs_status static_solve(int32_t side, int32_t variant, uint64_t seed, const doubl
     }
     launch_pack_beta(beta_stage, m1, n, g.beta, g.beta4, st);
     launch_isaacs_assemble(g.Kd, side, g.alpha, g.beta, g.r0, g.code, g.rhs, st);
-    if (w0) GS_CUDA(cudaMemcpyAsync(w, w0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    else GS_CUDA(cudaMemsetAsync(w, 0, n * sizeof(double), st));
+    // w0 == w: the warm start is already in place
+    if (w0 && w0 != w) GS_CUDA(cudaMemcpyAsync(w, w0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else if (!w0) GS_CUDA(cudaMemsetAsync(w, 0, n * sizeof(double), st));
 
     int cycles = 0;
     double res = 0.0;
-    solve_policy_system(&s, g, &cycles, &res);
+    const bool exact = solve_policy_system(&s, g, &cycles, &res);
     GS_CUDA(cudaStreamSynchronize(st));
     if (stats) {
         std::memset(stats, 0, sizeof *stats);
@@ -182,7 +195,11 @@ gs_status static_solve(int32_t side, int32_t variant, uint64_t seed, const doubl
         stats->systems = 1;
         stats->levels = (int)g.lv.size();
         stats->res_inf = res;
-        stats->converged = 1;
+        stats->converged = exact ? 1 : 0;
+    }
+    if (!exact) {
+        set_last_error("static solve: %d cycles reached before the float64 floor", cycles);
+        return GS_ENOTCONV;
     }
     return GS_OK;
 }

@@ -230,6 +230,10 @@ static void alloc_grid(gs_solver* s, Arena& ar, IsaacsGrid& g) {
         L.u32 = ar.alloc<float>(L.n);
         L.f32 = ar.alloc<float>(L.n);
         L.r32 = ar.alloc<float>(L.n);
+        if (l == 0) {
+            L.w64 = ar.alloc<double>(L.n);
+            L.w32 = ar.alloc<float>(L.n);
+        }
         if (l + 1 < g.lv.size()) {
             const size_t sc = (size_t)(L.side - 1) / 2;
             L.P64 = ar.alloc<double>(8 * (sc + 1) * (sc + 1));
@@ -314,9 +318,10 @@ int tail_level(const gs_solver* s, const IsaacsGrid& g) {
 // float64 correction (iterative refinement), until the float64 stopping test.
 // rel_tol > 0 also stops once the residual fell by that factor (an inexact
 // policy evaluation); do_setup = false reuses the hierarchy of the previous
-// call (valid when the policy codes are unchanged).  Returns true when the
-// solve stopped at the float64 floor / tolerance rather than at rel_tol.
-bool linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bool do_setup) {
+// call (valid when the policy codes are unchanged).  Returns why the solve
+// stopped: kLinExact (float64 floor or tolerance), kLinInexact (the residual
+// fell by rel_tol) or kLinCapped (max_cycles reached short of both).
+int linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bool do_setup) {
     const bool mixed = s->opt.precision != GS_PREC_FP64;
     SolveArgs a{};
     a.K = g.Kd;
@@ -360,11 +365,23 @@ bool linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bo
         L.A32 = Lv.A32;
         L.P64 = Lv.P64;
         L.P32 = Lv.P32;
+        L.u2 = mixed ? (void*)Lv.r32 : (void*)Lv.r64;
     }
+    a.v2 = g.lv[0].r64;
+    a.v3 = g.lv[0].w64;
+    a.e2 = g.lv[0].r32;
+    a.r2 = g.lv[0].w32;
+    a.tc0 = 16;
+    a.tcc = mixed ? 16 : 8;
     // levels from smem_from on are staged in block 0's shared memory, as many as fit
     a.smem_from = std::max(a.tail, 1);
     while (a.smem_from < a.nlev && tail_smem_bytes(a) > (size_t)kTailSmemMax)
         ++a.smem_from;
+    // tiled V-cycles where they apply: V-cycles with at least one grid-wide
+    // level, every buffer present, shared memory within the launch's limit
+    a.tiled = s->opt.cycle_kernel == 0 && a.gamma == 1 && a.tail >= 1 && g.lv[0].w64 &&
+              (a.max_blocks == 0 || a.max_blocks >= 2) &&
+              tiled_smem_bytes(a) <= (size_t)kTiledSmemMax;
     GS_CUDA(cudaMemsetAsync(s->mgd, 0, sizeof(MGState), s->st));
     if (do_setup) {
         KScope ks(s, GS_K_MG_SETUP);
@@ -391,7 +408,9 @@ bool linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, bo
     }
     cnt.cycles += s->mgh->out.cycles;
     cnt.last_lin_res = s->mgh->out.res;
-    return s->mgh->out.reason != 2;
+    const int why = s->mgh->out.reason;
+    if (why == kLinCapped) cnt.lin_capped = true;
+    return why;
 }
 
 // The Galerkin hierarchy must be rebuilt unless it was built for (nearly)
@@ -437,12 +456,13 @@ bool amgpi(gs_solver* s, IsaacsGrid& g, double eps, bool beta_given, Counters& c
         };
         for (int j = 0; j < s->opt.max_inner; ++j) {
             // Algorithm 1 step 1: evaluate MIN's policy (inexactly inside the loop)
-            const bool exact = linear_solve(s, g, cnt, s->opt.pi_rtol, need_setup(s, g));
+            const int why = linear_solve(s, g, cnt, s->opt.pi_rtol, need_setup(s, g));
             ++cnt.systems;
+            if (why == kLinCapped) break;   // not evaluated: no decision may rest on it
             if (inner_improve() != 0) continue;
-            if (!exact) {
+            if (why == kLinInexact) {
                 // confirm on the float64-floor solution of the same system before stopping
-                linear_solve(s, g, cnt, 0.0, need_setup(s, g));
+                if (linear_solve(s, g, cnt, 0.0, need_setup(s, g)) == kLinCapped) break;
                 if (inner_improve() != 0) continue;
             }
             break;
@@ -458,6 +478,9 @@ bool amgpi(gs_solver* s, IsaacsGrid& g, double eps, bool beta_given, Counters& c
         g.stale_rows += h.code_changed;
         cnt.res_inf = bits_to_double(h.res);
         cnt.res_l2 = std::sqrt(h.res_sq / (double)g.n);
+        // a policy evaluation stopped at the cycle cap ends the iteration
+        // unconverged: its value is the best iterate, not a fixed point
+        if (cnt.lin_capped) break;
         if (cnt.res_inf <= eps || h.changed == 0) {
             converged = true;
             break;
@@ -481,10 +504,10 @@ void default_policies(gs_solver* s, IsaacsGrid& g) {
 bool solve_policy_system(gs_solver* s, IsaacsGrid& g, int* cycles, double* res) {
     Counters cnt;
     g.hier_valid = false;
-    const bool exact = linear_solve(s, g, cnt, 0.0, true);
+    const int why = linear_solve(s, g, cnt, 0.0, true);
     *cycles = cnt.cycles;
     *res = cnt.last_lin_res;
-    return exact;
+    return why == kLinExact;
 }
 
 gs_status run_solve(gs_solver* s, gs_solve_stats* stats) {
@@ -503,12 +526,20 @@ gs_status run_solve(gs_solver* s, gs_solve_stats* stats) {
         GS_CUDA(cudaMemsetAsync(g0.v, 0, g0.n * sizeof(double), s->st));
         bool beta_given = false;
         converged = false;
+        s->level_stats.clear();
         for (size_t k = 0; k < P.grids.size(); ++k) {
             IsaacsGrid& g = *P.grids[k];
             const bool last = k + 1 == P.grids.size();
             const double h = 1.0 / (g.side + 1);
+            const int outer0 = cnt.outer, systems0 = cnt.systems;
             converged = amgpi(s, g, last ? s->opt.eps : s->opt.fmg_c * h * h, beta_given, cnt);
             ++fmg_levels;
+            s->level_stats.insert(s->level_stats.end(),
+                                  {g.side, cnt.outer - outer0, cnt.systems - systems0});
+            if (cnt.lin_capped) {   // the finer levels are not reached
+                converged = false;
+                break;
+            }
             if (!last) {
                 IsaacsGrid& f = *P.grids[k + 1];
                 launch_fmg_interp(g.side, g.v, g.alpha, g.beta, g.beta4, f.v, f.alpha, f.beta,
@@ -530,6 +561,7 @@ gs_status run_solve(gs_solver* s, gs_solve_stats* stats) {
         }
         if (!s->init_v) GS_CUDA(cudaMemsetAsync(fine.v, 0, fine.n * sizeof(double), s->st));
         converged = amgpi(s, fine, s->opt.eps, s->init_beta, cnt);
+        s->level_stats = {fine.side, cnt.outer, cnt.systems};
     }
     GS_CUDA(cudaEventRecord(e1, s->st));
     sync(s);
@@ -590,6 +622,53 @@ gs_status run_improve(gs_solver* s, const double* v, uint8_t* alpha_out, uint8_t
     return GS_OK;
 }
 
+gs_status run_fmg_interpolate(int side_c, int variant, const double* v_c, const uint8_t* alpha_c,
+                              const uint8_t* beta_c, double* v_f, uint8_t* alpha_f,
+                              uint8_t* beta_f, cudaStream_t st) {
+    const int m1 = variant == 1 ? 5 : 4;
+    const size_t nc = (size_t)side_c * side_c;
+    const int side_f = 2 * side_c + 1;
+    const size_t nf = (size_t)side_f * side_f;
+    Arena ar(0, 0, st);
+    double* vc = ar.alloc<double>(nc);
+    uint8_t* ac = ar.alloc<uint8_t>(nc);
+    uint8_t* bstage_c = ar.alloc<uint8_t>(nc * m1);
+    uint32_t* bc = ar.alloc<uint32_t>(nc);
+    uint8_t* b4c = ar.alloc<uint8_t>(nc);
+    double* vf = ar.alloc<double>(nf);
+    uint8_t* af = ar.alloc<uint8_t>(nf);
+    uint32_t* bf = ar.alloc<uint32_t>(nf);
+    uint8_t* b4f = ar.alloc<uint8_t>(nf);
+    uint8_t* bstage_f = ar.alloc<uint8_t>(nf * m1);
+    int* bad = ar.alloc<int>(2);
+    GS_CUDA(cudaMemcpyAsync(vc, v_c, nc * sizeof(double), cudaMemcpyDefault, st));
+    GS_CUDA(cudaMemcpyAsync(ac, alpha_c, nc, cudaMemcpyDefault, st));
+    GS_CUDA(cudaMemcpyAsync(bstage_c, beta_c, nc * m1, cudaMemcpyDefault, st));
+    GS_CUDA(cudaMemsetAsync(bad, 0, 2 * sizeof(int), st));
+    GS_CUDA(cudaMemsetAsync(b4c, 0, nc, st));
+    k_check_actions<<<div_up(nc, 256), 256, 0, st>>>(ac, nc, m1, bad);
+    k_check_actions<<<div_up(nc * m1, 256), 256, 0, st>>>(bstage_c, nc * m1, 4, bad + 1);
+    GS_CHECK_LAUNCH_N(2);
+    int hbad[2];
+    GS_CUDA(cudaMemcpyAsync(hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (hbad[0] || hbad[1]) {
+        set_last_error("fmg_interpolate: action out of range");
+        return GS_EINVAL;
+    }
+    k_pack_beta<<<div_up(nc, 256), 256, 0, st>>>(bstage_c, m1, nc, bc, b4c);
+    GS_CHECK_LAUNCH();
+    launch_fmg_interp(side_c, vc, ac, bc, m1 == 5 ? b4c : nullptr, vf, af, bf,
+                      m1 == 5 ? b4f : nullptr, st);
+    k_unpack_beta<<<div_up(nf, 256), 256, 0, st>>>(bf, b4f, m1, nf, bstage_f);
+    GS_CHECK_LAUNCH();
+    if (v_f) GS_CUDA(cudaMemcpyAsync(v_f, vf, nf * sizeof(double), cudaMemcpyDefault, st));
+    if (alpha_f) GS_CUDA(cudaMemcpyAsync(alpha_f, af, nf, cudaMemcpyDefault, st));
+    if (beta_f) GS_CUDA(cudaMemcpyAsync(beta_f, bstage_f, nf * m1, cudaMemcpyDefault, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    return GS_OK;
+}
+
 gs_status run_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* beta,
                            const double* w0, double* w_out, gs_solve_stats* stats) {
     Problem& P = *s->prob;
@@ -621,7 +700,7 @@ gs_status run_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* be
     launch_isaacs_assemble(g.Kd, g.side, g.alpha, g.beta, g.r0, g.code, g.rhs, s->st);
     Counters cnt;
     g.hier_valid = false;
-    linear_solve(s, g, cnt, 0.0, true);
+    const int why = linear_solve(s, g, cnt, 0.0, true);
     GS_CUDA(cudaMemcpyAsync(w_out, g.v, g.n * sizeof(double), cudaMemcpyDefault, s->st));
     sync(s);
     if (stats) {
@@ -630,6 +709,11 @@ gs_status run_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* be
         stats->systems = 1;
         stats->levels = (int)g.lv.size();
         stats->res_inf = cnt.last_lin_res;
+        stats->converged = why == kLinExact ? 1 : 0;
+    }
+    if (why != kLinExact) {
+        set_last_error("policy_solve: %d cycles reached before the float64 floor", cnt.cycles);
+        return GS_ENOTCONV;
     }
     return GS_OK;
 }

@@ -45,6 +45,8 @@ struct Level {
     float* P32 = nullptr;
     double *u64 = nullptr, *f64 = nullptr, *r64 = nullptr;
     float *u32 = nullptr, *f32 = nullptr, *r32 = nullptr;
+    double* w64 = nullptr;     // level 0: third value buffer of the tiled cycles (float64 path)
+    float* w32 = nullptr;      // level 0: second right-hand side of the tiled cycles (mixed path)
 };
 
 // An Isaacs grid with its policies, value and multigrid hierarchy.
@@ -118,8 +120,12 @@ struct Counters {
     int outer = 0, systems = 0, cycles = 0;
     double res_inf = 0, res_l2 = 0;
     bool converged = false;
+    bool lin_capped = false;   // a linear solve stopped at max_cycles
     double last_lin_res = 0;
 };
+
+// Why a multigrid linear solve stopped (SolveOut::reason).
+enum { kLinExact = 1, kLinInexact = 2, kLinCapped = 3 };
 
 }  // namespace gs
 
@@ -151,6 +157,7 @@ struct gs_solver {
     std::unique_ptr<gs::Problem> prob;
     bool init_v = false, init_alpha = false, init_beta = false;
     int last_levels = 0;
+    std::vector<int> level_stats;      // per FAMGpi level of the last solve: side, outer, systems
 };
 
 namespace gs {
@@ -171,10 +178,14 @@ gs_status run_line(gs_solver* s, gs_solve_stats* stats);
 gs_status run_solve(gs_solver* s, gs_solve_stats* stats);
 gs_status run_improve(gs_solver* s, const double* v, uint8_t* alpha_out, uint8_t* beta_out,
                       double* fv_out);
+gs_status run_fmg_interpolate(int side_c, int variant, const double* v_c, const uint8_t* alpha_c,
+                              const uint8_t* beta_c, double* v_f, uint8_t* alpha_f,
+                              uint8_t* beta_f, cudaStream_t st);
 gs_status run_policy_solve(gs_solver* s, const uint8_t* alpha, const uint8_t* beta,
                            const double* w0, double* w_out, gs_solve_stats* stats);
 // Multigrid solve of the assembled policy-fixed system of g to the float64
 // floor (fresh hierarchy); g.v holds the initial guess and receives w.
+// Returns false when max_cycles was reached before the floor.
 bool solve_policy_system(gs_solver* s, IsaacsGrid& g, int* cycles, double* res);
 void launch_pack_beta(const uint8_t* src, int m1, size_t n, uint32_t* beta, uint8_t* beta4,
                       cudaStream_t st);

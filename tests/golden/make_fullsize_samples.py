@@ -6,11 +6,13 @@ takes minutes to an hour per workload, too long to run beside the GPU.
 Calls only oracle/ (and the seeded input generators of synth/).
 
     python tests/golden/make_fullsize_samples.py isaacs2047_seed3   # ~16 min, ~12 GB
+    python tests/golden/make_fullsize_samples.py isaacs1023_seed2   # ~3 min
     python tests/golden/make_fullsize_samples.py obstacle1023
     python tests/golden/make_fullsize_samples.py batch4096
 
-* isaacs2047_seed2, isaacs2047_seed3: Algorithm 2 with Algorithm 1 inside
-  (sparse LU) on the plain 2047 x 2047 Isaacs game, from the default start.
+* isaacs2047_seed2, isaacs2047_seed3, isaacs1023_seed2: Algorithm 2 with
+  Algorithm 1 inside (sparse LU) on the plain 2047 x 2047 (1023 x 1023) Isaacs
+  game, from the default start.
 * obstacle1023: the obstacle variant at 1023 x 1023, seed 2.  The oracle runs
   its own FAMGpi (Algorithm 4, from 31 x 31, eps_l = 0.01 h_l^2) with eps = 0
   on the finest level, so the last policy iteration runs until MAX's policy
@@ -68,18 +70,22 @@ def write(name, header, body):
         fh.writelines(body)
 
 
-def isaacs2047(seed: int):
+def isaacs_plain(side: int, seed: int):
     t0 = time.time()
-    res = oracle.policy_iteration(isaacs_game(2047, 0, seed=seed))
-    idx = sample_states(res.v.size, SAMPLES, 2047)
-    write(f"isaacs2047_plain_seed{seed}_samples.txt",
+    res = oracle.policy_iteration(isaacs_game(side, 0, seed=seed))
+    idx = sample_states(res.v.size, SAMPLES, side)
+    write(f"isaacs{side}_plain_seed{seed}_samples.txt",
           ["FP64 oracle, Algorithm 2 with Algorithm 1 inside (sparse LU), plain Isaacs game",
-           f"2047 x 2047, seed {seed}; written by make_fullsize_samples.py isaacs2047_seed{seed}",
+           f"{side} x {side}, seed {seed}; written by make_fullsize_samples.py isaacs{side}_seed{seed}",
            "columns: state v alpha beta(x,0..m1-1) gap_max gap_min(x,0..m1-1)",
            f"outer {res.outer} systems {res.systems} residual {res.residual:.3e}"],
           [f"vmax {np.max(np.abs(res.v)):.17e}\n"] + rows(res, idx))
-    print(f"isaacs2047 seed {seed}: outer {res.outer} systems {res.systems} residual {res.residual:.2e} "
-          f"in {time.time() - t0:.0f} s")
+    print(f"isaacs{side} seed {seed}: outer {res.outer} systems {res.systems} "
+          f"residual {res.residual:.2e} in {time.time() - t0:.0f} s")
+
+
+def isaacs2047(seed: int):
+    isaacs_plain(2047, seed)
 
 
 def obstacle1023():
@@ -126,6 +132,7 @@ def batch4096():
 
 if __name__ == "__main__":
     jobs = {"isaacs2047_seed2": lambda: isaacs2047(2), "isaacs2047_seed3": lambda: isaacs2047(3),
+            "isaacs1023_seed2": lambda: isaacs_plain(1023, 2),
             "obstacle1023": obstacle1023, "batch4096": batch4096}
     for name in sys.argv[1:] or list(jobs):
         jobs[name]()

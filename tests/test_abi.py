@@ -38,6 +38,7 @@ def test_struct_layouts_match_header(gs):
     assert gs.gs_options.cycle_gamma.offset == 116
     assert gs.gs_options.nu1_coarse.offset == 120 and gs.gs_options.nu2_coarse.offset == 124
     assert gs.gs_options.game_threads.offset == 128
+    assert gs.gs_options.cycle_kernel.offset == 132
     assert gs.gs_options.pi_rtol.offset == 96
     assert ctypes.sizeof(gs.gs_solve_stats) == 48
 
@@ -51,8 +52,18 @@ def test_host_side_checks_without_gpu(gs):
     assert gs.lib.gamesolve_create(None, None) == gs.GS_EINVAL
     h = ctypes.c_void_p()
     for kw in ({"coarse_max": 0}, {"nu1_coarse": -2}, {"nu1_coarse": 0, "nu2_coarse": 0},
-               {"game_threads": 384}):
+               {"game_threads": 384}, {"cycle_kernel": 2}):
         bad = gs.default_options(**kw)
         assert gs.lib.gamesolve_create(ctypes.byref(h), ctypes.byref(bad)) == gs.GS_EINVAL, kw
     assert gs.lib.gamesolve_solve(None, None) == gs.GS_EINVAL
     gs.lib.gamesolve_destroy(None)
+
+
+def test_barrier_selftest_rejects_bad_arguments_without_gpu(gs):
+    # checked before any CUDA call: no blocks, a limit outside 1 us .. 100 ms,
+    # an absent block outside the launch
+    f = gs.lib.gamesolve_selftest_barrier
+    assert f(0, -1, 10**6, 1, None, None) == gs.GS_EINVAL
+    assert f(4, -1, 10, 1, None, None) == gs.GS_EINVAL
+    assert f(4, -1, 10**9, 1, None, None) == gs.GS_EINVAL
+    assert f(4, 4, 10**6, 1, None, None) == gs.GS_EINVAL

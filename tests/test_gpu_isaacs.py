@@ -248,3 +248,42 @@ def test_wcycle_needs_no_more_cycles_than_vcycle(gs, prec, tail_side):
     assert stw["cycles"] <= stv["cycles"], (stv, stw)
     assert stw["res_inf"] < 1e-14
     assert rel_err(ww, wv) <= 1e-12
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("side_c", [1, 7, 31, 63])
+def test_fmg_interpolation_matches_oracle(gs, side_c, variant):
+    """FAMGpi's interpolations I (value) and U (strategies) of Sec. 5.2, run
+    by the CUDA kernel the solver uses, against the oracle's: policies bit for
+    bit, values to 1e-15 (a mean of 2 or 4 numbers, summed in another order)."""
+    rng = np.random.default_rng(100 * side_c + variant)
+    n, m1 = side_c * side_c, 5 if variant else 4
+    v = rng.standard_normal(n)
+    alpha = rng.integers(0, m1, n).astype(np.uint8)
+    beta = rng.integers(0, 4, (n, m1)).astype(np.uint8)
+    vf, af, bf = gs.fmg_interpolate(side_c, variant, v, alpha, beta)
+    v_ref = interp_value(v, side_c)
+    assert np.max(np.abs(vf - v_ref)) <= 1e-15 * np.max(np.abs(v_ref))
+    assert np.array_equal(af, interp_policy(alpha, side_c))
+    assert np.array_equal(bf, interp_policy(beta, side_c))
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fmg_level_counts_match_oracle(gs, variant):
+    """FAMGpi from side 15 to 127 (Algorithm 4), every policy evaluation to the
+    float64 floor (pi_rtol = 0): per level, the MAX iterations and the linear
+    systems solved are the oracle's, so the GPU follows the same path of
+    policies on every level, not only to the same fixed point."""
+    side, seed = 127, 3
+    c = 0.1 if variant == 0 else 0.01
+    xi = synth.isaacs_noise(side, seed)
+    _, per_level = famg_pi(side, 15, variant, xi, c=c, eps=0.0)
+    want = [(s, r.outer, r.systems) for s, r in zip((15, 31, 63, 127), per_level)]
+    for prec in ("fp64", "mixed"):
+        with gs.GameSolver(precision=prec, fmg=1, fmg_side=15, fmg_c=c, pi_rtol=0.0,
+                           setup_reuse=0.0) as s:
+            s.set_isaacs_grid(side, variant, seed)
+            st = s.solve()
+            got = s.level_stats()
+        assert st["converged"] == 1
+        assert got == want, (prec, got, want)

@@ -3,23 +3,63 @@
 Each result must be the same alone and in the mix: Isaacs values bit for bit
 (their kernels' arithmetic does not depend on what else runs), finite games to
 1e-12 relative (a grid-wide game's reductions may use a different number of
-blocks when the server caps its share of the GPU).
+blocks when the server caps its share of the GPU).  Every result is also
+checked against the FP64 oracle: the small mix against full oracle solves,
+the full-size requests against stored oracle runs at sampled states
+(1023 x 1023 plain and obstacle) or, where no oracle run fits the test's
+time, against the oracle's Shapley operator applied to the served value.
 """
+import os
+
 import numpy as np
 import pytest
 
+import oracle
 import synth
+from oracle.fmg import famg_pi
+from oracle.game import game_from_csr
+from oracle.isaacs import isaacs_game, default_alpha0
 
 pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-9          # value bar of the mixed path, relative to max |v*|
+SURE = 1e-8               # policies compared where the oracle's gap exceeds this
 
 
 def mix():
     reqs = []
-    for k, side in enumerate((15, 63, 127, 255, 31, 63, 127)):
-        reqs.append(("isaacs", side, k % 2, 100 + k))
+    for k, (side, variant) in enumerate(((15, 0), (63, 1), (127, 0), (255, 0), (31, 1), (63, 0),
+                                         (127, 1))):
+        reqs.append(("isaacs", side, variant, 100 + k))
     for k, n in enumerate((300, 1500, 5000, 9000)):
         reqs.append(("game", n, synth.random_game(n, 500 + k)))
     return reqs
+
+
+def oracle_result(r):
+    """The oracle's solution of a request: policy iteration (obstacle grids via
+    the oracle's own FAMGpi, which reaches the same unique fixed point in
+    fewer steps; games above 2000 states with the fixed-point evaluation)."""
+    if r[0] == "isaacs":
+        side, variant, seed = r[1], r[2], r[3]
+        if variant == 1 and side >= 31:
+            res, _ = famg_pi(side, 15, 1, synth.isaacs_noise(side, seed), c=0.01, eps=0.0)
+            return res
+        return oracle.policy_iteration(isaacs_game(side, variant, seed=seed),
+                                       alpha0=default_alpha0(side, variant))
+    n, (rp, col, prob, rew, mu) = r[1], r[2]
+    game = game_from_csr(n, 4, 4, rp, col, prob, rew, mu)
+    return oracle.policy_iteration(game, solver="auto" if n <= 2000 else "fixed_point")
+
+
+def check_against_oracle(v, a, b, ref, tag):
+    scale = np.max(np.abs(ref.v))
+    assert np.max(np.abs(v - ref.v)) <= TOL_MIXED * scale, tag
+    sure_a = ref.gap_max > SURE
+    assert np.array_equal(a[sure_a], ref.alpha[sure_a]), tag
+    m = min(b.shape[1], ref.beta.shape[1], 4)
+    sure_b = ref.gap_min[:, :m] > SURE
+    assert np.array_equal(b[:, :m][sure_b], ref.beta[:, :m][sure_b]), tag
 
 
 def alone(gs, r):
@@ -58,6 +98,7 @@ def test_results_alone_equal_in_the_mix(gs):
             assert np.array_equal(a, a0) and np.array_equal(b, b0)
         else:
             assert np.max(np.abs(v - v0)) <= 1e-12 * np.max(np.abs(v0)), i
+        check_against_oracle(v, a, b, oracle_result(r), (i, r[:2]))
         for j, other in enumerate(infos):
             if j != i and other["t_start"] < info["t_end"] and info["t_start"] < other["t_end"]:
                 overlap += 1
@@ -69,14 +110,13 @@ def test_full_size_requests_alone_equal_in_the_mix(gs):
     (plain and obstacle) and the largest and smallest games of its pool
     (937,562 and 63,437 states, tables borrowed from device memory as the
     benchmark serves them), four slots."""
-    import os
 
     import torch
     games = []
     for n, seed in ((937_562, 5007), (63_437, 5000)):
         rp, col, prob, rew, mu = synth.random_game_parallel(n, seed, workers=os.cpu_count() or 1)
         games.append((n, (rp, col, prob, rew, mu)))
-    reqs = [("isaacs", 1023, 0, 5), ("isaacs", 1023, 1, 6), ("isaacs", 511, 0, 7),
+    reqs = [("isaacs", 1023, 0, 2), ("isaacs", 1023, 1, 2), ("isaacs", 511, 0, 7),
             ("isaacs", 63, 0, 8)] + [("game", n, t) for n, t in games]
     ref = [alone(gs, r) for r in reqs]
     dev = {n: tuple(torch.from_numpy(x).cuda() for x in t[:4]) + (t[4],) for n, t in games}
@@ -99,6 +139,25 @@ def test_full_size_requests_alone_equal_in_the_mix(gs):
             assert np.array_equal(a, a0) and np.array_equal(b, b0), i
         else:
             assert np.max(np.abs(v - v0)) <= 1e-12 * np.max(np.abs(v0)), i
+    # against the oracle: stored runs at sampled states for the 1023 x 1023
+    # grids (seed 2), the oracle's Shapley operator elsewhere
+    from test_gpu_fullsize_samples import load_grid_samples, check_sample
+    for i, name in ((0, "isaacs1023_plain_seed2_samples.txt"),
+                    (1, "isaacs1023_obstacle_seed2_samples.txt")):
+        vmax, sample = load_grid_samples(name)
+        v, a, b = out[i]
+        check_sample(v, a, b, vmax, sample, TOL_MIXED)
+    for i in (2, 3):
+        side, variant, seed = reqs[i][1:]
+        v = out[i][0]
+        q = oracle.shapley_q(isaacs_game(side, variant, seed=seed), v)
+        assert np.max(np.abs(q.min(axis=2).max(axis=1) - v)) <= 1e-12, i
+    n, (rp, col, prob, rew, mu) = games[1]
+    v = out[5][0]
+    q = oracle.shapley_q(game_from_csr(n, 4, 4, rp, col, prob, rew, mu), v)
+    res = np.max(np.abs(q.min(axis=2).max(axis=1) - v))
+    # a-posteriori bound of the mu-contraction: |v - v*| <= res / (1 - mu)
+    assert res / (1 - mu) <= TOL_MIXED * np.max(np.abs(v)), res
 
 
 def test_memory_budget_serialises(gs):

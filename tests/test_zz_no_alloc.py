@@ -30,7 +30,7 @@ def _static_solve(gs, torch, side, variant, seed, alpha_d, beta_d, w_d, precisio
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_bf16"])
-@pytest.mark.parametrize("side,variant", [(127, 0), (63, 1)])
+@pytest.mark.parametrize("side,variant", [(127, 0), (63, 1), (127, 1)])
 def test_static_solve_matches_allocating_solve(gs, side, variant, precision):
     import torch
     rng = np.random.default_rng(side + variant)
@@ -71,3 +71,34 @@ def test_static_solve_rejects_oversize_and_host_memory(gs):
         side, 0, 1, None, a_h.ctypes.data, b_d.data_ptr(), None, w_d.data_ptr(), 0, None,
         ctypes.byref(st))
     assert code == gs.GS_EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("side,variant", [(15, 0), (31, 1)])
+def test_static_solve_matches_oracle_and_allocates_nothing(gs, side, variant, precision):
+    """Against the oracle's direct solve of the same policy-fixed system
+    (Eq. (LSPI)), and with the device's free memory unchanged across the
+    call: the entry point takes its scratch from the static array only."""
+    import torch
+    import oracle
+    from oracle.isaacs import isaacs_game
+    rng = np.random.default_rng(side)
+    n, m1 = side * side, 5 if variant else 4
+    seed = 4
+    alpha = rng.integers(0, m1, size=n).astype(np.uint8)
+    beta = rng.integers(0, 4, size=(n, m1)).astype(np.uint8)
+    A, r = oracle.policy_system(isaacs_game(side, variant, seed=seed), alpha, beta)
+    w_ref = oracle.solve_policy_system(A, r, "dense")
+    alpha_d = torch.from_numpy(alpha).cuda()
+    beta_d = torch.from_numpy(beta).cuda()
+    w_d = torch.zeros(n, dtype=torch.float64, device="cuda")
+    code, _ = _static_solve(gs, torch, side, variant, seed, alpha_d, beta_d, w_d, precision)
+    assert code == gs.GS_OK
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        code, st = _static_solve(gs, torch, side, variant, seed, alpha_d, beta_d, w_d, precision)
+        assert code == gs.GS_OK and st.converged == 1
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    w = w_d.cpu().numpy()
+    assert np.max(np.abs(w - w_ref)) <= 1e-10 * np.max(np.abs(w_ref))
