@@ -37,6 +37,8 @@ DTYPES = {"fp64": "f64", "mixed": "f32+f64", "mixed_bf16": "bf16(weights)+f32+f6
 # would set it; the library's default stays V(1,1)).
 ISAACS_CYCLE = {"nu1": 1, "nu2": 2}
 SIDE = 1023          # the metric's workload; --side changes it (e.g. 2047 for profiling)
+# the V-cycle kernel the library's default options launch (tiled grid-wide levels)
+CYCLE_KERNEL = "k_mg_cycles_tiled"
 SEED = 2
 
 def cycle_sweeps(cycle: dict):
@@ -98,7 +100,7 @@ def mg_cycle_bytes(n: int, prec: str, launches: int, cycles: int, sweeps: int = 
 # DRAM bytes per k_mg_cycles launch from the committed capture of the current
 # kernel (profiles/k_mg_cycles_isaacs1023_mixed.md): read + write, with ncu's
 # cache flush before the launch.  Keyed by (side, precision).
-PROFILED_TRAFFIC = {(1023, "mixed"): 45.91e6 + 0.95e6}
+PROFILED_TRAFFIC = {}
 
 
 def load_peaks():
@@ -227,40 +229,107 @@ def oracle_batch_sample(sizes, seed: int, games: int = 48, workers: int = 0):
 
 # Policy iterations the FP64 oracle needs for this workload (1023^2, seed 2),
 # counted by a full oracle run (tests/golden/oracle_counts_1023.txt).
-def oracle_counts():
+def _oracle_counts_file():
     path = os.path.join(ROOT, "tests", "golden", "oracle_counts_1023.txt")
     d = {}
     with open(path) as fh:
         for ln in fh:
             if ln.strip() and not ln.startswith("#"):
                 k, v = ln.split()
-                d[k] = int(v)
-    return d["systems"], d["outer"]
+                d[k] = float(v)
+    return d
+
+
+def oracle_counts():
+    d = _oracle_counts_file()
+    return int(d["systems"]), int(d["outer"])
+
+
+def oracle_full_solve_seconds():
+    """Wall time of the full oracle solve recorded with the counts (or None)."""
+    return _oracle_counts_file().get("seconds")
+
+
+def load_samples(name):
+    """(vmax, state indices, values) of a stored oracle run at sampled states."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", name)
+    vmax, idx, vals = None, [], []
+    with open(path) as fh:
+        for ln in fh:
+            if ln.startswith("#"):
+                continue
+            if ln.startswith("vmax"):
+                vmax = float(ln.split()[1])
+                continue
+            t = ln.split()
+            idx.append(int(t[0]))
+            vals.append(float(t[1]))
+    return vmax, np.array(idx, np.int64), np.array(vals)
+
+
+def err_vs_samples(v, samples):
+    """max over the sampled states of |v - v_oracle| / max |v_oracle|."""
+    import numpy as np
+    vmax, idx, vals = samples
+    return float(np.max(np.abs(v[idx] - vals)) / vmax)
+
+
+def measure_l2_copy_gbs(device="cuda"):
+    """Copy bandwidth of a buffer pair that stays in the 129 MB L2 (2 x 24 MiB),
+    best of 20 timed repetitions of 20 copies (read + write bytes)."""
+    import torch
+    a = torch.empty(24 << 20, dtype=torch.uint8, device=device)
+    b = torch.empty_like(a)
+    a.fill_(1)
+    best = 0.0
+    for _ in range(20):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(20):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 20 * 2 * a.numel() / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
 
 
 def run_reference(args):
+    """The FP64 oracle on the host.  One step is one unit of the oracle's own
+    policy iteration at 1023^2: a sparse-LU policy evaluation followed by an
+    improvement sweep (both timed).  A whole oracle solve of this workload is
+    `systems` evaluations and `systems + outer` improvements (counted by a full
+    oracle run, tests/golden/oracle_counts_1023.txt), so
+    value = 1 / (systems * t_eval + (systems + outer) * t_improve), while
+    ms_per_step is the measured time of one step."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
     systems, outer = oracle_counts()
-    times = []
+    t_evals, t_imps = [], []
     for k in range(args.warmup + args.steps):
-        t_solve, _, _ = oracle_sample(systems, outer)
+        _, t_eval, t_imp = oracle_sample(systems, outer)
         if k >= args.warmup:
-            times.append(t_solve)
-    sec = statistics.mean(times)
-    value = 1.0 / sec
+            t_evals.append(t_eval)
+            t_imps.append(t_imp)
+    t_eval, t_imp = statistics.mean(t_evals), statistics.mean(t_imps)
+    value = 1.0 / (systems * t_eval + (systems + outer) * t_imp)
+    full = oracle_full_solve_seconds()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": (t_eval + t_imp) * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"isaacs_{SIDE}x{SIDE}_plain_amgpi", "side": SIDE, "seed": SEED,
                    "variant": "plain", "solver": "oracle PI + SuperLU", "parallelism": "none"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: one sparse-LU policy evaluation + one improvement at "
-                                   f"{SIDE}^2, scaled by the oracle's {systems} systems / {outer} "
-                                   f"outer iterations per solve"},
+                         "sample": f"per step: one sparse-LU policy evaluation ({t_eval:.2f} s) + one "
+                                   f"improvement ({t_imp:.2f} s) of the oracle at {SIDE}^2; a solve is "
+                                   f"{systems} evaluations + {systems + outer} improvements"
+                                   + (f"; a full oracle solve measured {full:.0f} s on the build host"
+                                      if full else "")},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -524,6 +593,10 @@ def run_ours(args):
     for k, v in values.items():
         if k != "fp64":
             compare["rel_diff_" + k + "_vs_fp64"] = float(np.max(np.abs(v - v64)) / np.max(np.abs(v64)))
+    # every result against the FP64 oracle: its stored run at 1,026 sampled states
+    if (SIDE, SEED) == (1023, 2):
+        samples = load_samples("isaacs1023_plain_seed2_samples.txt")
+        compare["err_vs_oracle_sampled"] = {k: err_vs_samples(v, samples) for k, v in values.items()}
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
@@ -556,7 +629,7 @@ def run_ours(args):
         bpl = total / tr_n
         avg_s = tr_ms * 1e-3 / tr_n
         ach = bpl / avg_s / 1e9
-        line["roofline"] = {"kernel": "k_mg_cycles", "bound": "hbm", "achieved": ach,
+        line["roofline"] = {"kernel": CYCLE_KERNEL, "bound": "hbm", "achieved": ach,
                             "peak": peak, "unit": "GB/s", "frac": ach / peak,
                             "peak_source": peak_kind,
                             "traffic": PROFILED_TRAFFIC.get((SIDE, prec)),
@@ -567,6 +640,18 @@ def run_ours(args):
                                     + json.dumps({k: round(v, 1) for k, v in
                                                   mg_bytes_per_state(kind, sweeps,
                                                                      sweeps_c).items()})}
+
+    # roofline of the same launches against the L2 (the 1023^2 working set stays in it)
+    if "roofline" in line and SIDE <= 1023:
+        l2 = measure_l2_copy_gbs()
+        r = line["roofline"]
+        line["roofline_l2"] = {"kernel": r["kernel"], "achieved": r["achieved"], "peak": l2,
+                               "unit": "GB/s", "frac": r["achieved"] / l2,
+                               "peak_source": "measured in this run: L2-resident 24 MiB copy"}
+
+    # the precision workload: 2047^2, seed 3, every precision, against the oracle
+    if not args.no_2047 and SIDE == 1023 and world == 1:
+        line["side_2047"] = run_2047(args, stream, peak, peak_kind)
 
     # end to end through the C-ABI with host buffers
     if not args.no_e2e:
@@ -605,6 +690,57 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def run_2047(args, stream, peak, peak_kind):
+    """The precision configuration: 2047 x 2047 plain Isaacs game, seed 3,
+    flat AMGpi to the float64 floor, each precision timed over a few solves
+    (L2 flushed between them), the V-cycle kernel's HBM roofline, and every
+    result's error against the stored FP64 oracle run (sampled states)."""
+    import numpy as np
+    import torch
+    import paper_1107_1653_gb300 as gs
+    side, seed, n = 2047, 3, 2047 * 2047
+    samples = load_samples("isaacs2047_plain_seed3_samples.txt")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out, values = {}, {}
+    for prec in ("mixed", "fp64", "mixed_bf16"):
+        s = gs.GameSolver(precision=prec, stream=stream, **ISAACS_CYCLE)
+        s.set_isaacs_grid(side, 0, seed)
+        s.solve()
+        s.trace("mg_cycles")
+        ts = []
+        st = None
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = s.solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        tr_ms, tr_n = s.trace_read()
+        values[prec] = s.get_value()
+        s.close()
+        ms = statistics.mean(ts)
+        sweeps, sweeps_c = cycle_sweeps(ISAACS_CYCLE)
+        total = mg_cycle_bytes(n, prec, tr_n, st["cycles"] * 3, sweeps, sweeps_c)
+        ach = total / tr_n / (tr_ms * 1e-3 / tr_n) / 1e9
+        out[prec] = {"solves_per_s": 1000.0 / ms, "ms_per_solve": ms, "outer": st["outer"],
+                     "systems": st["systems"], "cycles": st["cycles"],
+                     "err_vs_oracle_sampled": err_vs_samples(values[prec], samples),
+                     "roofline": {"kernel": CYCLE_KERNEL, "bound": "hbm", "achieved": ach,
+                                  "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                  "peak_source": peak_kind, "avg_us": tr_ms * 1e3 / tr_n}}
+    v64 = values["fp64"]
+    for k in ("mixed", "mixed_bf16"):
+        out[k]["rel_diff_vs_fp64"] = float(np.max(np.abs(values[k] - v64)) / np.max(np.abs(v64)))
+    out["config"] = {"side": side, "states": n, "seed": seed, "cycle": cycle_label(ISAACS_CYCLE),
+                     "l2": "flushed between solves (256 MiB write)",
+                     "oracle": "isaacs2047_plain_seed3_samples.txt (1,026 states)"}
+    return out
 
 
 def run_line(args):
@@ -671,6 +807,8 @@ def main():
     ap.add_argument("--trace-kernel", default="mg_cycles", choices=["mg_cycles", "none"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-2047", action="store_true",
+                    help="skip the 2047^2 precision configuration's block")
     ap.add_argument("--side", type=int, default=SIDE)
     ap.add_argument("--workload", default="isaacs", choices=["isaacs", "batch", "serving", "line"],
                     help="isaacs: the metric's 1023^2 solve (default); batch: 4096 random "

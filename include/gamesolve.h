@@ -102,12 +102,26 @@ typedef struct {
                               (default): 512, autotuned for batches of >= 1024 games (the
                               first solve times both on a sample; the choice is kept for the
                               process per precision, largest game, actions and row length) */
-    int32_t cycle_kernel;  /* Isaacs grids' V-cycles: 0 tiled where they apply (each
+    int32_t cycle_kernel;  /* Isaacs grids' V-cycles: 0 (default) tiled where they apply (each
                               thread block runs a whole smoothing leg of a tile of a level in
                               shared memory, with a halo recomputed by its neighbours: about
                               two grid-wide barriers per level and cycle); 1 one grid-wide
-                              phase per relaxation colour (default).  Same arithmetic per point.
+                              phase per relaxation colour.  Same arithmetic per point.
                               W-cycles always take the latter. */
+    int32_t game_solver;   /* policy evaluation of a single finite game (gamesolve_set_game):
+                              0 (default) relaxation plus the constant-vector coarse
+                              correction (fits random, expander-like games); 1 algebraic
+                              multigrid built for every policy-fixed system: strength of
+                              connection, C/F splitting, extended+i interpolation, Galerkin
+                              coarse operators, V-cycles with C/F Gauss-Seidel (Sec. 4.3; for
+                              structured games such as a grid or a chain given as tables).
+                              With options.fmg: full multilevel policy iteration on coarse
+                              games made by aggregation (Algorithm 4 without a PDE) */
+    int32_t amg_coarsening;/* game_solver 1: 0 (default) PMIS independent-set splitting; 1 PMIS
+                              followed by the Ruge-Stueben second pass (strong F-F couplings
+                              without a common C point promote a point to C); interpolation
+                              is extended+i (distance two) with either */
+    double  amg_theta;     /* game_solver 1: strength threshold theta (0 = default 0.25) */
 } gs_options;
 
 /* Statistics of the last gamesolve_solve (the columns of the paper's tables, Sec. 6). */
@@ -128,7 +142,8 @@ typedef struct {
  * fmg_c 0.1, literal mu, tail_side 31, no memory budget, default stream,
  * pi_rtol 1e-2, setup_reuse 1e-2, grid_blocks 0, cycle_gamma 1, nu1_coarse and
  * nu2_coarse -1 (as on the finest level), game_threads 0 (autotuned),
- * cycle_kernel 1 (one phase per colour). */
+ * cycle_kernel 0 (tiled), game_solver 0, amg_coarsening 0,
+ * amg_theta 0 (0.25). */
 void gamesolve_default_options(gs_options* opt);
 
 /* Creates a solver on the current CUDA device.  opt may be NULL (defaults).
@@ -147,7 +162,12 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt);
  * and policy_solve are for Isaacs grids.
  * Errors (GS_EINVAL, solver unchanged): n < 1 or too large, m1 or m2 outside
  * [1, 8], row_ptr not non-decreasing from 0, a column out of range, a
- * probability outside [0, 1], a row sum above 1 + 1e-12, mu outside (0, 1). */
+ * probability outside [0, 1], a row sum above 1 + 1e-12, mu outside (0, 1).
+ * mu = 1 (undiscounted, as the stopping games of Sec. 6.2-6.3) is accepted
+ * with options.game_solver = 1; every pair of policies must then make the
+ * chain leave the state space with probability one (stop rows or
+ * substochastic rows reached), else its system is singular and the solve
+ * fails. */
 gs_status gamesolve_set_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2,
                              const int64_t* row_ptr, const int32_t* col,
                              const double* prob, const double* reward, double mu);

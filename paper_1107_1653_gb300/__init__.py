@@ -41,6 +41,8 @@ class gs_options(ctypes.Structure):
         ("nu1_coarse", ctypes.c_int32), ("nu2_coarse", ctypes.c_int32),
         ("game_threads", ctypes.c_int32),
         ("cycle_kernel", ctypes.c_int32),
+        ("game_solver", ctypes.c_int32), ("amg_coarsening", ctypes.c_int32),
+        ("amg_theta", ctypes.c_double),
     ]
 
 

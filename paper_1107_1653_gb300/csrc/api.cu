@@ -80,7 +80,10 @@ void gamesolve_default_options(gs_options* o) {
     o->nu1_coarse = -1;
     o->nu2_coarse = -1;
     o->game_threads = 0;
-    o->cycle_kernel = 1;
+    o->cycle_kernel = 0;
+    o->game_solver = 0;
+    o->amg_coarsening = 0;
+    o->amg_theta = 0.0;
 }
 
 gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
@@ -100,7 +103,8 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
         o.grid_blocks < 0 || o.cycle_gamma < 0 || o.cycle_gamma > 2 || o.nu1_coarse < -1 ||
         o.nu2_coarse < -1 ||
         (o.game_threads != 0 && o.game_threads != 256 && o.game_threads != 512) ||
-        o.cycle_kernel < 0 || o.cycle_kernel > 1 ||
+        o.cycle_kernel < 0 || o.cycle_kernel > 1 || o.game_solver < 0 || o.game_solver > 1 ||
+        o.amg_coarsening < 0 || o.amg_coarsening > 1 || !(o.amg_theta >= 0.0 && o.amg_theta < 1.0) ||
         (o.nu1_coarse < 0 ? o.nu1 : o.nu1_coarse) + (o.nu2_coarse < 0 ? o.nu2 : o.nu2_coarse) < 1) {
         set_last_error("create: invalid option value");
         return GS_EINVAL;
@@ -136,7 +140,7 @@ gs_status gamesolve_set_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2,
                              const int64_t* row_ptr, const int32_t* col, const double* prob,
                              const double* reward, double mu) {
     if (!s || n < 1 || m1 < 1 || m1 > 8 || m2 < 1 || m2 > 8 || !row_ptr || !col || !prob ||
-        !reward || !(mu > 0.0 && mu < 1.0)) {
+        !reward || !(mu > 0.0 && (mu < 1.0 || (mu == 1.0 && s->opt.game_solver == 1)))) {
         set_last_error("set_game: invalid argument");
         return GS_EINVAL;
     }
@@ -269,7 +273,11 @@ gs_status gamesolve_solve(gs_solver* s, gs_solve_stats* stats) {
         set_last_error("solve: no problem set");
         return GS_ESTATE;
     }
-    if (s->prob->kind == 2) return guarded([&]() { return run_games(s, stats); });
+    if (s->prob->kind == 2) {
+        if (s->opt.game_solver == 1 && s->prob->game->count == 1)
+            return guarded([&]() { return run_game_amg(s, stats); });
+        return guarded([&]() { return run_games(s, stats); });
+    }
     if (s->prob->kind == 3) return guarded([&]() { return run_line(s, stats); });
     return guarded([&]() { return run_solve(s, stats); });
 }
@@ -366,8 +374,8 @@ gs_status gamesolve_fmg_interpolate(int32_t side_c, int32_t variant, const doubl
 gs_status gamesolve_get_level_stats(const gs_solver* s, int32_t* stats, int32_t cap,
                                     int32_t* levels) {
     if (!s || cap < 0 || (cap > 0 && !stats)) return GS_EINVAL;
-    if (!s->prob || s->prob->kind != 1 || s->level_stats.empty()) {
-        set_last_error("get_level_stats: no solved Isaacs grid");
+    if (!s->prob || (s->prob->kind != 1 && s->prob->kind != 2) || s->level_stats.empty()) {
+        set_last_error("get_level_stats: no solved Isaacs grid or single game");
         return GS_ESTATE;
     }
     const int nl = (int)s->level_stats.size() / 3;

@@ -10,6 +10,7 @@
 // stochastic M the constant vector is the slow mode of I - mu M (eigenvalue
 // 1 - mu), which relaxation cannot remove and the coarse correction removes
 // exactly; the other modes contract at the rate of M's second eigenvalue.
+#include <algorithm>
 #include <cfloat>
 
 #include "games.cuh"
@@ -624,7 +625,50 @@ __global__ void __launch_bounds__(kThreads) k_game_pi_grid(const __grid_constant
     solve_game<T>(B, 0, C);
 }
 
+// One policy improvement of game 0 over the whole grid (the algebraic
+// multigrid path runs policy iteration from the host): keep-current
+// tolerance from |v|_inf (bits at scal + 4), changed entries summed into
+// scal[0], |F(v) - v|_inf (outer mode) as bits at scal + 2.
+__global__ void k_game_improve_one(const __grid_constant__ BatchArgs B, int mode, int* scal) {
+    Game G;
+    G.T = B.T;
+    G.x0 = 0;
+    G.n = B.st_off[1];
+    G.R = B.T.m1 * B.T.m2;
+    G.row0 = 0;
+    G.mu = B.mu[0];
+    G.mu_f = f64_to_f32(G.mu);
+    const double vm = from_bits(*reinterpret_cast<const unsigned long long*>(scal + 4));
+    const double tau = 1e-13 * fmax(1.0, vm);
+    const float tauf = f64_to_f32(tau), vmaxf = f64_to_f32(vm);
+    int changed = 0;
+    unsigned long long rb = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < G.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double r = 0.0;
+        changed += improve_state(G, B.out, mode, i, tau, tauf, vmaxf, B.out.v, &r);
+        const unsigned long long b = bits_of(r);
+        rb = b > rb ? b : rb;
+    }
+    changed = warp_sum(changed);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, rb, o);
+        rb = w > rb ? w : rb;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (changed) atomicAdd(scal, changed);
+        atomicMax(reinterpret_cast<unsigned long long*>(scal + 2), rb);
+    }
+}
+
 }  // namespace
+
+void launch_game_improve_one(const BatchArgs& B, int mode, int64_t n, int* scal, cudaStream_t st) {
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+    k_game_improve_one<<<g, 256, 0, st>>>(B, mode, scal);
+    GS_CHECK_LAUNCH();
+}
 
 void launch_game_validate(const GameTables& T, int count, const int64_t* st_off, int64_t rows,
                           int* bad, cudaStream_t st) {

@@ -94,6 +94,12 @@ int game_grid_blocks(int64_t n, int cap);
 void launch_game_pi_grid(const BatchArgs& B, const GridWork& W, int blocks, bool mixed,
                          cudaStream_t st);
 
+// One policy improvement of a single game (game 0 of B) over the whole grid:
+// mode 0 outer (alpha and beta), 1 inner (beta at alpha), 2 MIN's reply for
+// every a; assembles sel/rhs.  scal[0] += changed entries, scal + 2 (bits) =
+// max |F(v) - v| (outer); the tie tolerance comes from |v|_inf at scal + 4.
+void launch_game_improve_one(const BatchArgs& B, int mode, int64_t n, int* scal, cudaStream_t st);
+
 // Games of at least this many states, set alone, run on the whole grid.
 constexpr int64_t kGameGridMinStates = 4096;
 

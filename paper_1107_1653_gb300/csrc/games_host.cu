@@ -44,9 +44,13 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
     }
     std::vector<double> mu_h(count);
     GS_CUDA(cudaMemcpy(mu_h.data(), mu, sizeof(double) * count, cudaMemcpyDefault));
+    // mu = 1 (undiscounted, as the stopping games of Sec. 6.2-6.3) only for one
+    // game on the algebraic multigrid path: the constant-vector correction
+    // of the two-level method needs leakage on every row
+    const bool undiscounted_ok = count == 1 && s->opt.game_solver == 1;
     for (double m : mu_h)
-        if (!(m > 0.0 && m < 1.0)) {
-            set_last_error("set_game: mu must lie in (0, 1)");
+        if (!(m > 0.0 && (m < 1.0 || (m == 1.0 && undiscounted_ok)))) {
+            set_last_error("set_game: mu must lie in (0, 1) (mu = 1 only with options.game_solver = 1)");
             throw Error{GS_EINVAL};
         }
     const int64_t n_total = off[count];

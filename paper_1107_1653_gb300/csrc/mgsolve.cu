@@ -891,6 +891,36 @@ __device__ __forceinline__ void for_rect(int x0, int x1, int y0, int y1, F&& f) 
     }
 }
 
+// Like for_rect, with B points per thread in flight: ld(i, j) (global loads)
+// runs for all B points before st(i, j, value) (shared-memory stores), so a
+// thread has B points' loads outstanding at once.
+template <int B, class Load, class Store>
+__device__ __forceinline__ void batched_rect(int x0, int x1, int y0, int y1, Load&& ld, Store&& st) {
+    const int nx = x1 - x0, ny = y1 - y0;
+    if (nx <= 0 || ny <= 0) return;
+    const FastDiv dv((unsigned)nx);
+    const unsigned cnt = (unsigned)(nx * ny);
+    using V = decltype(ld(0, 0));
+    for (unsigned base = threadIdx.x; base < cnt; base += B * blockDim.x) {
+        V val[B];
+        int ii[B], jj[B];
+        bool ok[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const unsigned t = base + b * blockDim.x;
+            ok[b] = t < cnt;
+            unsigned r;
+            const int q = (int)dv.divmod(ok[b] ? t : 0u, &r);
+            ii[b] = x0 + (int)r;
+            jj[b] = y0 + q;
+            if (ok[b]) val[b] = ld(ii[b], jj[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (ok[b]) st(ii[b], jj[b], val[b]);
+    }
+}
+
 // Shared-memory forms of the level operators (same arithmetic as L0Op / L9Op).
 struct TFine32 {
     const IsaacsConsts* K;
@@ -1058,33 +1088,49 @@ __device__ __forceinline__ T diag9(const T* A, int wh, int q) {
 // Down leg of a coarse level l (1 <= l < tail): pre-smoothing (the first
 // colour was done by the restriction into l), residual, restriction.
 template <typename T, typename W>
-__device__ void tile_down(const SolveArgs& a, int l, char* smem, int worker, int nworkers) {
+__device__ __noinline__ void tile_down(const SolveArgs& a, int l, char* smem, int worker, int nworkers) {
     const LevelArgs& L = a.L[l];
     const LevelArgs& C = a.L[l + 1];
     const int sf = L.side, sc = L.sc, nu = a.nu1c;
     const int K1 = nu > 0 ? 4 * nu - 1 : 0;
     const int H = 1 + K1;
     const bool zero_uc = l + 1 == a.tail;
-    const int ntiles = tile_count(a.tcc, sc);
+    const int tc = a.tc[l];
+    const int ntiles = tile_count(tc, sc);
     const W* gA = (const W*)L.A;
     T* gu = (T*)L.u;
     const T* gf = (const T*)L.f;
+    struct Pt { T f, A[9]; };
     for (int k = worker; k < ntiles; k += nworkers) {
-        const Tile t = make_tile(k, a.tcc, sc, sf, H);
+        const Tile t = make_tile(k, tc, sc, sf, H);
         const int wh = t.w * t.h;
         T* A = (T*)smem;
         T* u = A + 9 * wh;
         T* f = u + wh;
         T* r = f + wh;   // residuals at fine points [2 I0, 2 I1] x [2 J0, 2 J1]
-        for_rect(t.gx0, t.gx1, t.gy0, t.gy1, [&](int i, int j) {
-            const size_t x = (size_t)j * sf + i;
-            const int q = t.loc(i, j);
-            f[q] = gf[x];
+        batched_rect<2>(
+            t.gx0, t.gx1, t.gy0, t.gy1,
+            [&](int i, int j) {
+                const size_t x = (size_t)j * sf + i;
+                Pt p;
+                p.f = gf[x];
 #pragma unroll
-            for (int d = 0; d < 9; ++d) A[d * wh + q] = (T)wval(gA[d * L.n + x]);
-            // u from the zero start, the first colour (C points) relaxed: f / diag
-            u[q] = nu > 0 && (i & j & 1) ? f[q] / diag9(A, wh, q) : T(0);
-        });
+                for (int d = 0; d < 9; ++d) p.A[d] = (T)wval(gA[d * L.n + x]);
+                return p;
+            },
+            [&](int i, int j, const Pt& p) {
+                const int q = t.loc(i, j);
+                f[q] = p.f;
+                T d = p.A[0];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) A[e * wh + q] = p.A[e];
+                if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                    for (int e = 1; e < 9; ++e) d -= p.A[e];
+                }
+                // u from the zero start, the first colour (C points) relaxed: f / diag
+                u[q] = nu > 0 && (i & j & 1) ? p.f / d : T(0);
+            });
         __syncthreads();
         const T9<T> op{A, sf, t.w, wh};
         Valid v{t.gx0, t.gx1, t.gy0, t.gy1};
@@ -1112,32 +1158,44 @@ __device__ void tile_down(const SolveArgs& a, int l, char* smem, int worker, int
 
 // Up leg of a coarse level l: prolongation from l + 1, post-smoothing.
 template <typename T, typename W>
-__device__ void tile_up(const SolveArgs& a, int l, char* smem, int worker, int nworkers) {
+__device__ __noinline__ void tile_up(const SolveArgs& a, int l, char* smem, int worker, int nworkers) {
     const LevelArgs& L = a.L[l];
     const LevelArgs& C = a.L[l + 1];
     const int sf = L.side, sc = L.sc, nu = a.nu2c;
     const int H = 4 * nu;
-    const int ntiles = tile_count(a.tcc, sc);
+    const int tc = a.tc[l];
+    const int ntiles = tile_count(tc, sc);
     const W* gA = (const W*)L.A;
     const W* gP = (const W*)L.P;
     const T* guc = (const T*)(l + 1 == a.tail ? C.u : C.u2);
     const T* gu = (const T*)L.u;   // after the pre-smoothing
     T* gu2 = (T*)L.u2;             // after the post-smoothing (other tiles still read gu)
     const T* gf = (const T*)L.f;
+    struct Pt { T u, f, A[9]; };
     for (int k = worker; k < ntiles; k += nworkers) {
-        const Tile t = make_tile(k, a.tcc, sc, sf, H);
+        const Tile t = make_tile(k, tc, sc, sf, H);
         const int wh = t.w * t.h;
         T* A = (T*)smem;
         T* u = A + 9 * wh;
         T* f = u + wh;
-        for_rect(t.gx0, t.gx1, t.gy0, t.gy1, [&](int i, int j) {
-            const size_t x = (size_t)j * sf + i;
-            const int q = t.loc(i, j);
-            u[q] = gu[x] + prolonged<T, W>(gP, guc, sc, i, j);
-            f[q] = gf[x];
+        batched_rect<2>(
+            t.gx0, t.gx1, t.gy0, t.gy1,
+            [&](int i, int j) {
+                const size_t x = (size_t)j * sf + i;
+                Pt p;
+                p.u = gu[x] + prolonged<T, W>(gP, guc, sc, i, j);
+                p.f = gf[x];
 #pragma unroll
-            for (int d = 0; d < 9; ++d) A[d * wh + q] = (T)wval(gA[d * L.n + x]);
-        });
+                for (int d = 0; d < 9; ++d) p.A[d] = (T)wval(gA[d * L.n + x]);
+                return p;
+            },
+            [&](int i, int j, const Pt& p) {
+                const int q = t.loc(i, j);
+                u[q] = p.u;
+                f[q] = p.f;
+#pragma unroll
+                for (int d = 0; d < 9; ++d) A[d * wh + q] = p.A[d];
+            });
         __syncthreads();
         const T9<T> op{A, sf, t.w, wh};
         Valid v{t.gx0, t.gx1, t.gy0, t.gy1};
@@ -1184,7 +1242,7 @@ __device__ void tile_fine_mixed(const SolveArgs& a, bool full, int slot, const F
     const int K1 = a.nu1 > 0 ? 2 * a.nu1 - 1 : 0;
     const int H = 2 + K1 + K2;
     const bool zero_uc = a.tail == 1;
-    const int ntiles = tile_count(a.tc0, sc);
+    const int ntiles = tile_count(a.tc[0], sc);
     const W* gP = (const W*)L.P;
     const float* guc = (const float*)(a.tail == 1 ? C.u : C.u2);
     const float* ge = (const float*)B.e_in;
@@ -1193,7 +1251,7 @@ __device__ void tile_fine_mixed(const SolveArgs& a, bool full, int slot, const F
     float* gr_out = (float*)B.r_out;
     unsigned long long rm = 0, vm = 0;
     for (int k = worker; k < ntiles; k += nworkers) {
-        const Tile t = make_tile(k, a.tc0, sc, sf, H);
+        const Tile t = make_tile(k, a.tc[0], sc, sf, H);
         const int wh = t.w * t.h;
         double* v = (double*)smem;
         float* e = (float*)(v + wh);
@@ -1295,12 +1353,12 @@ __device__ void tile_fine_fp64(const SolveArgs& a, bool full, int slot, const Fi
     const int K1 = 2 * a.nu1;
     const int H = 1 + K1 + K2;
     const bool zero_uc = a.tail == 1;
-    const int ntiles = tile_count(a.tc0, sc);
+    const int ntiles = tile_count(a.tc[0], sc);
     const double* gP = (const double*)L.P;
     const double* guc = (const double*)(a.tail == 1 ? C.u : C.u2);
     unsigned long long rm = 0, vm = 0;
     for (int k = worker; k < ntiles; k += nworkers) {
-        const Tile t = make_tile(k, a.tc0, sc, sf, H);
+        const Tile t = make_tile(k, a.tc[0], sc, sf, H);
         const int wh = t.w * t.h;
         double* v = (double*)smem;
         double* f = v + wh;
@@ -1362,7 +1420,7 @@ __device__ void tile_fine_fp64(const SolveArgs& a, bool full, int slot, const Fi
 }
 
 template <typename T, typename W>
-__device__ __forceinline__ void tile_fine(const SolveArgs& a, bool full, int slot, const FineBufs& B,
+__device__ __noinline__ void tile_fine(const SolveArgs& a, bool full, int slot, const FineBufs& B,
                                           char* smem, int worker, int nworkers) {
     if constexpr (sizeof(T) == 4) tile_fine_mixed<W>(a, full, slot, B, smem, worker, nworkers);
     else tile_fine_fp64(a, full, slot, B, smem, worker, nworkers);
@@ -1397,6 +1455,58 @@ __device__ __forceinline__ FineBufs fine_bufs(const SolveArgs& a, bool full, int
     return B;
 }
 
+// First post-smoothing colour of the finest level fused with the
+// prolongation: a colour-0 point's Gauss-Seidel value needs only its four
+// neighbours (colour 1), taken as u + P u_c on the fly; the colour-0 points'
+// own prolonged values would be overwritten unread, and the colour-1 points'
+// are not needed by the next colour either (it reads only colour 0).
+template <typename T, typename W>
+__device__ __noinline__ void relax_fine_prolonged(const SolveArgs& a, const T* uc, size_t start,
+                                                  size_t stride) {
+    const LevelArgs& L = a.L[0];
+    const L0Op<T> op{a.K, a.code, L.side};
+    T* __restrict__ u = (T*)L.u;
+    const T* __restrict__ f = (const T*)L.f;
+    const W* P = (const W*)L.P;
+    const int side = L.side, sc = L.sc, hs = (side + 1) / 2;
+    const unsigned cnt = (unsigned)side * hs, st = (unsigned)stride;
+    const FastDiv dv(hs);
+    auto nb = [&](int i, int j) -> T {
+        return u[(size_t)j * side + i] + prolonged<T, W>(P, uc, sc, i, j);
+    };
+    for (unsigned t = (unsigned)start; t < cnt; t += st) {
+        unsigned r;
+        const int j = (int)dv.divmod(t, &r), i = (j & 1) + 2 * (int)r;
+        if (i >= side) continue;
+        const T uW = i > 0 ? nb(i - 1, j) : T(0);
+        const T uE = i + 1 < side ? nb(i + 1, j) : T(0);
+        const T uS = j > 0 ? nb(i, j - 1) : T(0);
+        const T uN = j + 1 < side ? nb(i, j + 1) : T(0);
+        u[(size_t)j * side + i] = op.relaxed_nb(f, i, j, uW, uE, uS, uN);
+    }
+}
+
+// The tail's V-cycle and the grid-wide phases of the finest level as calls of
+// their own (the tiled kernel's register budget is that of two blocks per SM).
+template <typename T, typename W>
+__device__ __noinline__ void tail_vcycle(const SolveArgs& a, const LevelArgs* tl, const double* inv) {
+    block_vcycle<T, W>(a, tl, inv, a.tail, true);
+}
+template <typename T, typename W>
+__device__ __noinline__ void fine_relax(const SolveArgs& a, int c, bool zero, size_t gt, size_t gs) {
+    relax_level<T, W>(a, a.L[0], 0, c, zero, gt, gs);
+}
+template <typename T, typename W>
+__device__ __noinline__ void fine_restrict(const SolveArgs& a, size_t gt, size_t gs) {
+    restrict_level<T, W>(a, a.L[0], a.L[1], 0, 1 < a.tail && 1 < a.nlev - 1 && sweeps_pre(a, 1) > 0, gt, gs);
+}
+__device__ __noinline__ void fine_check(const SolveArgs& a, int slot, size_t gt, size_t gs) {
+    check_phase(a, slot, gt, gs);
+}
+__device__ __noinline__ void fine_update(const SolveArgs& a, int c, size_t gt, size_t gs) {
+    relax_fine_update(L0Op<float>{a.K, a.code, a.L[0].side}, a.L[0], a.v, c, gt, gs);
+}
+
 // V-cycles with tiled grid-wide levels; block 0 stages and runs the tail.
 template <typename T, typename W>
 __global__ void __launch_bounds__(kMGThreads, 2) k_mg_cycles_tiled(const __grid_constant__ SolveArgs a) {
@@ -1404,14 +1514,18 @@ __global__ void __launch_bounds__(kMGThreads, 2) k_mg_cycles_tiled(const __grid_
     __shared__ LevelArgs tl[kMaxLevels];
     const GridSync G{a.bar, gridDim.x};
     const int worker = (int)blockIdx.x - 1, nworkers = (int)gridDim.x - 1;
+    const size_t gt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t gs = (size_t)gridDim.x * blockDim.x;
     if (!G.sync()) return;   // set-up complete (and error state shared)
     prof_mark(8000);
     double* inv = a.inv;
     int slot = 0, cur = 0;
     // block 0 stages the tail while the others take the first residual check
-    // with the first cycle's pre-smoothing and restriction
+    // (with the first cycle's pre-smoothing and restriction when the finest
+    // level is tiled)
     if (blockIdx.x == 0) stage_tail<T, W>(a, smem_t, tl, &inv);
-    else tile_fine<T, W>(a, false, slot, fine_bufs<T>(a, false, cur), smem_t, worker, nworkers);
+    else if (a.tile_fine) tile_fine<T, W>(a, false, slot, fine_bufs<T>(a, false, cur), smem_t, worker, nworkers);
+    else fine_check(a, slot, gt - blockDim.x, gs - blockDim.x);
     if (!G.sync()) return;
     prof_mark(6000);
     double prev = 0.0, res0 = 0.0;
@@ -1440,7 +1554,7 @@ __global__ void __launch_bounds__(kMGThreads, 2) k_mg_cycles_tiled(const __grid_
             }
             if constexpr (sizeof(T) == 4) {
                 // the last value went to the second set: copy it home
-                if (cur == 1) {
+                if (a.tile_fine && cur == 1) {
                     const size_t n = a.L[0].n;
                     for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
                          x += (size_t)gridDim.x * blockDim.x)
@@ -1453,12 +1567,29 @@ __global__ void __launch_bounds__(kMGThreads, 2) k_mg_cycles_tiled(const __grid_
             a.out->rmax[slot ^ 1] = 0ull;
             a.out->vmax[slot ^ 1] = 0ull;
         }
+        if (!a.tile_fine) {
+            // finest level, one phase per colour: pre-smoothing (the first
+            // colour from the zero start was done by the residual check in
+            // the mixed path), then the restriction
+            const bool z = a.mixed != 0;
+            const bool done0 = z && fine_colour0_in_check(a);
+            for (int k = 0; k < a.nu1; ++k)
+                for (int c = 0; c < 2; ++c) {
+                    if (done0 && k == 0 && c == 0) continue;
+                    fine_relax<T, W>(a, c, z && k == 0 && c == 0, gt, gs);
+                    if (!G.sync()) return;
+                    prof_mark(1000 + c);
+                }
+            fine_restrict<T, W>(a, gt, gs);
+            if (!G.sync()) return;
+            prof_mark(2000);
+        }
         for (int l = 1; l < a.tail; ++l) {
             if (worker >= 0) tile_down<T, W>(a, l, smem_t, worker, nworkers);
             if (!G.sync()) return;
             prof_mark(2000 + 10 * l);
         }
-        if (blockIdx.x == 0) block_vcycle<T, W>(a, tl, inv, a.tail, true);
+        if (blockIdx.x == 0) tail_vcycle<T, W>(a, tl, inv);
         if (!G.sync()) return;
         prof_mark(4000);
         for (int l = a.tail - 1; l >= 1; --l) {
@@ -1467,8 +1598,46 @@ __global__ void __launch_bounds__(kMGThreads, 2) k_mg_cycles_tiled(const __grid_
             prof_mark(3000 + 10 * l);
         }
         slot ^= 1;
-        if (worker >= 0) tile_fine<T, W>(a, true, slot, fine_bufs<T>(a, true, cur), smem_t, worker, nworkers);
-        cur ^= 1;
+        if (a.tile_fine) {
+            if (worker >= 0)
+                tile_fine<T, W>(a, true, slot, fine_bufs<T>(a, true, cur), smem_t, worker, nworkers);
+            cur ^= 1;
+            if (!G.sync()) return;
+            prof_mark(6000);
+            continue;
+        }
+        // finest level, one phase per colour: the prolongation folded into
+        // the first post-smoothing colour, the float64 update v += e into the
+        // last (mixed path), then the residual check
+        const T* uc = (const T*)(a.tail == 1 ? a.L[1].u : a.L[1].u2);
+        if (a.nu2 == 0) {
+            LevelArgs C = a.L[1];
+            C.u = (void*)uc;
+            prolong_phase<T, W>(a.L[0], C, gt, gs);
+            if (!G.sync()) return;
+            if (a.mixed) {
+                axpy_phase(a, gt, gs);
+                if (!G.sync()) return;
+            }
+        }
+        for (int k = 0; k < a.nu2; ++k)
+            for (int c = 0; c < 2; ++c) {
+                if (k == 0 && c == 0) {
+                    relax_fine_prolonged<T, W>(a, uc, gt, gs);
+                } else {
+                    bool done = false;
+                    if constexpr (sizeof(T) == 4) {
+                        if (k == a.nu2 - 1 && c == 1) {
+                            fine_update(a, c, gt, gs);
+                            done = true;
+                        }
+                    }
+                    if (!done) fine_relax<T, W>(a, c, false, gt, gs);
+                }
+                if (!G.sync()) return;
+                prof_mark(1000 + c);
+            }
+        fine_check(a, slot, gt, gs);
         if (!G.sync()) return;
         prof_mark(6000);
     }
@@ -1536,8 +1705,8 @@ int tiled_max_tiles(const SolveArgs& a) {
         const int nt = (sc + tc - 1) / tc;
         return nt * nt;
     };
-    int m = tiles(a.tc0, a.L[0].sc);
-    for (int l = 1; l < a.tail; ++l) m = std::max(m, tiles(a.tcc, a.L[l].sc));
+    int m = a.tile_fine ? tiles(a.tc[0], a.L[0].sc) : 0;
+    for (int l = 1; l < a.tail; ++l) m = std::max(m, tiles(a.tc[l], a.L[l].sc));
     return m;
 }
 
@@ -1550,24 +1719,38 @@ size_t tiled_smem_bytes(const SolveArgs& a) {
     };
     auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
     size_t need = tail_smem_bytes(a);
-    {   // finest level
+    if (a.tile_fine) {   // finest level
         const LevelArgs& L = a.L[0];
         const int K1 = a.mixed ? (a.nu1 > 0 ? 2 * a.nu1 - 1 : 0) : 2 * a.nu1;
         const int H = (a.mixed ? 2 : 1) + K1 + 2 * a.nu2;
-        const size_t w = side(a.tc0, L.sc, L.side, H), wh = w * w;
-        const size_t rw = 2 * (size_t)std::min(a.tc0, L.sc) + 1;
+        const size_t w = side(a.tc[0], L.sc, L.side, H), wh = w * w;
+        const size_t rw = 2 * (size_t)std::min(a.tc[0], L.sc) + 1;
         need = std::max(need, 16 * wh + r16(wh) + rw * rw * T);
     }
     for (int l = 1; l < a.tail; ++l) {
         const LevelArgs& L = a.L[l];
         const int K1 = a.nu1c > 0 ? 4 * a.nu1c - 1 : 0;
-        const size_t wd = side(a.tcc, L.sc, L.side, 1 + K1);
-        const size_t rw = 2 * (size_t)std::min(a.tcc, L.sc) + 1;
+        const size_t wd = side(a.tc[l], L.sc, L.side, 1 + K1);
+        const size_t rw = 2 * (size_t)std::min(a.tc[l], L.sc) + 1;
         need = std::max(need, 11 * T * wd * wd + rw * rw * T);
-        const size_t wu = side(a.tcc, L.sc, L.side, 4 * a.nu2c);
+        const size_t wu = side(a.tc[l], L.sc, L.side, 4 * a.nu2c);
         need = std::max(need, 11 * T * wu * wu);
     }
     return need;
+}
+
+void set_tile_sides(SolveArgs& a, int workers) {
+    // the finest level's tile (when tiled): 16 x 16 points of level 1
+    a.tc[0] = 16;
+    // coarse levels: about one tile per worker block, at least 2 x 2 points
+    // of the next level, at most 16 x 16 (8 x 8 in float64: shared memory)
+    int root = 1;
+    while ((root + 1) * (root + 1) <= std::max(1, workers)) ++root;
+    const int cap = a.mixed ? 16 : 8;
+    for (int l = 1; l < kMaxLevels; ++l) {
+        const int sc = l < a.nlev ? a.L[l].sc : 1;
+        a.tc[l] = std::max(2, std::min(cap, (sc + root - 1) / root));
+    }
 }
 
 size_t tail_smem_bytes(const SolveArgs& a) {

@@ -57,7 +57,8 @@ struct SolveArgs {
     double lin_tol;
     double rel_tol;  // also stop once the residual fell by this factor (0: floor only)
     int tiled;       // V-cycles with tiled grid-wide levels (k_mg_cycles_tiled)
-    int tc0, tcc;    // tile sides, in points of the next coarser level: finest, coarse levels
+    int tile_fine;   // tiled: the finest level tiled too (else one phase per colour there)
+    int tc[kMaxLevels];   // tile side of level l, in points of level l + 1
     double* v2;      // tiled cycles, finest level: second value buffer
     double* v3;      // float64 path: third value buffer
     void* e2;        // mixed path: second correction buffer
@@ -82,5 +83,8 @@ size_t tail_smem_bytes(const SolveArgs& a);
 // needs (the tail's and the largest tile's, whichever is more).
 constexpr int kTiledSmemMax = 110 * 1024;
 size_t tiled_smem_bytes(const SolveArgs& a);
+
+// Tile sides of a tiled launch for `workers` tile-taking thread blocks.
+void set_tile_sides(SolveArgs& a, int workers);
 
 }  // namespace gs

@@ -371,8 +371,16 @@ int linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, boo
     a.v3 = g.lv[0].w64;
     a.e2 = g.lv[0].r32;
     a.r2 = g.lv[0].w32;
-    a.tc0 = 16;
-    a.tcc = mixed ? 16 : 8;
+    a.tile_fine = 0;
+    // about two blocks per SM in a tiled launch; tile sides for that many workers
+    {
+        int dev = 0, sms = 0;
+        GS_CUDA(cudaGetDevice(&dev));
+        GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int blocks = 2 * sms;
+        if (a.max_blocks > 0) blocks = std::min(blocks, a.max_blocks);
+        set_tile_sides(a, std::max(1, blocks - 1));
+    }
     // levels from smem_from on are staged in block 0's shared memory, as many as fit
     a.smem_from = std::max(a.tail, 1);
     while (a.smem_from < a.nlev && tail_smem_bytes(a) > (size_t)kTailSmemMax)

@@ -5,6 +5,7 @@
 #include <memory>
 #include <vector>
 
+#include "amg.cuh"
 #include "kernels.cuh"
 #include "mgsolve.cuh"
 #include "games.cuh"
@@ -25,6 +26,7 @@ public:
     T* alloc(size_t count) {
         return static_cast<T*>(raw(count * sizeof(T)));
     }
+    void* raw_bytes(size_t bytes) { return raw(bytes); }
     size_t held() const { return held_; }
 
 private:
@@ -90,6 +92,11 @@ struct GameProblem {
     GridBarrier* bar = nullptr;
     std::vector<int> stats_h;
     std::vector<double> res_h;
+    // algebraic multigrid path (options.game_solver = 1): the current
+    // hierarchy, small device scalars and the longest row of the tables
+    std::unique_ptr<AmgHierarchy> amg;
+    int* amg_scal = nullptr;               // [0] changed, [2..3] |F(v)-v| bits, [4..5] |v| bits
+    int amg_row_max = 0;
     GameTables tables() const {
         return {m1,   m2, row_ptr, col, prob, prob_bf16 ? nullptr : prob32,
                 prob_bf16 ? (const __nv_bfloat16*)prob32 : nullptr, rew, leak, leak32, k_uniform};
@@ -171,6 +178,7 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
                                             const int32_t* col, const double* prob,
                                             const double* reward, const double* mu);
 gs_status run_games(gs_solver* s, gs_solve_stats* stats);
+gs_status run_game_amg(gs_solver* s, gs_solve_stats* stats);
 std::unique_ptr<Problem> build_line_problem(gs_solver* s, int32_t n, const double* c,
                                             const double* psi1, const double* psi2, double v_left,
                                             double v_right);

@@ -133,6 +133,18 @@ struct L0Op<double> {
         }
         return s / am[0];
     }
+    // The same update with the four neighbours' values given (W, E, S, N).
+    __device__ __forceinline__ double relaxed_nb(const double* f, int i, int j, double uW, double uE,
+                                                 double uS, double uN) const {
+        const size_t x = (size_t)j * side + i;
+        const double* am = K->am[code[x]];
+        double s = f[x];
+        if (i > 0) s -= am[1] * uW;
+        if (i + 1 < side) s -= am[2] * uE;
+        if (j > 0) s -= am[3] * uS;
+        if (j + 1 < side) s -= am[4] * uN;
+        return s / am[0];
+    }
 };
 
 template <>
@@ -173,6 +185,18 @@ struct L0Op<float> {
         if (i + 1 < side) { diag -= am[2]; if (!zero) s -= am[2] * u[x + 1]; }
         if (j > 0) { diag -= am[3]; if (!zero) s -= am[3] * u[x - side]; }
         if (j + 1 < side) { diag -= am[4]; if (!zero) s -= am[4] * u[x + side]; }
+        return s / diag;
+    }
+    __device__ __forceinline__ float relaxed_nb(const float* f, int i, int j, float uW, float uE,
+                                                float uS, float uN) const {
+        const size_t x = (size_t)j * side + i;
+        const int c = code[x];
+        const float* am = K->amf[c];
+        float diag = l0_rowsum_f(K, c, i, j, side), s = f[x];
+        if (i > 0) { diag -= am[1]; s -= am[1] * uW; }
+        if (i + 1 < side) { diag -= am[2]; s -= am[2] * uE; }
+        if (j > 0) { diag -= am[3]; s -= am[3] * uS; }
+        if (j + 1 < side) { diag -= am[4]; s -= am[4] * uN; }
         return s / diag;
     }
 };

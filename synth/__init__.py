@@ -212,3 +212,87 @@ def stopping_line(points: int):
     c = h * h * 0.5 * np.pi ** 2 * np.cos(np.pi * x)
     n = m - 1
     return c, np.full(n, -psi_bar), np.full(n, psi_bar), float(psi_bar), float(-psi_bar)
+
+
+def isaacs_tables(side: int, variant: int, seed: int):
+    """The finite-difference Isaacs workload written out as explicit CSR
+    transition tables (the C-ABI's gamesolve_set_game layout), so that the
+    general finite-game path can be run on it.  Problem data only: the grid,
+    the upwind stencil probabilities and the rewards of the workload's
+    definition (interior side x side, h = 1/(side+1), directions
+    0:+x1 1:-x1 2:+x2 3:-x2, drift (e_a - e_b)/2, normaliser 2 + h, neighbours
+    on the boundary dropped, mu = 1/(1+h^2), reward (1 - mu)(sin pi x1 sin pi x2
+    + 0.1(a - b) + xi) with xi from isaacs_noise; variant 1 adds MAX's stop
+    action a = 4 with no successors and reward 0.2 - |x - (1/2,1/2)|^2).
+
+    Returns (n, m1, m2, row_ptr, col, prob, reward, mu); row (x*m1 + a)*m2 + b.
+    """
+    h = 1.0 / (side + 1)
+    c0 = 2.0 + h
+    mu = 1.0 / (1.0 + h * h)
+    kappa = (h * h) / (1.0 + h * h)
+    n = side * side
+    m1, m2 = (5 if variant == 1 else 4), 4
+    xi = isaacs_noise(side, seed)
+    steps = ((1, 0), (-1, 0), (0, 1), (0, -1))
+    row_ptr = [0]
+    cols, probs, rews = [], [], []
+    for x in range(n):
+        i1, i2 = x % side, x // side
+        x1, x2 = (i1 + 1) * h, (i2 + 1) * h
+        base = np.sin(np.pi * x1) * np.sin(np.pi * x2) + xi[x]
+        for a in range(m1):
+            for b in range(m2):
+                if a == 4:
+                    rews.append(0.2 - ((x1 - 0.5) ** 2 + (x2 - 0.5) ** 2))
+                    row_ptr.append(len(cols))
+                    continue
+                d1 = 0.5 * (steps[a][0] - steps[b][0])
+                d2 = 0.5 * (steps[a][1] - steps[b][1])
+                for (s1, s2), drift in (((1, 0), d1), ((-1, 0), -d1), ((0, 1), d2), ((0, -1), -d2)):
+                    j1, j2 = i1 + s1, i2 + s2
+                    if 0 <= j1 < side and 0 <= j2 < side:
+                        cols.append(j2 * side + j1)
+                        probs.append((0.5 + h * max(drift, 0.0)) / c0)
+                if a == b:
+                    cols.append(x)
+                    probs.append(h / c0)
+                rews.append(kappa * (base + 0.1 * (a - b)))
+                row_ptr.append(len(cols))
+    return (n, m1, m2, np.array(row_ptr, np.int64), np.array(cols, np.int32),
+            np.array(probs, np.float64), np.array(rews, np.float64), mu)
+
+
+def two_stop_tables(points: int):
+    """The two-sided stopping game of Sec. 6.3 on `points` grid points as
+    explicit CSR tables (gamesolve_set_game layout, undiscounted: mu = 1):
+    n = points - 2 interior states, actions 0 = stop, 1 = continue for both
+    players; (a, b = 0): MIN stops, reward psi_bar; (a = 0, b = 1): MAX stops,
+    reward -psi_bar; (1, 1): both continue to the two neighbours with
+    probability 1/2 each, reward h^2 r(x) plus half of an end point's stop
+    value where a neighbour is an end point (v(0) = psi_bar, v(1) = -psi_bar).
+
+    Returns (n, m1, m2, row_ptr, col, prob, reward, mu)."""
+    c, psi1, psi2, v_left, v_right = stopping_line(points)
+    n = points - 2
+    row_ptr = [0]
+    cols, probs, rews = [], [], []
+    for x in range(n):
+        for a in range(2):
+            for b in range(2):
+                if b == 0:
+                    rews.append(psi2[x])
+                elif a == 0:
+                    rews.append(psi1[x])
+                else:
+                    r = c[x]
+                    for j, end in ((x - 1, v_left), (x + 1, v_right)):
+                        if 0 <= j < n:
+                            cols.append(j)
+                            probs.append(0.5)
+                        else:
+                            r += 0.5 * end
+                    rews.append(r)
+                row_ptr.append(len(cols))
+    return (n, 2, 2, np.array(row_ptr, np.int64), np.array(cols, np.int32),
+            np.array(probs, np.float64), np.array(rews, np.float64), 1.0)

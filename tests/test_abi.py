@@ -32,8 +32,9 @@ def test_every_declared_symbol_is_exported(gs):
 
 
 def test_struct_layouts_match_header(gs):
-    # gs_options: 136 bytes, the stream pointer at 88; gs_solve_stats: 48 bytes
-    assert ctypes.sizeof(gs.gs_options) == 136 and gs.gs_options.stream.offset == 88
+    # gs_options: 152 bytes, the stream pointer at 88; gs_solve_stats: 48 bytes
+    assert ctypes.sizeof(gs.gs_options) == 152 and gs.gs_options.stream.offset == 88
+    assert gs.gs_options.game_solver.offset == 136 and gs.gs_options.amg_theta.offset == 144
     assert gs.gs_options.grid_blocks.offset == 112
     assert gs.gs_options.cycle_gamma.offset == 116
     assert gs.gs_options.nu1_coarse.offset == 120 and gs.gs_options.nu2_coarse.offset == 124
@@ -52,7 +53,8 @@ def test_host_side_checks_without_gpu(gs):
     assert gs.lib.gamesolve_create(None, None) == gs.GS_EINVAL
     h = ctypes.c_void_p()
     for kw in ({"coarse_max": 0}, {"nu1_coarse": -2}, {"nu1_coarse": 0, "nu2_coarse": 0},
-               {"game_threads": 384}, {"cycle_kernel": 2}):
+               {"game_threads": 384}, {"cycle_kernel": 2}, {"game_solver": 2},
+               {"amg_coarsening": 2}, {"amg_theta": 1.0}):
         bad = gs.default_options(**kw)
         assert gs.lib.gamesolve_create(ctypes.byref(h), ctypes.byref(bad)) == gs.GS_EINVAL, kw
     assert gs.lib.gamesolve_solve(None, None) == gs.GS_EINVAL

@@ -420,3 +420,46 @@ def test_config_reward_hand_values():
     h = 0.25
     x = 4                                       # centre point (1/2, 1/2)
     assert abs(g.rew[x, 1, 3] - h * h / (1 + h * h) * (1.0 - 0.2)) <= 1e-17
+
+
+# ----------------------------------------------------------------- table generators
+def _rows_as_sets(game):
+    """{(x, a, b): (sorted successor/probability pairs, reward)} of a Game."""
+    out = {}
+    n, m1, m2 = game.n, game.m1, game.m2
+    for x in range(n):
+        for a in range(m1):
+            for b in range(m2):
+                pairs = sorted((int(y), float(p)) for y, p in zip(game.succ[x, a, b], game.prob[x, a, b])
+                               if y >= 0 and p != 0.0)
+                out[(x, a, b)] = (pairs, float(game.rew[x, a, b]))
+    return out
+
+
+@pytest.mark.parametrize("side,variant", [(3, 0), (7, 0), (7, 1)])
+def test_isaacs_tables_are_the_oracles_game(side, variant):
+    """synth's CSR tables of the Isaacs workload (input of the finite-game path)
+    describe the same game as the oracle's own generator."""
+    n, m1, m2, rp, col, prob, rew, mu = synth.isaacs_tables(side, variant, 5)
+    ours = _rows_as_sets(game_from_csr(n, m1, m2, rp, col, prob, rew, mu))
+    ref_game = isaacs_game(side, variant, seed=5)
+    ref = _rows_as_sets(ref_game)
+    assert abs(mu - ref_game.mu) <= 1e-16
+    for key in ref:
+        (pa, ra), (pb, rb) = ours[key], ref[key]
+        assert [y for y, _ in pa] == [y for y, _ in pb], key
+        assert np.allclose([p for _, p in pa], [p for _, p in pb], rtol=0, atol=1e-16), key
+        assert abs(ra - rb) <= 1e-16 + 1e-15 * abs(rb), key
+
+
+def test_two_stop_tables_are_the_oracles_game():
+    from oracle.stopping1d import two_stop_game
+    n, m1, m2, rp, col, prob, rew, mu = synth.two_stop_tables(17)
+    ours = _rows_as_sets(game_from_csr(n, m1, m2, rp, col, prob, rew, mu))
+    ref_game = two_stop_game(17)
+    ref = _rows_as_sets(ref_game)
+    assert mu == ref_game.mu == 1.0
+    for key in ref:
+        (pa, ra), (pb, rb) = ours[key], ref[key]
+        assert pa == pb, key
+        assert abs(ra - rb) <= 1e-15, key

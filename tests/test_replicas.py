@@ -88,4 +88,9 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
         rc = bench.run_reference(type("A", (), {"steps": 2, "warmup": 1})())
     line = json.loads(buf.getvalue())
     assert rc == 0 and line["impl"] == "reference" and line["n_gpus"] == 2
-    assert len(called) == 3 and line["value"] == pytest.approx(1.0)
+    # one evaluation (0.5 s) + one improvement (0.1 s) per step; a solve is
+    # `systems` evaluations and `systems + outer` improvements
+    systems, outer = bench.oracle_counts()
+    assert len(called) == 3
+    assert line["value"] == pytest.approx(1.0 / (systems * 0.5 + (systems + outer) * 0.1))
+    assert line["ms_per_step"] == pytest.approx(600.0)
