@@ -160,8 +160,10 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt);
  * launch: policy iteration on the device with bounded grid barriers); a
  * smaller one runs in one thread block.  Warm starts (set_initial), improve
  * and policy_solve are for Isaacs grids.
- * Errors (GS_EINVAL, solver unchanged): n < 1 or too large, m1 or m2 outside
- * [1, 8], row_ptr not non-decreasing from 0, a column out of range, a
+ * Errors (GS_EINVAL, solver unchanged): n < 1 or too large, m1 outside
+ * [1, 64] or m2 outside [1, 255] (games with more than 8 MAX actions take the
+ * float64 improvement without the float32 screen), row_ptr not
+ * non-decreasing from 0, a column out of range, a
  * probability outside [0, 1], a row sum above 1 + 1e-12, mu outside (0, 1).
  * mu = 1 (undiscounted, as the stopping games of Sec. 6.2-6.3) is accepted
  * with options.game_solver = 1; every pair of policies must then make the

@@ -540,10 +540,12 @@ struct Aug {
     __device__ double& operator()(int r, int c) const { return m[r * w + c]; }
 };
 
+// The augmented matrix lives in shared memory (n <= kAmgInvSmem) or in the
+// global scratch gm (larger coarsest levels).
 __global__ void k_amg_coarse_inv(int n, int W, const int* __restrict__ col, const double* __restrict__ a,
-                                 double* __restrict__ inv, int* __restrict__ status) {
+                                 double* __restrict__ inv, int* __restrict__ status, double* gm) {
     extern __shared__ double msh[];
-    const Aug M{msh, 2 * n};
+    const Aug M{gm ? gm : msh, 2 * n};
     __shared__ int piv;
     for (int k = threadIdx.x; k < n * 2 * n; k += blockDim.x) {
         const int r = k / (2 * n), c = k % (2 * n);
@@ -1350,9 +1352,9 @@ gs_status run_game_fmg(gs_solver* s, gs_solve_stats* stats) {
             R.levels = r.levels;
             R.res = r.res;
             R.converged = r.converged;
-        } else if (!r.converged) {
-            break;
         }
+        // a coarse level that stops short of its fixed point still hands its
+        // iterate up: the coarse games only provide the starting point
     }
     s->level_stats = per;
     GS_CUDA(cudaEventRecord(e1, st));
@@ -1506,11 +1508,13 @@ void AmgHierarchy::build(const GameTables& T, const int64_t* sel, double mu, int
     static bool attr = false;
     if (!attr) {
         GS_CUDA(cudaFuncSetAttribute(k_amg_coarse_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(2 * kAmgCoarsest * kAmgCoarsest * sizeof(double))));
+                                     (int)(2 * kAmgInvSmem * kAmgInvSmem * sizeof(double))));
         attr = true;
     }
-    k_amg_coarse_inv<<<1, 256, 2 * (size_t)Lc.n * Lc.n * sizeof(double), st>>>(Lc.n, Lc.W, Lc.col, Lc.a64,
-                                                                             inv, scal + 4);
+    const bool in_smem = Lc.n <= kAmgInvSmem;
+    double* gm = in_smem ? nullptr : ar->alloc<double>(2 * (size_t)Lc.n * Lc.n);
+    k_amg_coarse_inv<<<1, in_smem ? 256 : 1024, in_smem ? 2 * (size_t)Lc.n * Lc.n * sizeof(double) : 0, st>>>(
+        Lc.n, Lc.W, Lc.col, Lc.a64, inv, scal + 4, gm);
     GS_CHECK_LAUNCH();
     read_scal();
     if (hs[4]) {

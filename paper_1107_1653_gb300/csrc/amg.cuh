@@ -13,7 +13,8 @@
 namespace gs {
 
 constexpr int kAmgMaxLevels = 24;
-constexpr int kAmgCoarsest = 64;        // the coarsest level is solved by its inverse
+constexpr int kAmgCoarsest = 128;       // the coarsest level is solved by its inverse
+constexpr int kAmgInvSmem = 64;         // inverted in shared memory up to this size
 constexpr int kAmgRowCap = 96;          // entries of a coarse row the set-up accumulates
 constexpr int kAmgCoarseSweeps = 30;    // Jacobi sweeps on a coarsest level too large to invert
 constexpr int kAmgMaxColours = 128;     // colours of the Gauss-Seidel smoother's colouring

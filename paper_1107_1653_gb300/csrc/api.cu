@@ -139,7 +139,7 @@ gs_status gamesolve_create(gs_solver** out, const gs_options* opt) {
 gs_status gamesolve_set_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2,
                              const int64_t* row_ptr, const int32_t* col, const double* prob,
                              const double* reward, double mu) {
-    if (!s || n < 1 || m1 < 1 || m1 > 8 || m2 < 1 || m2 > 8 || !row_ptr || !col || !prob ||
+    if (!s || n < 1 || m1 < 1 || m1 > kGameMaxM1 || m2 < 1 || m2 > kGameMaxM2 || !row_ptr || !col || !prob ||
         !reward || !(mu > 0.0 && (mu < 1.0 || (mu == 1.0 && s->opt.game_solver == 1)))) {
         set_last_error("set_game: invalid argument");
         return GS_EINVAL;
@@ -169,7 +169,7 @@ gs_status gamesolve_set_game_batch(gs_solver* s, int32_t count, int32_t m1, int3
                                    const int64_t* state_offsets, const int64_t* row_ptr,
                                    const int32_t* col, const double* prob, const double* reward,
                                    const double* mu) {
-    if (!s || count < 1 || m1 < 1 || m1 > 8 || m2 < 1 || m2 > 8 || !state_offsets || !row_ptr ||
+    if (!s || count < 1 || m1 < 1 || m1 > kGameMaxM1 || m2 < 1 || m2 > kGameMaxM2 || !state_offsets || !row_ptr ||
         !col || !prob || !reward || !mu) {
         set_last_error("set_game_batch: invalid argument");
         return GS_EINVAL;

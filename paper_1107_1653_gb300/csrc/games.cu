@@ -169,7 +169,7 @@ __device__ __noinline__ int improve_state_exact(const Game& G, const BatchOut& O
     const int64_t x = G.x0 + i;
     const int64_t rb = G.row0 + i * G.R;
     const int acur = O.alpha[x];
-    double Fa[8];
+    double Fa[kGameMaxM1];
     int changed = 0;
     for (int a = 0; a < m1; ++a) {
         if (mode == 1 && a != acur) continue;
@@ -216,13 +216,16 @@ __device__ __noinline__ int improve_state_exact(const Game& G, const BatchOut& O
 // Returns the number of changed policy entries; *res gets |F(v) - v| (outer).
 __device__ int improve_state(const Game& G, const BatchOut& O, int mode, int64_t i, double tau,
                              float tauf, float vmaxf, const double* v, double* res) {
+    // games with many MAX actions (fine discretisations of continuous action
+    // sets) take the float64 decisions directly
+    if (G.T.m1 > kScreenMaxM1) return improve_state_exact(G, O, mode, i, tau, v, res);
     const int m1 = G.T.m1, m2 = G.T.m2;
     const int64_t x = G.x0 + i;
     const int64_t rb = G.row0 + i * G.R;
     const int acur = O.alpha[x];
     const float* v32 = O.v32 + G.x0;
-    float Fa[8];
-    int bsel[8];
+    float Fa[kScreenMaxM1];
+    int bsel[kScreenMaxM1];
     bool sure = true;
     for (int a = 0; a < m1 && sure; ++a) {
         if (mode == 1 && a != acur) continue;

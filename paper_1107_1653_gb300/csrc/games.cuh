@@ -70,6 +70,13 @@ struct GridWork {
     GridBarrier* bar;    // zeroed before the launch
 };
 
+// Action counts: MAX at most kGameMaxM1, MIN at most kGameMaxM2 (policies are
+// bytes).  Games with at most kScreenMaxM1 MAX actions take the float32-screened
+// improvement, larger ones the float64 decisions directly.
+constexpr int kGameMaxM1 = 64;
+constexpr int kGameMaxM2 = 255;
+constexpr int kScreenMaxM1 = 8;
+
 // Largest game the one-block-per-game kernel takes (its three correction
 // vectors live in shared memory).
 constexpr int kGameMaxStatesMixed = 16384;

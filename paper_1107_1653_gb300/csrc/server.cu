@@ -223,7 +223,7 @@ gs_status gamesolve_server_submit(gs_server* S, const gs_request* req, int64_t* 
             return GS_EINVAL;
         }
     } else if (req->kind == 2) {
-        if (req->n < 1 || req->m1 < 1 || req->m1 > 8 || req->m2 < 1 || req->m2 > 8 ||
+        if (req->n < 1 || req->m1 < 1 || req->m1 > kGameMaxM1 || req->m2 < 1 || req->m2 > kGameMaxM2 ||
             !req->row_ptr || !req->col || !req->prob || !req->reward) {
             set_last_error("server_submit: invalid game");
             return GS_EINVAL;

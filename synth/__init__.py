@@ -296,3 +296,66 @@ def two_stop_tables(points: int):
                 row_ptr.append(len(cols))
     return (n, 2, 2, np.array(row_ptr, np.int64), np.array(cols, np.int32),
             np.array(probs, np.float64), np.array(rews, np.float64), 1.0)
+
+
+def iex1_tables(side: int, Ka: int, Kb: int, lo: float = -0.25, hi: float = 1.25):
+    """The Isaacs example of Sec. 6.1 (Eq. (Iex1d), lambda = 0, so mu = 1) with
+    finite action sets, as CSR tables (gamesolve_set_game layout).  Problem
+    data only.  h = 1/(side+1); MAX's actions a_k = (cos 2 pi k/Ka, sin 2 pi
+    k/Ka); MIN's actions the Kb x Kb grid over [lo, hi]^2 (index j1 * Kb + j2).
+    With d = a - b and c = 4 + h|d1| + h|d2|, the moves east / west / north /
+    south have probabilities (1 + h max(d1,0))/c, (1 + h max(-d1,0))/c,
+    (1 + h max(d2,0))/c, (1 + h max(-d2,0))/c; a move onto the boundary leaves
+    the state space and its probability times sin x1 sin x2 there joins the
+    reward h^2 (|b|^2/2 + f(x))/c, f = 2u - |grad u| + |grad u|^2/2 for
+    u = sin x1 sin x2.  Rows hold the interior moves in the order east, west,
+    north, south.
+
+    Returns (n, m1, m2, row_ptr, col, prob, reward, mu)."""
+    h = 1.0 / (side + 1)
+    n = side * side
+    t = 2.0 * np.pi * np.arange(Ka) / Ka
+    a1, a2 = np.cos(t), np.sin(t)
+    g = lo + (hi - lo) * np.arange(Kb) / (Kb - 1)
+    b1 = np.repeat(g, Kb)
+    b2 = np.tile(g, Kb)
+    m1, m2 = Ka, Kb * Kb
+    d1 = a1[:, None] - b1[None, :]
+    d2 = a2[:, None] - b2[None, :]
+    c = 4.0 + h * (np.abs(d1) + np.abs(d2))
+    moves = [((1, 0), (1.0 + h * np.maximum(d1, 0.0)) / c), ((-1, 0), (1.0 + h * np.maximum(-d1, 0.0)) / c),
+             ((0, 1), (1.0 + h * np.maximum(d2, 0.0)) / c), ((0, -1), (1.0 + h * np.maximum(-d2, 0.0)) / c)]
+    x = np.arange(n)
+    i1, i2 = x % side, x // side
+    x1, x2 = (i1 + 1) * h, (i2 + 1) * h
+    u = np.sin(x1) * np.sin(x2)
+    gn = np.sqrt((np.cos(x1) * np.sin(x2)) ** 2 + (np.sin(x1) * np.cos(x2)) ** 2)
+    f = 2.0 * u - gn + 0.5 * gn * gn
+    half_b2 = 0.5 * (b1 * b1 + b2 * b2)
+    reward = (h * h / c)[None] * (half_b2[None, None, :] + f[:, None, None])     # [n, m1, m2]
+    cols, probs, count = [], [], np.zeros(n, np.int64)
+    for (s1, s2), p in moves:
+        j1, j2 = i1 + s1, i2 + s2
+        inside = (j1 >= 0) & (j1 < side) & (j2 >= 0) & (j2 < side)
+        psi = np.sin((j1 + 1) * h) * np.sin((j2 + 1) * h)
+        reward += np.where(inside, 0.0, psi)[:, None, None] * p[None]
+        cols.append(np.where(inside, j2 * side + j1, -1))
+        probs.append(p)
+        count += inside
+    # rows in (x, a, b) order, each with its interior moves
+    k_of = count                                             # moves per row of state x
+    row_len = np.repeat(k_of, m1 * m2)
+    row_ptr = np.concatenate([[0], np.cumsum(row_len)]).astype(np.int64)
+    col = np.empty(int(row_ptr[-1]), np.int32)
+    prob = np.empty(int(row_ptr[-1]), np.float64)
+    pos = row_ptr[:-1].reshape(n, m1, m2).copy()
+    for cset, p in zip(cols, probs):
+        ok = cset >= 0
+        xs = np.nonzero(ok)[0]
+        if len(xs) == 0:
+            continue
+        dst = pos[xs]                                        # [k, m1, m2]
+        col[dst.reshape(-1)] = np.repeat(cset[xs], m1 * m2)
+        prob[dst.reshape(-1)] = np.broadcast_to(p[None], (len(xs), m1, m2)).reshape(-1)
+        pos[xs] += 1
+    return (n, m1, m2, row_ptr, col, prob, reward.reshape(-1), 1.0)

@@ -134,3 +134,35 @@ def test_algebraic_famg_on_the_obstacle_grid(gs):
         s.solve()
         lv = s.level_stats()
     assert lv[-1][0] == n and all(lv[k][0] < lv[k + 1][0] for k in range(len(lv) - 1))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("side", [15, 31])
+def test_continuous_action_isaacs_matches_oracle(gs, side, prec):
+    """The Isaacs example of Sec. 6.1 with continuous action sets (NEXT-3),
+    read as fine discretisations of them (16 directions on MAX's unit circle,
+    a 9 x 9 grid of MIN's b), undiscounted (lambda = 0): the tables path with
+    algebraic multigrid against the oracle's own generator and policy
+    iteration."""
+    from oracle.iex1 import iex1_game
+    key = ("iex1", side)
+    if key not in _ORACLE:
+        _ORACLE[key] = oracle.policy_iteration(iex1_game(side, 16, 9))
+    ref = _ORACLE[key]
+    v, a, b, st = solve_tables(gs, synth.iex1_tables(side, 16, 9), precision=prec)
+    assert st["converged"] == 1 and st["outer"] == ref.outer
+    check(v, a, b, ref, TOL[prec])
+
+
+def test_continuous_action_isaacs_approaches_the_exact_solution(gs):
+    """On finer grids (and a finer MIN grid) the GPU value approaches the
+    paper's exact solution sin x1 sin x2 (Sec. 6.1)."""
+    from oracle.iex1 import exact_value
+    errs = []
+    for side, Ka, Kb in ((31, 16, 9), (63, 32, 13)):
+        v, _, _, st = solve_tables(gs, synth.iex1_tables(side, Ka, Kb), precision="mixed")
+        assert st["converged"] == 1
+        h = 1.0 / (side + 1)
+        idx = np.arange(side * side)
+        errs.append(np.max(np.abs(v - exact_value((idx % side + 1) * h, (idx // side + 1) * h))))
+    assert errs[1] < errs[0] < 3e-4, errs

@@ -287,3 +287,25 @@ def test_fmg_level_counts_match_oracle(gs, variant):
             got = s.level_stats()
         assert st["converged"] == 1
         assert got == want, (prec, got, want)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
+@pytest.mark.parametrize("side,variant,cyc", [(63, 0, (1, 1)), (255, 1, (1, 2)), (1023, 0, (1, 2)),
+                                              (255, 0, (2, 1))])
+def test_tiled_cycles_match_per_colour_kernel(gs, side, variant, cyc, prec):
+    """The tiled V-cycle kernel (default) and the one-phase-per-colour kernel
+    run the same arithmetic per point: the same policy-fixed solve reaches the
+    same value (to rounding of a different contraction order) in the same
+    number of cycles."""
+    rng = np.random.default_rng(side + variant)
+    n, m1 = side * side, 5 if variant else 4
+    alpha = rng.integers(0, m1, n).astype(np.uint8)
+    beta = rng.integers(0, 4, (n, m1)).astype(np.uint8)
+    out = {}
+    for ck in (0, 1):
+        with gs.GameSolver(precision=prec, cycle_kernel=ck, nu1=cyc[0], nu2=cyc[1]) as s:
+            s.set_isaacs_grid(side, variant, 3)
+            out[ck] = s.policy_solve(alpha, beta)
+    (w0, s0), (w1, s1) = out[0], out[1]
+    assert s0["cycles"] == s1["cycles"], (s0, s1)
+    assert rel_err(w0, w1) <= 1e-13

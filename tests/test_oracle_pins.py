@@ -463,3 +463,48 @@ def test_two_stop_tables_are_the_oracles_game():
         (pa, ra), (pb, rb) = ours[key], ref[key]
         assert pa == pb, key
         assert abs(ra - rb) <= 1e-15, key
+
+
+# ----------------------------------------------------------------- Isaacs example with continuous actions
+def test_iex1_tables_are_the_oracles_game():
+    """synth's tables of the Sec. 6.1 example with discretised action sets
+    (Eq. (Iex1d)) describe the oracle's game row by row."""
+    from oracle.iex1 import iex1_game
+    n, m1, m2, rp, col, prob, rew, mu = synth.iex1_tables(5, 4, 3)
+    ours = _rows_as_sets(game_from_csr(n, m1, m2, rp, col, prob, rew, mu))
+    ref_game = iex1_game(5, 4, 3)
+    ref = _rows_as_sets(ref_game)
+    assert mu == ref_game.mu == 1.0
+    for key in ref:
+        (pa, ra), (pb, rb) = ours[key], ref[key]
+        assert [y for y, _ in pa] == [y for y, _ in pb], key
+        assert np.allclose([p for _, p in pa], [p for _, p in pb], rtol=0, atol=1e-16), key
+        assert abs(ra - rb) <= 1e-16 + 1e-14 * abs(rb), key
+
+
+def test_iex1_rows_are_stochastic_up_to_the_boundary():
+    """Every (a, b) row sums to one when all four neighbours are interior and
+    to less near the boundary (Sec. 6.1's remark), with non-negative weights."""
+    from oracle.iex1 import iex1_game
+    g = iex1_game(7, 8, 5)
+    tot = g.prob.sum(axis=-1)
+    interior = (g.succ >= 0).all(axis=-1)
+    assert np.all(g.prob >= 0)
+    assert np.allclose(tot[interior], 1.0, atol=1e-15)
+    assert np.all(tot[~interior] < 1.0)
+
+
+def test_iex1_converges_to_the_exact_solution():
+    """The discrete value approaches the paper's exact solution sin x1 sin x2
+    as the grid and the action sets refine (Sec. 6.1); policy iteration needs
+    a handful of MAX steps, as the paper's Table 1 reports (3 outer steps)."""
+    from oracle.iex1 import iex1_game, exact_value
+    errs = []
+    for side, Ka, Kb in ((7, 8, 5), (15, 16, 9), (15, 32, 13)):
+        res = oracle.policy_iteration(iex1_game(side, Ka, Kb))
+        assert res.converged and res.outer <= 5
+        h = 1.0 / (side + 1)
+        idx = np.arange(side * side)
+        u = exact_value((idx % side + 1) * h, (idx // side + 1) * h)
+        errs.append(np.max(np.abs(res.v - u)))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 3e-4, errs
