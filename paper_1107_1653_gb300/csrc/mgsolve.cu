@@ -5,6 +5,7 @@
 // out of shared memory.  Every grid-wide wait is bounded in time; a wait that
 // gives up sets an error flag and the kernels return.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "gridsync.cuh"
@@ -22,17 +23,27 @@ constexpr unsigned kProfCap = 1u << 16;
 __device__ unsigned long long g_prof_ts[kProfCap];
 __device__ int g_prof_tag[kProfCap];
 __device__ unsigned g_prof_n;
+__device__ __forceinline__ void prof_record(int tag) {
+    const unsigned k = atomicAdd(&g_prof_n, 1u);
+    if (k < kProfCap) {
+        g_prof_ts[k] = global_ns();
+        g_prof_tag[k] = tag;
+    }
+}
 __device__ __forceinline__ void prof_mark(int tag) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const unsigned k = g_prof_n++;
-        if (k < kProfCap) {
-            g_prof_ts[k] = global_ns();
-            g_prof_tag[k] = tag;
-        }
+    if (blockIdx.x == 0 && threadIdx.x == 0) prof_record(tag);
+}
+// Blocks 1 and the last one record when their own work in a phase ended
+// (tag + 100000, tag + 200000), before they wait at the grid barrier.
+__device__ __forceinline__ void prof_done(int tag) {
+    if (blockIdx.x == 1 || blockIdx.x == gridDim.x - 1) {
+        __syncthreads();
+        if (threadIdx.x == 0) prof_record(tag + (blockIdx.x == 1 ? 100000 : 200000));
     }
 }
 #else
 __device__ __forceinline__ void prof_mark(int) {}
+__device__ __forceinline__ void prof_done(int) {}
 #endif
 
 __device__ __forceinline__ int colour_ox(int c) { return c == 0 || c == 3 ? 1 : 0; }
@@ -42,9 +53,11 @@ __device__ __forceinline__ int colour_oy(int c) { return c == 0 || c == 2 ? 1 : 
 // One colour of the C/F relaxation.  Level 0 (5-point) is red-black: colour 0
 // = the C points and the cell corners (mutually uncoupled), colour 1 = the
 // edge F points.  9-point levels: C points, then corners, x-edges, y-edges.
-template <typename T>
-__device__ void relax_fine(const L0Op<T>& op, const LevelArgs& L, int c, bool zero, size_t start,
-                           size_t stride) {
+// The zero-start flag is a template parameter: a run-time flag guarding the
+// neighbour loads kept the compiler from issuing a batch's loads together,
+// which doubled a phase's time.
+template <typename T, bool zero>
+__device__ void relax_fine_z(const L0Op<T>& op, const LevelArgs& L, int c, size_t start, size_t stride) {
     T* __restrict__ u = (T*)L.u;
     const T* __restrict__ f = (const T*)L.f;
     const int side = L.side, hs = (side + 1) / 2;
@@ -72,6 +85,13 @@ __device__ void relax_fine(const L0Op<T>& op, const LevelArgs& L, int c, bool ze
         const int j = (int)dv.divmod(t, &r), i = ((j + c) & 1) + 2 * (int)r;
         if (i < side) u[(size_t)j * side + i] = op.relaxed(f, u, i, j, zero);
     }
+}
+
+template <typename T>
+__device__ void relax_fine(const L0Op<T>& op, const LevelArgs& L, int c, bool zero, size_t start,
+                           size_t stride) {
+    if (zero) relax_fine_z<T, true>(op, L, c, start, stride);
+    else relax_fine_z<T, false>(op, L, c, start, stride);
 }
 
 // The last colour of the last fine relaxation fused with the float64 update
@@ -116,8 +136,8 @@ __device__ void relax_fine_update(const L0Op<float>& op, const LevelArgs& L, dou
     }
 }
 
-template <typename T, typename W>
-__device__ void relax_coarse(const LevelArgs& L, int c, bool zero, size_t start, size_t stride) {
+template <typename T, typename W, bool zero>
+__device__ void relax_coarse_z(const LevelArgs& L, int c, size_t start, size_t stride) {
     const L9Op<T, W> op{(const W*)L.A, L.n, L.side};
     T* u = (T*)L.u;
     const T* f = (const T*)L.f;
@@ -141,6 +161,12 @@ __device__ void relax_coarse(const LevelArgs& L, int c, bool zero, size_t start,
         const int j = oy + 2 * (int)dv.divmod(t, &r), i = ox + 2 * (int)r;
         u[(size_t)j * L.side + i] = op.relaxed(f, u, i, j, zero);
     }
+}
+
+template <typename T, typename W>
+__device__ void relax_coarse(const LevelArgs& L, int c, bool zero, size_t start, size_t stride) {
+    if (zero) relax_coarse_z<T, W, true>(L, c, start, stride);
+    else relax_coarse_z<T, W, false>(L, c, start, stride);
 }
 
 // f_{l+1} = R (f_l - A_l u_l) with the fine residuals formed on the fly;
@@ -921,68 +947,7 @@ __device__ __forceinline__ void batched_rect(int x0, int x1, int y0, int y1, Loa
     }
 }
 
-// Shared-memory forms of the level operators (same arithmetic as L0Op / L9Op).
-struct TFine32 {
-    const IsaacsConsts* K;
-    const uint8_t* code;   // staged codes
-    int side, w;
-    __device__ __forceinline__ float relaxed(const float* f, const float* u, int k, int i, int j) const {
-        const int c = code[k];
-        const float* am = K->amf[c];
-        float diag = l0_rowsum_f(K, c, i, j, side), s = f[k];
-        if (i > 0) { diag -= am[1]; s -= am[1] * u[k - 1]; }
-        if (i + 1 < side) { diag -= am[2]; s -= am[2] * u[k + 1]; }
-        if (j > 0) { diag -= am[3]; s -= am[3] * u[k - w]; }
-        if (j + 1 < side) { diag -= am[4]; s -= am[4] * u[k + w]; }
-        return s / diag;
-    }
-    __device__ __forceinline__ float diag(int k, int i, int j) const {
-        const int c = code[k];
-        const float* am = K->amf[c];
-        float d = l0_rowsum_f(K, c, i, j, side);
-        if (i > 0) d -= am[1];
-        if (i + 1 < side) d -= am[2];
-        if (j > 0) d -= am[3];
-        if (j + 1 < side) d -= am[4];
-        return d;
-    }
-    __device__ __forceinline__ float resid(const float* f, const float* u, int k, int i, int j) const {
-        const int c = code[k];
-        const float* am = K->amf[c];
-        const float ux = u[k];
-        float Au = l0_rowsum_f(K, c, i, j, side) * ux;
-        if (i > 0) Au += am[1] * (u[k - 1] - ux);
-        if (i + 1 < side) Au += am[2] * (u[k + 1] - ux);
-        if (j > 0) Au += am[3] * (u[k - w] - ux);
-        if (j + 1 < side) Au += am[4] * (u[k + w] - ux);
-        return f[k] - Au;
-    }
-};
-
-struct TFine64 {
-    const IsaacsConsts* K;
-    const uint8_t* code;
-    int side, w;
-    // fx - (A v)(i, j): five fused multiply-adds, boundary couplings times +0
-    __device__ __forceinline__ double resid(double fx, const double* v, int k, int i, int j) const {
-        const double* am = K->am[code[k]];
-        double r = fma(-am[0], v[k], fx);
-        r = fma(-am[1], load_or_zero(v, (size_t)(k - 1), i > 0), r);
-        r = fma(-am[2], load_or_zero(v, (size_t)(k + 1), i + 1 < side), r);
-        r = fma(-am[3], load_or_zero(v, (size_t)(k - w), j > 0), r);
-        return fma(-am[4], load_or_zero(v, (size_t)(k + w), j + 1 < side), r);
-    }
-    __device__ __forceinline__ double relaxed(const double* f, const double* u, int k, int i, int j) const {
-        const double* am = K->am[code[k]];
-        double s = f[k];
-        if (i > 0) s -= am[1] * u[k - 1];
-        if (i + 1 < side) s -= am[2] * u[k + 1];
-        if (j > 0) s -= am[3] * u[k - w];
-        if (j + 1 < side) s -= am[4] * u[k + w];
-        return s / am[0];
-    }
-};
-
+// Shared-memory form of the 9-point level operator (same arithmetic as L9Op).
 // 9-point level in shared memory: A[d * wh + k] in the cycle's type (float32
 // rows in leakage form: row sum in slot 0).
 template <typename T>
@@ -1213,248 +1178,6 @@ __device__ __noinline__ void tile_up(const SolveArgs& a, int l, char* smem, int 
     }
 }
 
-// Buffers of the finest level's phase: what it reads and what it writes.
-// Other tiles stage their halos from the inputs while a tile writes its own
-// points, so outputs never alias inputs (the kernel swaps them each cycle).
-struct FineBufs {
-    const double* v_in;
-    const void* e_in;   // mixed: correction e after the pre-smoothing
-    const void* r_in;   // mixed: its right-hand side (float64 residual, rounded)
-    double* v_out;      // mixed: v + e after the post-smoothing; float64: v after it
-    void* e_out;        // mixed: next correction after the pre-smoothing
-    void* r_out;
-    double* v_pre;      // float64: v after the next pre-smoothing
-};
-
-// The finest level's phase, mixed path (float32 correction e of the float64
-// value v).  full: prolongation, post-smoothing and v += e first (else the
-// launch's first residual evaluation, e = 0).  Then the float64 residual
-// r = rhs - A v with |r|_inf, |v|_inf into out slot `slot`, r rounded to
-// float32 as the correction's right-hand side, the pre-smoothing from e = 0
-// (first colour e = r / diag) and the restriction into level 1.
-template <typename W>
-__device__ void tile_fine_mixed(const SolveArgs& a, bool full, int slot, const FineBufs& B,
-                                char* smem, int worker, int nworkers) {
-    const LevelArgs& L = a.L[0];
-    const LevelArgs& C = a.L[1];
-    const int sf = L.side, sc = L.sc;
-    const int K2 = full ? 2 * a.nu2 : 0;
-    const int K1 = a.nu1 > 0 ? 2 * a.nu1 - 1 : 0;
-    const int H = 2 + K1 + K2;
-    const bool zero_uc = a.tail == 1;
-    const int ntiles = tile_count(a.tc[0], sc);
-    const W* gP = (const W*)L.P;
-    const float* guc = (const float*)(a.tail == 1 ? C.u : C.u2);
-    const float* ge = (const float*)B.e_in;
-    const float* gr = (const float*)B.r_in;
-    float* ge_out = (float*)B.e_out;
-    float* gr_out = (float*)B.r_out;
-    unsigned long long rm = 0, vm = 0;
-    for (int k = worker; k < ntiles; k += nworkers) {
-        const Tile t = make_tile(k, a.tc[0], sc, sf, H);
-        const int wh = t.w * t.h;
-        double* v = (double*)smem;
-        float* e = (float*)(v + wh);
-        float* f = e + wh;
-        uint8_t* code = (uint8_t*)(f + wh);
-        for_rect(t.gx0, t.gx1, t.gy0, t.gy1, [&](int i, int j) {
-            const size_t x = (size_t)j * sf + i;
-            const int q = t.loc(i, j);
-            code[q] = a.code[x];
-            v[q] = B.v_in[x];
-            if (full) {
-                e[q] = ge[x] + prolonged<float, W>(gP, guc, sc, i, j);
-                f[q] = gr[x];
-            }
-        });
-        __syncthreads();
-        const TFine32 op{a.K, code, sf, t.w};
-        Valid vr{t.gx0, t.gx1, t.gy0, t.gy1};
-        if (full) {
-            for (int s = 0; s < a.nu2; ++s)
-                for (int c = 0; c < 2; ++c) {
-                    vr.shrink(sf);
-                    for_redblack(vr, c, [&](int i, int j) {
-                        const int q = t.loc(i, j);
-                        e[q] = op.relaxed(f, e, q, i, j);
-                    });
-                    __syncthreads();
-                }
-            for_rect(vr.x0, vr.x1, vr.y0, vr.y1, [&](int i, int j) {
-                const int q = t.loc(i, j);
-                v[q] += f32_to_f64(e[q]);
-            });
-            __syncthreads();
-        }
-        // float64 residual of the stopping test on a region one narrower
-        vr.shrink(sf);
-        const TFine64 op64{a.K, code, sf, t.w};
-        const bool relax0 = a.nu1 > 0;
-        for_rect(vr.x0, vr.x1, vr.y0, vr.y1, [&](int i, int j) {
-            const int q = t.loc(i, j);
-            const double r = op64.resid(a.rhs[(size_t)j * sf + i], v, q, i, j);
-            const float rf = f64_to_f32(r);
-            f[q] = rf;
-            if (i >= t.ox0 && i < t.ox1 && j >= t.oy0 && j < t.oy1) {
-                rm = max(rm, abs_bits(r));
-                vm = max(vm, abs_bits(v[q]));
-            }
-            e[q] = relax0 && ((i + j) & 1) == 0 ? rf / op.diag(q, i, j) : 0.0f;
-        });
-        __syncthreads();
-        // pre-smoothing: the first colour was the pointwise e = r / diag
-        for (int s = 0; s < a.nu1; ++s)
-            for (int c = 0; c < 2; ++c) {
-                if (s == 0 && c == 0) continue;
-                vr.shrink(sf);
-                for_redblack(vr, c, [&](int i, int j) {
-                    const int q = t.loc(i, j);
-                    e[q] = op.relaxed(f, e, q, i, j);
-                });
-                __syncthreads();
-            }
-        // residuals of the correction at fine points [2 I0, 2 I1] x [2 J0, 2 J1]
-        const int rx1 = min(sf, 2 * t.I1 + 1), ry1 = min(sf, 2 * t.J1 + 1);
-        const int rw = 2 * (t.I1 - t.I0) + 1;
-        float* r = (float*)(code + ((wh + 15) & ~15));
-        for_rect(t.ox0, rx1, t.oy0, ry1, [&](int i, int j) {
-            r[(j - t.oy0) * rw + (i - t.ox0)] = op.resid(f, e, t.loc(i, j), i, j);
-        });
-        // the tile's own points
-        for_rect(t.ox0, t.ox1, t.oy0, t.oy1, [&](int i, int j) {
-            const size_t x = (size_t)j * sf + i;
-            const int q = t.loc(i, j);
-            if (full) B.v_out[x] = v[q];
-            ge_out[x] = e[q];
-            gr_out[x] = f[q];
-        });
-        __syncthreads();
-        tile_restrict<float, W>(t, r, rw, L, C, zero_uc);
-        __syncthreads();
-    }
-    rm = warp_max_u64(rm);
-    vm = warp_max_u64(vm);
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(&a.out->rmax[slot], rm);
-        atomicMax(&a.out->vmax[slot], vm);
-    }
-}
-
-// The finest level's phase, float64 path (the cycle relaxes v itself,
-// right-hand side rhs): full: prolongation and post-smoothing, the result to
-// v_out; the residual of the stopping test at the tile's own points; the
-// pre-smoothing (to v_pre) and the restriction.
-__device__ void tile_fine_fp64(const SolveArgs& a, bool full, int slot, const FineBufs& B,
-                               char* smem, int worker, int nworkers) {
-    const LevelArgs& L = a.L[0];
-    const LevelArgs& C = a.L[1];
-    const int sf = L.side, sc = L.sc;
-    const int K2 = full ? 2 * a.nu2 : 0;
-    const int K1 = 2 * a.nu1;
-    const int H = 1 + K1 + K2;
-    const bool zero_uc = a.tail == 1;
-    const int ntiles = tile_count(a.tc[0], sc);
-    const double* gP = (const double*)L.P;
-    const double* guc = (const double*)(a.tail == 1 ? C.u : C.u2);
-    unsigned long long rm = 0, vm = 0;
-    for (int k = worker; k < ntiles; k += nworkers) {
-        const Tile t = make_tile(k, a.tc[0], sc, sf, H);
-        const int wh = t.w * t.h;
-        double* v = (double*)smem;
-        double* f = v + wh;
-        uint8_t* code = (uint8_t*)(f + wh);
-        for_rect(t.gx0, t.gx1, t.gy0, t.gy1, [&](int i, int j) {
-            const size_t x = (size_t)j * sf + i;
-            const int q = t.loc(i, j);
-            code[q] = a.code[x];
-            v[q] = full ? B.v_in[x] + prolonged<double, double>(gP, guc, sc, i, j) : B.v_in[x];
-            f[q] = a.rhs[x];
-        });
-        __syncthreads();
-        const TFine64 op{a.K, code, sf, t.w};
-        Valid vr{t.gx0, t.gx1, t.gy0, t.gy1};
-        for (int s = 0; s < (full ? a.nu2 : 0); ++s)
-            for (int c = 0; c < 2; ++c) {
-                vr.shrink(sf);
-                for_redblack(vr, c, [&](int i, int j) {
-                    const int q = t.loc(i, j);
-                    v[q] = op.relaxed(f, v, q, i, j);
-                });
-                __syncthreads();
-            }
-        for_rect(t.ox0, t.ox1, t.oy0, t.oy1, [&](int i, int j) {
-            const int q = t.loc(i, j);
-            rm = max(rm, abs_bits(op.resid(f[q], v, q, i, j)));
-            vm = max(vm, abs_bits(v[q]));
-            if (full) B.v_out[(size_t)j * sf + i] = v[q];
-        });
-        __syncthreads();
-        for (int s = 0; s < a.nu1; ++s)
-            for (int c = 0; c < 2; ++c) {
-                vr.shrink(sf);
-                for_redblack(vr, c, [&](int i, int j) {
-                    const int q = t.loc(i, j);
-                    v[q] = op.relaxed(f, v, q, i, j);
-                });
-                __syncthreads();
-            }
-        const int rx1 = min(sf, 2 * t.I1 + 1), ry1 = min(sf, 2 * t.J1 + 1);
-        const int rw = 2 * (t.I1 - t.I0) + 1;
-        double* r = (double*)(code + ((wh + 15) & ~15));
-        for_rect(t.ox0, rx1, t.oy0, ry1, [&](int i, int j) {
-            const int q = t.loc(i, j);
-            r[(j - t.oy0) * rw + (i - t.ox0)] = op.resid(f[q], v, q, i, j);
-        });
-        for_rect(t.ox0, t.ox1, t.oy0, t.oy1,
-                 [&](int i, int j) { B.v_pre[(size_t)j * sf + i] = v[t.loc(i, j)]; });
-        __syncthreads();
-        tile_restrict<double, double>(t, r, rw, L, C, zero_uc);
-        __syncthreads();
-    }
-    rm = warp_max_u64(rm);
-    vm = warp_max_u64(vm);
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(&a.out->rmax[slot], rm);
-        atomicMax(&a.out->vmax[slot], vm);
-    }
-}
-
-template <typename T, typename W>
-__device__ __noinline__ void tile_fine(const SolveArgs& a, bool full, int slot, const FineBufs& B,
-                                          char* smem, int worker, int nworkers) {
-    if constexpr (sizeof(T) == 4) tile_fine_mixed<W>(a, full, slot, B, smem, worker, nworkers);
-    else tile_fine_fp64(a, full, slot, B, smem, worker, nworkers);
-}
-
-// Buffers of the finest level's phase for set `cur` (see FineBufs).
-// Mixed: the sets (v, e, r) = (a.v, L0.u, L0.f) and (a.v2, a.e2, a.r2); the
-// first phase reads v from set 0 and writes e, r there; a full phase reads
-// set cur and writes set cur ^ 1.  Float64: a.v always receives the result
-// after the post-smoothing; the pre-smoothed v alternates between a.v2 and
-// a.v3 (cur), the first phase reading a.v.
-template <typename T>
-__device__ __forceinline__ FineBufs fine_bufs(const SolveArgs& a, bool full, int cur) {
-    FineBufs B{};
-    if constexpr (sizeof(T) == 4) {
-        double* vs[2] = {a.v, a.v2};
-        void* es[2] = {a.L[0].u, a.e2};
-        void* rs[2] = {a.L[0].f, a.r2};
-        const int in = cur, out = full ? cur ^ 1 : cur;
-        B.v_in = vs[in];
-        B.e_in = es[in];
-        B.r_in = rs[in];
-        B.v_out = vs[out];
-        B.e_out = es[out];
-        B.r_out = rs[out];
-    } else {
-        double* ys[2] = {a.v2, a.v3};
-        B.v_in = full ? ys[cur] : a.v;
-        B.v_out = a.v;
-        B.v_pre = full ? ys[cur ^ 1] : ys[0];
-    }
-    return B;
-}
-
 // First post-smoothing colour of the finest level fused with the
 // prolongation: a colour-0 point's Gauss-Seidel value needs only its four
 // neighbours (colour 1), taken as u + P u_c on the fly; the colour-0 points'
@@ -1486,6 +1209,13 @@ __device__ __noinline__ void relax_fine_prolonged(const SolveArgs& a, const T* u
     }
 }
 
+// Where level l's values after its post-smoothing are, in the tiled kernel:
+// u2 for a tiled level (its neighbours stage u while it writes), u for the
+// tail's top level and for the large coarse levels relaxed one phase per colour.
+__device__ __forceinline__ const void* final_u(const SolveArgs& a, int l) {
+    return l == a.tail || l < a.tile_from ? a.L[l].u : a.L[l].u2;
+}
+
 // The tail's V-cycle and the grid-wide phases of the finest level as calls of
 // their own (the tiled kernel's register budget is that of two blocks per SM).
 template <typename T, typename W>
@@ -1499,6 +1229,24 @@ __device__ __noinline__ void fine_relax(const SolveArgs& a, int c, bool zero, si
 template <typename T, typename W>
 __device__ __noinline__ void fine_restrict(const SolveArgs& a, size_t gt, size_t gs) {
     restrict_level<T, W>(a, a.L[0], a.L[1], 0, 1 < a.tail && 1 < a.nlev - 1 && sweeps_pre(a, 1) > 0, gt, gs);
+}
+// One colour of a large coarse level l (first sweep's first colour excluded:
+// the restriction into l did it), its restriction into l + 1, and the
+// prolongation into it from l + 1.
+template <typename T, typename W>
+__device__ __noinline__ void coarse_relax(const SolveArgs& a, int l, int c, size_t gt, size_t gs) {
+    relax_level<T, W>(a, a.L[l], l, c, false, gt, gs);
+}
+template <typename T, typename W>
+__device__ __noinline__ void coarse_restrict(const SolveArgs& a, int l, size_t gt, size_t gs) {
+    restrict_level<T, W>(a, a.L[l], a.L[l + 1], l,
+                         l + 1 < a.tail && l + 1 < a.nlev - 1 && sweeps_pre(a, l + 1) > 0, gt, gs);
+}
+template <typename T, typename W>
+__device__ __noinline__ void coarse_prolong(const SolveArgs& a, int l, size_t gt, size_t gs) {
+    LevelArgs C = a.L[l + 1];
+    C.u = (void*)final_u(a, l + 1);
+    prolong_phase<T, W>(a.L[l], C, gt, gs);
 }
 __device__ __noinline__ void fine_check(const SolveArgs& a, int slot, size_t gt, size_t gs) {
     check_phase(a, slot, gt, gs);
@@ -1519,13 +1267,11 @@ __global__ void __launch_bounds__(kMGThreads, 2) k_mg_cycles_tiled(const __grid_
     if (!G.sync()) return;   // set-up complete (and error state shared)
     prof_mark(8000);
     double* inv = a.inv;
-    int slot = 0, cur = 0;
+    int slot = 0;
     // block 0 stages the tail while the others take the first residual check
-    // (with the first cycle's pre-smoothing and restriction when the finest
-    // level is tiled)
     if (blockIdx.x == 0) stage_tail<T, W>(a, smem_t, tl, &inv);
-    else if (a.tile_fine) tile_fine<T, W>(a, false, slot, fine_bufs<T>(a, false, cur), smem_t, worker, nworkers);
     else fine_check(a, slot, gt - blockDim.x, gs - blockDim.x);
+    prof_done(6000);
     if (!G.sync()) return;
     prof_mark(6000);
     double prev = 0.0, res0 = 0.0;
@@ -1552,22 +1298,13 @@ __global__ void __launch_bounds__(kMGThreads, 2) k_mg_cycles_tiled(const __grid_
                 a.out->res = res;
                 a.out->vmax_final = vm;
             }
-            if constexpr (sizeof(T) == 4) {
-                // the last value went to the second set: copy it home
-                if (a.tile_fine && cur == 1) {
-                    const size_t n = a.L[0].n;
-                    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-                         x += (size_t)gridDim.x * blockDim.x)
-                        a.v[x] = a.v2[x];
-                }
-            }
             return;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.out->rmax[slot ^ 1] = 0ull;
             a.out->vmax[slot ^ 1] = 0ull;
         }
-        if (!a.tile_fine) {
+        {
             // finest level, one phase per colour: pre-smoothing (the first
             // colour from the zero start was done by the residual check in
             // the mixed path), then the restriction
@@ -1577,39 +1314,61 @@ __global__ void __launch_bounds__(kMGThreads, 2) k_mg_cycles_tiled(const __grid_
                 for (int c = 0; c < 2; ++c) {
                     if (done0 && k == 0 && c == 0) continue;
                     fine_relax<T, W>(a, c, z && k == 0 && c == 0, gt, gs);
+                    prof_done(1000 + c);
                     if (!G.sync()) return;
                     prof_mark(1000 + c);
                 }
             fine_restrict<T, W>(a, gt, gs);
+            prof_done(2000);
             if (!G.sync()) return;
             prof_mark(2000);
         }
         for (int l = 1; l < a.tail; ++l) {
-            if (worker >= 0) tile_down<T, W>(a, l, smem_t, worker, nworkers);
+            if (l < a.tile_from) {
+                // a large coarse level, one phase per colour: its first colour
+                // from the zero start came with the restriction into it
+                for (int k = 0; k < a.nu1c; ++k)
+                    for (int c = 0; c < 4; ++c) {
+                        if (k == 0 && c == 0) continue;
+                        coarse_relax<T, W>(a, l, c, gt, gs);
+                        if (!G.sync()) return;
+                        prof_mark(1000 + 10 * l + c);
+                    }
+                coarse_restrict<T, W>(a, l, gt, gs);
+            } else if (worker >= 0) {
+                tile_down<T, W>(a, l, smem_t, worker, nworkers);
+            }
+            prof_done(2000 + 10 * l);
             if (!G.sync()) return;
             prof_mark(2000 + 10 * l);
         }
         if (blockIdx.x == 0) tail_vcycle<T, W>(a, tl, inv);
+        prof_done(4000);
         if (!G.sync()) return;
         prof_mark(4000);
         for (int l = a.tail - 1; l >= 1; --l) {
+            if (l < a.tile_from) {
+                coarse_prolong<T, W>(a, l, gt, gs);
+                if (!G.sync()) return;
+                prof_mark(3000 + 10 * l);
+                for (int k = 0; k < a.nu2c; ++k)
+                    for (int c = 0; c < 4; ++c) {
+                        coarse_relax<T, W>(a, l, c, gt, gs);
+                        if (!G.sync()) return;
+                        prof_mark(1500 + 10 * l + c);
+                    }
+                continue;
+            }
             if (worker >= 0) tile_up<T, W>(a, l, smem_t, worker, nworkers);
+            prof_done(3000 + 10 * l);
             if (!G.sync()) return;
             prof_mark(3000 + 10 * l);
         }
         slot ^= 1;
-        if (a.tile_fine) {
-            if (worker >= 0)
-                tile_fine<T, W>(a, true, slot, fine_bufs<T>(a, true, cur), smem_t, worker, nworkers);
-            cur ^= 1;
-            if (!G.sync()) return;
-            prof_mark(6000);
-            continue;
-        }
         // finest level, one phase per colour: the prolongation folded into
         // the first post-smoothing colour, the float64 update v += e into the
         // last (mixed path), then the residual check
-        const T* uc = (const T*)(a.tail == 1 ? a.L[1].u : a.L[1].u2);
+        const T* uc = (const T*)final_u(a, 1);
         if (a.nu2 == 0) {
             LevelArgs C = a.L[1];
             C.u = (void*)uc;
@@ -1634,10 +1393,12 @@ __global__ void __launch_bounds__(kMGThreads, 2) k_mg_cycles_tiled(const __grid_
                     }
                     if (!done) fine_relax<T, W>(a, c, false, gt, gs);
                 }
+                prof_done(1100 + 10 * k + c);
                 if (!G.sync()) return;
-                prof_mark(1000 + c);
+                prof_mark(1100 + 10 * k + c);
             }
         fine_check(a, slot, gt, gs);
+        prof_done(6000);
         if (!G.sync()) return;
         prof_mark(6000);
     }
@@ -1705,8 +1466,8 @@ int tiled_max_tiles(const SolveArgs& a) {
         const int nt = (sc + tc - 1) / tc;
         return nt * nt;
     };
-    int m = a.tile_fine ? tiles(a.tc[0], a.L[0].sc) : 0;
-    for (int l = 1; l < a.tail; ++l) m = std::max(m, tiles(a.tc[l], a.L[l].sc));
+    int m = 0;
+    for (int l = std::max(1, a.tile_from); l < a.tail; ++l) m = std::max(m, tiles(a.tc[l], a.L[l].sc));
     return m;
 }
 
@@ -1719,15 +1480,7 @@ size_t tiled_smem_bytes(const SolveArgs& a) {
     };
     auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
     size_t need = tail_smem_bytes(a);
-    if (a.tile_fine) {   // finest level
-        const LevelArgs& L = a.L[0];
-        const int K1 = a.mixed ? (a.nu1 > 0 ? 2 * a.nu1 - 1 : 0) : 2 * a.nu1;
-        const int H = (a.mixed ? 2 : 1) + K1 + 2 * a.nu2;
-        const size_t w = side(a.tc[0], L.sc, L.side, H), wh = w * w;
-        const size_t rw = 2 * (size_t)std::min(a.tc[0], L.sc) + 1;
-        need = std::max(need, 16 * wh + r16(wh) + rw * rw * T);
-    }
-    for (int l = 1; l < a.tail; ++l) {
+    for (int l = std::max(1, a.tile_from); l < a.tail; ++l) {
         const LevelArgs& L = a.L[l];
         const int K1 = a.nu1c > 0 ? 4 * a.nu1c - 1 : 0;
         const size_t wd = side(a.tc[l], L.sc, L.side, 1 + K1);
@@ -1740,8 +1493,7 @@ size_t tiled_smem_bytes(const SolveArgs& a) {
 }
 
 void set_tile_sides(SolveArgs& a, int workers) {
-    // the finest level's tile (when tiled): 16 x 16 points of level 1
-    a.tc[0] = 16;
+    a.tc[0] = 0;   // the finest level is not tiled (one grid-wide phase per colour)
     // coarse levels: about one tile per worker block, at least 2 x 2 points
     // of the next level, at most 16 x 16 (8 x 8 in float64: shared memory)
     int root = 1;
@@ -1805,7 +1557,10 @@ void launch_mg_cycles(const SolveArgs& a, cudaStream_t st) {
         int per_sm = 0;
         GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tiled_kernel(kind), kMGThreads,
                                                               smem));
-        int nb = std::min(std::max(1, per_sm) * o.sms, 1 + tiled_max_tiles(a));
+        // one block per tile of the largest tiled level (plus block 0), the
+        // whole GPU when a large coarse level runs grid-wide phases
+        int nb = std::max(1, per_sm) * o.sms;
+        if (a.tile_from <= 1) nb = std::min(nb, 1 + tiled_max_tiles(a));
         if (a.max_blocks > 0) nb = std::min(nb, a.max_blocks);
         nb = std::max(nb, 2);
         GS_CUDA(cudaLaunchCooperativeKernel(tiled_kernel(kind), dim3(nb), dim3(kMGThreads), args, smem,

@@ -57,12 +57,9 @@ struct SolveArgs {
     double lin_tol;
     double rel_tol;  // also stop once the residual fell by this factor (0: floor only)
     int tiled;       // V-cycles with tiled grid-wide levels (k_mg_cycles_tiled)
-    int tile_fine;   // tiled: the finest level tiled too (else one phase per colour there)
-    int tc[kMaxLevels];   // tile side of level l, in points of level l + 1
-    double* v2;      // tiled cycles, finest level: second value buffer
-    double* v3;      // float64 path: third value buffer
-    void* e2;        // mixed path: second correction buffer
-    void* r2;        // mixed path: second right-hand-side buffer
+    int tile_from;   // tiled cycles: coarse levels l >= tile_from are tiled, larger ones
+                     // (1 <= l < tile_from) take one grid-wide phase per colour
+    int tc[kMaxLevels];   // tile side of level l >= 1, in points of level l + 1
     double* inv;     // inverse of the coarsest operator (n_L x n_L)
     int* inv_status;
     GridBarrier* bar;
@@ -82,6 +79,9 @@ size_t tail_smem_bytes(const SolveArgs& a);
 // Largest dynamic shared memory a tiled cycle launch may take, and what one
 // needs (the tail's and the largest tile's, whichever is more).
 constexpr int kTiledSmemMax = 110 * 1024;
+// Largest coarse level side the tiled kernel tiles: a 1023 x 1023 coarse level
+// (the 2047 x 2047 grid's first) measured faster one phase per colour.
+constexpr int kTiledMaxSide = 511;
 size_t tiled_smem_bytes(const SolveArgs& a);
 
 // Tile sides of a tiled launch for `workers` tile-taking thread blocks.

@@ -149,10 +149,6 @@ gs_status static_solve(int32_t side, int32_t variant, uint64_t seed, const doubl
         L.u32 = cv.take<float>(L.n);
         L.f32 = cv.take<float>(L.n);
         L.r32 = cv.take<float>(L.n);
-        if (l == 0) {
-            L.w64 = cv.take<double>(L.n);
-            L.w32 = cv.take<float>(L.n);
-        }
         if (l + 1 < g.lv.size()) {
             const size_t sc = (size_t)(L.side - 1) / 2;
             L.P64 = cv.take<double>(8 * (sc + 1) * (sc + 1));

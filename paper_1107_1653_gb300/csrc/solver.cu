@@ -230,10 +230,6 @@ static void alloc_grid(gs_solver* s, Arena& ar, IsaacsGrid& g) {
         L.u32 = ar.alloc<float>(L.n);
         L.f32 = ar.alloc<float>(L.n);
         L.r32 = ar.alloc<float>(L.n);
-        if (l == 0) {
-            L.w64 = ar.alloc<double>(L.n);
-            L.w32 = ar.alloc<float>(L.n);
-        }
         if (l + 1 < g.lv.size()) {
             const size_t sc = (size_t)(L.side - 1) / 2;
             L.P64 = ar.alloc<double>(8 * (sc + 1) * (sc + 1));
@@ -367,11 +363,6 @@ int linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, boo
         L.P32 = Lv.P32;
         L.u2 = mixed ? (void*)Lv.r32 : (void*)Lv.r64;
     }
-    a.v2 = g.lv[0].r64;
-    a.v3 = g.lv[0].w64;
-    a.e2 = g.lv[0].r32;
-    a.r2 = g.lv[0].w32;
-    a.tile_fine = 0;
     // about two blocks per SM in a tiled launch; tile sides for that many workers
     {
         int dev = 0, sms = 0;
@@ -381,13 +372,15 @@ int linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, boo
         if (a.max_blocks > 0) blocks = std::min(blocks, a.max_blocks);
         set_tile_sides(a, std::max(1, blocks - 1));
     }
+    a.tile_from = 1;
+    while (a.tile_from < a.tail && a.L[a.tile_from].side > kTiledMaxSide) ++a.tile_from;
     // levels from smem_from on are staged in block 0's shared memory, as many as fit
     a.smem_from = std::max(a.tail, 1);
     while (a.smem_from < a.nlev && tail_smem_bytes(a) > (size_t)kTailSmemMax)
         ++a.smem_from;
     // tiled V-cycles where they apply: V-cycles with at least one grid-wide
-    // level, every buffer present, shared memory within the launch's limit
-    a.tiled = s->opt.cycle_kernel == 0 && a.gamma == 1 && a.tail >= 1 && g.lv[0].w64 &&
+    // level, shared memory within the launch's limit
+    a.tiled = s->opt.cycle_kernel == 0 && a.gamma == 1 && a.tail >= 1 &&
               (a.max_blocks == 0 || a.max_blocks >= 2) &&
               tiled_smem_bytes(a) <= (size_t)kTiledSmemMax;
     GS_CUDA(cudaMemsetAsync(s->mgd, 0, sizeof(MGState), s->st));

@@ -47,8 +47,6 @@ struct Level {
     float* P32 = nullptr;
     double *u64 = nullptr, *f64 = nullptr, *r64 = nullptr;
     float *u32 = nullptr, *f32 = nullptr, *r32 = nullptr;
-    double* w64 = nullptr;     // level 0: third value buffer of the tiled cycles (float64 path)
-    float* w32 = nullptr;      // level 0: second right-hand side of the tiled cycles (mixed path)
 };
 
 // An Isaacs grid with its policies, value and multigrid hierarchy.

@@ -291,7 +291,7 @@ def test_fmg_level_counts_match_oracle(gs, variant):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
 @pytest.mark.parametrize("side,variant,cyc", [(63, 0, (1, 1)), (255, 1, (1, 2)), (1023, 0, (1, 2)),
-                                              (255, 0, (2, 1))])
+                                              (255, 0, (2, 1)), (2047, 1, (1, 2))])
 def test_tiled_cycles_match_per_colour_kernel(gs, side, variant, cyc, prec):
     """The tiled V-cycle kernel (default) and the one-phase-per-colour kernel
     run the same arithmetic per point: the same policy-fixed solve reaches the
