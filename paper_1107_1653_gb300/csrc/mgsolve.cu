@@ -1209,6 +1209,39 @@ __device__ __noinline__ void relax_fine_prolonged(const SolveArgs& a, const T* u
     }
 }
 
+// u_0 += P u_1 at the finest level's colour-1 points (its edge points) only:
+// the colour-0 values are overwritten, unread, by the relaxation that follows.
+template <typename T, typename W>
+__device__ __noinline__ void prolong_colour1(const SolveArgs& a, const T* uc, size_t start, size_t stride) {
+    const LevelArgs& L = a.L[0];
+    T* __restrict__ u = (T*)L.u;
+    const W* P = (const W*)L.P;
+    const int side = L.side, sc = L.sc, hs = (side + 1) / 2;
+    const unsigned cnt = (unsigned)side * hs, st = (unsigned)stride;
+    const FastDiv dv(hs);
+    constexpr int K = 4;
+    unsigned t = (unsigned)start;
+    for (; t + (K - 1) * st < cnt; t += K * st) {
+        int i[K], j[K];
+        T val[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            unsigned r;
+            j[k] = (int)dv.divmod(t + k * st, &r);
+            i[k] = ((j[k] + 1) & 1) + 2 * (int)r;
+            val[k] = i[k] < side ? u[(size_t)j[k] * side + i[k]] + prolonged<T, W>(P, uc, sc, i[k], j[k]) : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (i[k] < side) u[(size_t)j[k] * side + i[k]] = val[k];
+    }
+    for (; t < cnt; t += st) {
+        unsigned r;
+        const int j = (int)dv.divmod(t, &r), i = ((j + 1) & 1) + 2 * (int)r;
+        if (i < side) u[(size_t)j * side + i] += prolonged<T, W>(P, uc, sc, i, j);
+    }
+}
+
 // Where level l's values after its post-smoothing are, in the tiled kernel:
 // u2 for a tiled level (its neighbours stage u while it writes), u for the
 // tail's top level and for the large coarse levels relaxed one phase per colour.
@@ -1381,7 +1414,15 @@ __global__ void __launch_bounds__(kMGThreads, 2) k_mg_cycles_tiled(const __grid_
         }
         for (int k = 0; k < a.nu2; ++k)
             for (int c = 0; c < 2; ++c) {
-                if (k == 0 && c == 0) {
+                if (k == 0 && c == 0 && a.tile_from > 1) {
+                    // large grids: the colour-1 points' prolongation in a phase
+                    // of its own (each is added once, not once per neighbour),
+                    // then a plain colour-0 relaxation
+                    prolong_colour1<T, W>(a, uc, gt, gs);
+                    if (!G.sync()) return;
+                    prof_mark(1090);
+                    fine_relax<T, W>(a, 0, false, gt, gs);
+                } else if (k == 0 && c == 0) {
                     relax_fine_prolonged<T, W>(a, uc, gt, gs);
                 } else {
                     bool done = false;
