@@ -431,35 +431,22 @@ def run_serving(args):
     the closed-loop capacity; p50/p99 latency and solves/s."""
     import numpy as np
     import torch
-    import synth
     torch.cuda.set_device(0)
     import paper_1107_1653_gb300 as gs
     rng = np.random.default_rng(5)
-    # pool of games at the quantile midpoints of U{1e3..1e6}; a request draws
-    # n ~ U and takes the pool game of its quantile bucket (the tables stay on
-    # the device and requests borrow them, as a server caching its models would)
-    qs = (np.arange(args.pool) + 0.5) / args.pool
-    pool_n = (1000 + qs * (1_000_000 - 1000)).astype(np.int64)
-    t0 = time.perf_counter()
-    pool = []
-    for i, n in enumerate(pool_n):
-        rp, col, prob, rew, mu = synth.random_game_parallel(int(n), 5000 + i, workers=os.cpu_count())
-        pool.append((int(n), torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(),
-                     torch.from_numpy(prob).cuda(), torch.from_numpy(rew).cuda(), mu))
-    t_gen = time.perf_counter() - t0
+    # every game request is a fresh random game n ~ U{1e3..1e6} given by its
+    # seed: the server draws its table on the device when the request runs
     sides = (63, 127, 255, 511, 1023)
 
     def draw(k):
         if rng.random() < 0.7:
             return ("isaacs", int(rng.choice(sides)), 5 + k)
-        n = int(rng.integers(1000, 1_000_001))
-        return ("game", min(args.pool - 1, int((n - 1000) / (999_001 / args.pool))))
+        return ("game", int(rng.integers(1000, 1_000_001)), 50_000 + k)
 
     def submit(srv, r):
         if r[0] == "isaacs":
             return srv.submit_isaacs(r[1], 0, r[2])
-        n, rp, col, prob, rew, mu = pool[r[1]]
-        return srv.submit_game(n, 4, 4, rp, col, prob, rew, mu, borrow=True)
+        return srv.submit_random_game(r[1], 4, 4, r[2], 0.99)
 
     with gs.GameServer(slots=args.slots, precision="mixed") as srv:
         # closed-loop capacity: a burst of requests submitted at once
@@ -498,13 +485,15 @@ def run_serving(args):
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "serving_mix", "requests": len(reqs), "slots": args.slots,
                    "arrival": "Poisson", "rate_per_s": rate, "capacity_per_s": cap,
-                   "game_pool": [int(n) for n in pool_n], "isaacs_sides": list(sides)},
+                   "games": "a fresh random game per request, n ~ U{1e3..1e6}, 4 x 4 actions, "
+                            "8 successors per row, mu 0.99, drawn on the device from its seed",
+                   "isaacs_sides": list(sides)},
         "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
         "p50_ms_isaacs": float(np.percentile(lat_i, 50) * 1e3) if len(lat_i) else None,
         "p99_ms_isaacs": float(np.percentile(lat_i, 99) * 1e3) if len(lat_i) else None,
         "p50_ms_games": float(np.percentile(lat_g, 50) * 1e3) if len(lat_g) else None,
         "p99_ms_games": float(np.percentile(lat_g, 99) * 1e3) if len(lat_g) else None,
-        "completed": ok, "makespan_s": makespan, "generation_s": t_gen,
+        "completed": ok, "makespan_s": makespan,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -819,7 +808,6 @@ def main():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--burst", type=int, default=64)
     ap.add_argument("--slots", type=int, default=4)
-    ap.add_argument("--pool", type=int, default=8)
     ap.add_argument("--profile", action="store_true",
                     help="run one solve only (for ncu); prints the solve statistics")
     args = ap.parse_args()

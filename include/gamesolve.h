@@ -192,6 +192,31 @@ gs_status gamesolve_set_game_batch(gs_solver* s, int32_t count, int32_t m1, int3
                                    const int32_t* col, const double* prob,
                                    const double* reward, const double* mu);
 
+/* Draws a random finite discounted game (Sec. 2) into caller-owned device
+ * buffers, on `stream` (NULL = default stream; the call returns once the
+ * launch is queued): n states, m1 x m2 action pairs, k successors per row.
+ * Row rho = (x*m1 + a)*m2 + b uses outputs rho*17 .. rho*17+16 of the
+ * SplitMix64 stream `seed` (Steele, Lea & Flood 2014; a double in [0, 1) is
+ * the top 53 bits times 2^-53): outputs 0..k-1 pick k distinct successors
+ * uniformly from {0..n-1} (output t gives floor(u (n - t)), stepped past each
+ * earlier pick in ascending order), outputs 8..8+k-1 give -log1p(-u) draws
+ * normalised to probabilities (pairwise sum for k = 8, left to right
+ * otherwise; the last probability set to one minus the others), output 16 the
+ * reward 2u - 1.  Successors are stored in increasing column order.
+ * row_ptr: n*m1*m2 + 1 int64 (rho*k); col, prob: n*m1*m2*k; reward: n*m1*m2.
+ * Errors: GS_EINVAL (n < 1 or >= 2^31, m1 outside [1, 64], m2 outside
+ * [1, 255], k outside [1, min(8, n)], a NULL or non-device buffer). */
+gs_status gamesolve_random_game(int64_t n, int32_t m1, int32_t m2, int32_t k, uint64_t seed,
+                                int64_t* row_ptr, int32_t* col, double* prob, double* reward,
+                                void* stream);
+
+/* Sets the random game of gamesolve_random_game (same n, m1, m2, k, seed)
+ * with discount mu in (0, 1), drawn on the device: no table crosses the host.
+ * Scratch of the table's size is held during the call.
+ * Errors: as gamesolve_random_game and gamesolve_set_game. */
+gs_status gamesolve_set_random_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2, int32_t k,
+                                    uint64_t seed, double mu);
+
 /* Sets the two-sided stopping game on a line of Sec. 6.3 (Eq. (exVI2stop),
  * discretised): states x_1..x_n, n = 2^k - 1 <= 2047 (the interior points of a
  * uniform grid of n + 2 points), end values v_left = v(x_0), v_right =
@@ -387,29 +412,34 @@ gs_status gamesolve_isaacs_policy_solve_static(int32_t side, int32_t variant, ui
  * A request loop around the solvers: requests are queued in arrival order and
  * admitted to worker slots as slots and device memory free up.  Each slot has
  * its own CUDA stream and solver, its grid-wide launches capped to a share of
- * the GPU, so the work of the requests in flight overlaps on the device.  A
- * request's multigrid hierarchy and policies stay on the device for its whole
- * policy iteration; its value and policies are copied to host memory when it
+ * the GPU, so the work of the requests in flight overlaps on the device.
+ * Games of fewer than 4096 states (those a solver runs one thread block per
+ * game) that wait together with the same kind and action counts are taken by
+ * one slot as a batch of up to 256 and solved by one persistent launch
+ * (gamesolve_set_game_batch); they share t_start and t_end.  A request's
+ * multigrid hierarchy and policies stay on the device for its whole policy
+ * iteration; its value and policies are copied to host memory when it
  * completes.  Results do not depend on what else is in flight (the kernels'
- * arithmetic does not depend on timing; only the number of blocks a grid-wide
- * game reduction uses can change its rounding). */
+ * arithmetic does not depend on timing or on a game's batch; only the number
+ * of blocks a grid-wide game reduction uses can change its rounding). */
 typedef struct gs_server gs_server;
 
 typedef struct {
-    int32_t kind;            /* 1 Isaacs grid, 2 finite game */
+    int32_t kind;            /* 1 Isaacs grid, 2 finite game given as a table, 3 random finite
+                                game given by its seed (gamesolve_set_random_game) */
     int32_t side;            /* Isaacs: grid side (2^k - 1) */
     int32_t variant;         /* Isaacs: 0 plain, 1 obstacle */
-    int32_t m1, m2;          /* game: actions */
-    uint64_t seed;           /* Isaacs: noise stream */
-    int64_t n;               /* game: states */
+    int32_t m1, m2;          /* games: actions */
+    uint64_t seed;           /* Isaacs: noise stream; random game: its stream */
+    int64_t n;               /* games: states */
     const int64_t* row_ptr;  /* game: CSR table as for gamesolve_set_game (copied at submit) */
     const int32_t* col;
     const double* prob;
     const double* reward;
-    double mu;               /* game: discount */
+    double mu;               /* games: discount */
     int32_t flags;           /* GS_REQ_BORROW: the table is not copied at submit; the caller
                                 keeps it valid (host or device memory) until the request is done */
-    int32_t reserved;
+    int32_t k;               /* random game: successors per row, 1..8 (0 = 8) */
 } gs_request;
 
 enum { GS_REQ_BORROW = 1 };

@@ -65,7 +65,7 @@ class gs_request(ctypes.Structure):
         ("m1", ctypes.c_int32), ("m2", ctypes.c_int32), ("seed", ctypes.c_uint64),
         ("n", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
         ("prob", ctypes.c_void_p), ("reward", ctypes.c_void_p), ("mu", ctypes.c_double),
-        ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32), ("k", ctypes.c_int32),
     ]
 
 
@@ -90,6 +90,10 @@ _SIGS = {
     "gamesolve_set_game_batch": (_S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P,
                                       _P, _P, _P, _P]),
     "gamesolve_get_batch_stats": (_S, [_P, _P, _P]),
+    "gamesolve_random_game": (_S, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_uint64, _P, _P, _P, _P, _P]),
+    "gamesolve_set_random_game": (_S, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_uint64, ctypes.c_double]),
     "gamesolve_get_batch_shape": (_S, [_P, _P]),
     "gamesolve_set_stopping_line": (_S, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_double,
                                          ctypes.c_double]),
@@ -216,6 +220,12 @@ class GameSolver:
         prob, reward = _as(prob, np.float64), _as(reward, np.float64)
         _check(lib.gamesolve_set_game(self.h, n, m1, m2, _ptr(row_ptr), _ptr(col), _ptr(prob),
                                       _ptr(reward), mu), "gamesolve_set_game")
+        self.n, self.m1, self.count = n, m1, 1
+
+    def set_random_game(self, n, m1, m2, seed, mu, k=8):
+        """The random game of random_game(n, m1, m2, seed, k), drawn on the device."""
+        _check(lib.gamesolve_set_random_game(self.h, n, m1, m2, k, seed, mu),
+               "gamesolve_set_random_game")
         self.n, self.m1, self.count = n, m1, 1
 
     def set_stopping_line(self, c, psi1, psi2, v_left, v_right):
@@ -361,6 +371,16 @@ class GameServer:
         self._keep[t.value] = (n, m1)
         return t.value
 
+    def submit_random_game(self, n, m1, m2, seed, mu, k=8):
+        """A random game given by its seed: its table is drawn on the device when
+        the request runs (gamesolve_set_random_game)."""
+        r = gs_request(kind=3, n=n, m1=m1, m2=m2, seed=seed, mu=mu, k=k)
+        t = ctypes.c_int64()
+        _check(lib.gamesolve_server_submit(self.h, ctypes.byref(r), ctypes.byref(t)),
+               "gamesolve_server_submit")
+        self._keep[t.value] = (n, m1)
+        return t.value
+
     @staticmethod
     def _info(info):
         d = {k: getattr(info, k) for k, _ in gs_ticket_info._fields_ if k != "stats"}
@@ -400,6 +420,24 @@ def fmg_interpolate(side_c, variant, v_c, alpha_c, beta_c):
                                          _ptr(v), _ptr(a), _ptr(b), None),
            "gamesolve_fmg_interpolate")
     return v, a, b
+
+
+def random_game(n, m1, m2, seed, k=8, mu=0.99):
+    """The random game of gamesolve_random_game, drawn on the current CUDA device
+    and returned as host arrays (row_ptr, col, prob, reward, mu) in the layout of
+    GameSolver.set_game."""
+    import torch
+    rows = n * m1 * m2
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rp = torch.empty(rows + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(rows * k, dtype=torch.int32, device=dev)
+    prob = torch.empty(rows * k, dtype=torch.float64, device=dev)
+    rew = torch.empty(rows, dtype=torch.float64, device=dev)
+    _check(lib.gamesolve_random_game(n, m1, m2, k, seed, rp.data_ptr(), col.data_ptr(), prob.data_ptr(),
+                                     rew.data_ptr(), torch.cuda.current_stream().cuda_stream),
+           "gamesolve_random_game")
+    torch.cuda.synchronize()
+    return rp.cpu().numpy(), col.cpu().numpy(), prob.cpu().numpy(), rew.cpu().numpy(), float(mu)
 
 
 def exported_symbols():

@@ -182,6 +182,81 @@ gs_status gamesolve_set_game_batch(gs_solver* s, int32_t count, int32_t m1, int3
     });
 }
 
+namespace {
+// Device memory of the current device, or managed memory.
+bool on_device(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (at.type != cudaMemoryTypeDevice || cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.device == dev;
+}
+}  // namespace
+
+gs_status gamesolve_random_game(int64_t n, int32_t m1, int32_t m2, int32_t k, uint64_t seed,
+                                int64_t* row_ptr, int32_t* col, double* prob, double* reward,
+                                void* stream) {
+    if (!random_game_args_ok(n, m1, m2, k) || !row_ptr || !col || !prob || !reward) {
+        set_last_error("random_game: invalid argument");
+        return GS_EINVAL;
+    }
+    if (!on_device(row_ptr) || !on_device(col) || !on_device(prob) || !on_device(reward)) {
+        set_last_error("random_game: the table buffers must be device memory");
+        return GS_EINVAL;
+    }
+    return guarded([&]() -> gs_status {
+        launch_random_game(n, m1, m2, k, seed, row_ptr, col, prob, reward, (cudaStream_t)stream);
+        return GS_OK;
+    });
+}
+
+gs_status gamesolve_set_random_game(gs_solver* s, int64_t n, int32_t m1, int32_t m2, int32_t k,
+                                    uint64_t seed, double mu) {
+    if (!s || !random_game_args_ok(n, m1, m2, k) || !(mu > 0.0 && mu < 1.0)) {
+        set_last_error("set_random_game: invalid argument");
+        return GS_EINVAL;
+    }
+    return guarded([&]() -> gs_status {
+        // drawn into scratch buffers on the solver's stream, then set as a
+        // table given in device memory (copied into the problem)
+        const int64_t rows = n * m1 * m2, nnz = rows * k;
+        int64_t* rp = nullptr;
+        int32_t* col = nullptr;
+        double *prob = nullptr, *rew = nullptr;
+        auto release = [&]() {
+            cudaStreamSynchronize(s->st);
+            cudaFree(rp);
+            cudaFree(col);
+            cudaFree(prob);
+            cudaFree(rew);
+        };
+        try {
+            GS_CUDA(cudaMalloc(&rp, sizeof(int64_t) * (rows + 1)));
+            GS_CUDA(cudaMalloc(&col, sizeof(int32_t) * nnz));
+            GS_CUDA(cudaMalloc(&prob, sizeof(double) * nnz));
+            GS_CUDA(cudaMalloc(&rew, sizeof(double) * rows));
+            launch_random_game(n, m1, m2, k, seed, rp, col, prob, rew, s->st);
+            GS_CUDA(cudaStreamSynchronize(s->st));
+            const int64_t off[2] = {0, n};
+            auto P = build_game_problem(s, 1, m1, m2, off, rp, col, prob, rew, &mu);
+            s->prob = std::move(P);
+            reset_initial(s);
+        } catch (...) {
+            release();
+            throw;
+        }
+        release();
+        return GS_OK;
+    });
+}
+
 gs_status gamesolve_get_batch_stats(const gs_solver* s, int32_t* stats, double* res) {
     if (!s) return GS_EINVAL;
     if (!s->prob || s->prob->kind != 2) {

@@ -110,4 +110,12 @@ void launch_game_improve_one(const BatchArgs& B, int mode, int64_t n, int* scal,
 // Games of at least this many states, set alone, run on the whole grid.
 constexpr int64_t kGameGridMinStates = 4096;
 
+// Random games drawn on the device (randgame.cu): n states, m1 x m2 rows per
+// state, k <= 8 successors per row; CSR table into device buffers of
+// n*m1*m2 + 1, n*m1*m2*k, n*m1*m2*k and n*m1*m2 entries, row_ptr offset by
+// nnz_base (a game placed after others in a batch's concatenated table).
+bool random_game_args_ok(int64_t n, int32_t m1, int32_t m2, int32_t k);
+void launch_random_game(int64_t n, int32_t m1, int32_t m2, int32_t k, uint64_t seed, int64_t* row_ptr,
+                        int32_t* col, double* prob, double* reward, cudaStream_t st, int64_t nnz_base = 0);
+
 }  // namespace gs

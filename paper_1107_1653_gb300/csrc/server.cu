@@ -1,10 +1,14 @@
-// Serving: a request loop around the solvers.  Requests (Isaacs grids or
-// finite games) are queued in arrival order and admitted to worker slots as
-// slots and device memory free up; every slot owns a CUDA stream and a solver
-// whose grid-wide launches are capped to a share of the GPU, so the work of
-// the requests in flight overlaps on the device.  Each request's hierarchy and
+// Serving: a request loop around the solvers.  Requests (Isaacs grids,
+// finite games given as tables, random games given by a seed) are queued in
+// arrival order and admitted to worker slots as slots and device memory free
+// up; every slot owns a CUDA stream and a solver whose grid-wide launches are
+// capped to a share of the GPU, so the work of the requests in flight
+// overlaps on the device.  Small games (below the grid-wide threshold) waiting
+// together with the same action counts are solved as one batch by a single
+// persistent launch (one thread block per game).  Each request's hierarchy and
 // policies stay resident on the device for its whole policy iteration; its
 // value and policies are copied back to host memory when it completes.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -42,16 +46,32 @@ double now_s(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
-// Device bytes a request is expected to hold while it runs.
+// Successors per row of a random-game request (0 = 8).
+int succ_of(const gs_request& r) { return r.k > 0 ? r.k : 8; }
+
+// Device bytes a request is expected to hold while it runs, without its
+// table (added by the caller for tables given in memory).  A random game
+// holds its drawn table twice while it is set.
 size_t estimate_bytes(const gs_request& r) {
     if (r.kind == 1) {
         const size_t n = (size_t)r.side * r.side;
         return n * 220 + (64 << 10);
     }
     const size_t rows = (size_t)r.n * r.m1 * r.m2;
-    const size_t nnz = r.row_ptr ? 0 : 0;
-    (void)nnz;
-    return rows * 32 + (size_t)r.n * 60 + (64 << 10);
+    const size_t base = rows * 32 + (size_t)r.n * 60 + (64 << 10);
+    return r.kind == 3 ? base + 2 * rows * (8 + 12 * (size_t)succ_of(r)) : base;
+}
+
+// Games solved together by one batched launch: below the threshold where a
+// game alone takes the whole grid, so the batch runs the kernel each of them
+// would run alone.
+constexpr int kServeBatchMax = 256;
+bool batchable(const Request& R) {
+    return (R.spec.kind == 2 || R.spec.kind == 3) && R.spec.n < kGameGridMinStates;
+}
+bool same_batch(const Request& a, const Request& b) {
+    return a.spec.kind == b.spec.kind && a.spec.m1 == b.spec.m1 && a.spec.m2 == b.spec.m2 &&
+           (a.spec.kind == 2 || succ_of(a.spec) == succ_of(b.spec));
 }
 
 }  // namespace
@@ -86,6 +106,10 @@ void run_request(gs_solver* solver, Request& R) {
         st = gamesolve_set_isaacs_grid(solver, q.side, q.variant, q.seed, nullptr);
         R.n = (int64_t)q.side * q.side;
         R.m1 = q.variant == 1 ? 5 : 4;
+    } else if (q.kind == 3) {
+        st = gamesolve_set_random_game(solver, q.n, q.m1, q.m2, succ_of(q), q.seed, q.mu);
+        R.n = q.n;
+        R.m1 = q.m1;
     } else if (q.flags & GS_REQ_BORROW) {
         st = gamesolve_set_game(solver, q.n, q.m1, q.m2, q.row_ptr, q.col, q.prob, q.reward, q.mu);
         R.n = q.n;
@@ -111,6 +135,145 @@ void run_request(gs_solver* solver, Request& R) {
     R.status = st;
 }
 
+// Several small games of equal kind and action counts as one batch
+// (gamesolve_set_game_batch); results, statistics and status per request.
+// A batch the library rejects (a bad table among them) is run request by
+// request, so that each gets its own status.
+void run_batch(gs_solver* solver, cudaStream_t stream, std::vector<std::shared_ptr<Request>>& B) {
+    const int count = (int)B.size();
+    const gs_request& q0 = B[0]->spec;
+    const int m1 = q0.m1, m2 = q0.m2;
+    std::vector<int64_t> off(count + 1, 0);
+    std::vector<double> mu(count);
+    for (int g = 0; g < count; ++g) {
+        off[g + 1] = off[g] + B[g]->spec.n;
+        mu[g] = B[g]->spec.mu;
+    }
+    const int64_t rows = off[count] * m1 * m2;
+    gs_status st = GS_OK;
+    if (q0.kind == 3) {
+        // drawn on the device into one concatenated table
+        const int k = succ_of(q0);
+        int64_t* rp = nullptr;
+        int32_t* col = nullptr;
+        double *prob = nullptr, *rew = nullptr;
+        bool ok = cudaMalloc(&rp, sizeof(int64_t) * (rows + 1)) == cudaSuccess &&
+                  cudaMalloc(&col, sizeof(int32_t) * rows * k) == cudaSuccess &&
+                  cudaMalloc(&prob, sizeof(double) * rows * k) == cudaSuccess &&
+                  cudaMalloc(&rew, sizeof(double) * rows) == cudaSuccess;
+        if (ok) {
+            try {
+                for (int g = 0; g < count; ++g) {
+                    const int64_t r0 = off[g] * m1 * m2;
+                    launch_random_game(B[g]->spec.n, m1, m2, k, B[g]->spec.seed, rp + r0, col + r0 * k,
+                                       prob + r0 * k, rew + r0, stream, r0 * k);
+                }
+            } catch (const Error&) {
+                ok = false;
+            }
+        }
+        ok = ok && cudaStreamSynchronize(stream) == cudaSuccess;
+        st = ok ? gamesolve_set_game_batch(solver, count, m1, m2, off.data(), rp, col, prob, rew, mu.data())
+                : GS_ECUDA;
+        cudaStreamSynchronize(stream);
+        cudaFree(rp);
+        cudaFree(col);
+        cudaFree(prob);
+        cudaFree(rew);
+        cudaGetLastError();
+    } else {
+        // tables in memory: concatenated on the host (columns stay per game)
+        std::vector<int64_t> rp(rows + 1, 0);
+        std::vector<int32_t> col;
+        std::vector<double> prob, rew(rows);
+        int64_t r0 = 0;
+        bool bad = false;
+        for (int g = 0; g < count && !bad; ++g) {
+            Request& R = *B[g];
+            const gs_request& q = R.spec;
+            const int64_t rg = q.n * m1 * m2;
+            std::vector<int64_t> rpg;
+            const int64_t* rpp = R.row_ptr.data();
+            const int32_t* cp = R.col.data();
+            const double *pp = R.prob.data(), *wp = R.reward.data();
+            std::vector<int32_t> cg;
+            std::vector<double> pg, wg;
+            if (q.flags & GS_REQ_BORROW) {   // borrowed: host or device memory
+                rpg.resize(rg + 1);
+                cudaMemcpy(rpg.data(), q.row_ptr, sizeof(int64_t) * (rg + 1), cudaMemcpyDefault);
+                const int64_t nz = rpg[rg];
+                if (rpg[0] != 0 || nz < 0 || nz > ((int64_t)1 << 40)) {
+                    bad = true;
+                    break;
+                }
+                cg.resize(nz);
+                pg.resize(nz);
+                wg.resize(rg);
+                cudaMemcpy(cg.data(), q.col, sizeof(int32_t) * nz, cudaMemcpyDefault);
+                cudaMemcpy(pg.data(), q.prob, sizeof(double) * nz, cudaMemcpyDefault);
+                cudaMemcpy(wg.data(), q.reward, sizeof(double) * rg, cudaMemcpyDefault);
+                rpp = rpg.data();
+                cp = cg.data();
+                pp = pg.data();
+                wp = wg.data();
+            }
+            if (rpp[0] != 0 || rpp[rg] < 0 ||
+                (!(q.flags & GS_REQ_BORROW) && rpp[rg] != (int64_t)R.col.size())) {
+                bad = true;   // the library reports it when the request runs alone
+                break;
+            }
+            const int64_t base = (int64_t)col.size(), nz = rpp[rg];
+            for (int64_t r = 0; r < rg; ++r) rp[r0 + r + 1] = base + rpp[r + 1];
+            col.insert(col.end(), cp, cp + nz);
+            prob.insert(prob.end(), pp, pp + nz);
+            std::copy(wp, wp + rg, rew.begin() + r0);
+            r0 += rg;
+        }
+        if (bad) st = GS_EINVAL;
+        else if (cudaGetLastError() != cudaSuccess) st = GS_ECUDA;
+        else st = gamesolve_set_game_batch(solver, count, m1, m2, off.data(), rp.data(),
+                                           col.empty() ? (const int32_t*)rp.data() : col.data(),
+                                           prob.empty() ? (const double*)rew.data() : prob.data(),
+                                           rew.data(), mu.data());
+    }
+    if (st == GS_EINVAL) {
+        for (auto& R : B) run_request(solver, *R);
+        return;
+    }
+    gs_solve_stats total{};
+    if (st == GS_OK) st = gamesolve_solve(solver, &total);
+    if (st == GS_OK || st == GS_ENOTCONV) {
+        std::vector<double> v(off[count]);
+        std::vector<uint8_t> alpha(off[count]), beta((size_t)off[count] * m1);
+        std::vector<int32_t> gst(4 * (size_t)count);
+        std::vector<double> res(count);
+        gs_status g1 = gamesolve_get_value(solver, v.data(), off[count]);
+        if (g1 == GS_OK) g1 = gamesolve_get_policy(solver, alpha.data(), beta.data());
+        if (g1 == GS_OK) g1 = gamesolve_get_batch_stats(solver, gst.data(), res.data());
+        for (int g = 0; g < count; ++g) {
+            Request& R = *B[g];
+            R.n = R.spec.n;
+            R.m1 = m1;
+            if (g1 != GS_OK) {
+                R.status = g1;
+                continue;
+            }
+            R.v.assign(v.begin() + off[g], v.begin() + off[g + 1]);
+            R.alpha.assign(alpha.begin() + off[g], alpha.begin() + off[g + 1]);
+            R.beta.assign(beta.begin() + off[g] * m1, beta.begin() + off[g + 1] * m1);
+            R.stats = total;
+            R.stats.outer = gst[4 * g];
+            R.stats.systems = gst[4 * g + 1];
+            R.stats.cycles = gst[4 * g + 2];
+            R.stats.converged = gst[4 * g + 3];
+            R.stats.res_inf = res[g];
+            R.status = R.stats.converged ? GS_OK : GS_ENOTCONV;
+        }
+        return;
+    }
+    for (auto& R : B) R->status = st;
+}
+
 void worker(gs_server* S, int slot) {
     cudaSetDevice(S->device);
     cudaStream_t stream = nullptr;
@@ -125,7 +288,7 @@ void worker(gs_server* S, int slot) {
     gs_solver* solver = nullptr;
     const gs_status created = gamesolve_create(&solver, &o);
     while (true) {
-        std::shared_ptr<Request> R;
+        std::vector<std::shared_ptr<Request>> B;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->work_cv.wait(lk, [&] {
@@ -135,28 +298,53 @@ void worker(gs_server* S, int slot) {
                 return S->in_use + need <= S->budget || S->running == 0;
             });
             if (S->stop) break;
-            R = S->pending.front();
+            B.push_back(S->pending.front());
             S->pending.pop_front();
-            S->in_use += R->mem;
+            S->in_use += B[0]->mem;
+            // small games waiting with the same kind and action counts join it
+            if (batchable(*B[0])) {
+                for (auto it = S->pending.begin(); it != S->pending.end() && (int)B.size() < kServeBatchMax;) {
+                    if (batchable(**it) && same_batch(*B[0], **it) && S->in_use + (*it)->mem <= S->budget) {
+                        S->in_use += (*it)->mem;
+                        B.push_back(*it);
+                        it = S->pending.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+            }
             ++S->running;
-            R->state = 1;
-            R->t_start = now_s(S->t0);
+            const double t = now_s(S->t0);
+            for (auto& R : B) {
+                R->state = 1;
+                R->t_start = t;
+            }
         }
-        if (created == GS_OK) run_request(solver, *R);
-        else R->status = created;
-        R->row_ptr.clear();
-        R->row_ptr.shrink_to_fit();
-        R->col.clear();
-        R->col.shrink_to_fit();
-        R->prob.clear();
-        R->prob.shrink_to_fit();
-        R->reward.clear();
-        R->reward.shrink_to_fit();
+        if (created != GS_OK) {
+            for (auto& R : B) R->status = created;
+        } else if (B.size() == 1) {
+            run_request(solver, *B[0]);
+        } else {
+            run_batch(solver, stream, B);
+        }
+        for (auto& R : B) {
+            R->row_ptr.clear();
+            R->row_ptr.shrink_to_fit();
+            R->col.clear();
+            R->col.shrink_to_fit();
+            R->prob.clear();
+            R->prob.shrink_to_fit();
+            R->reward.clear();
+            R->reward.shrink_to_fit();
+        }
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            R->t_end = now_s(S->t0);
-            R->state = 2;
-            S->in_use -= R->mem;
+            const double t = now_s(S->t0);
+            for (auto& R : B) {
+                R->t_end = t;
+                R->state = 2;
+                S->in_use -= R->mem;
+            }
             --S->running;
         }
         S->work_cv.notify_all();
@@ -257,8 +445,14 @@ gs_status gamesolve_server_submit(gs_server* S, const gs_request* req, int64_t* 
         R->spec.col = nullptr;
         R->spec.prob = nullptr;
         R->spec.reward = nullptr;
+    } else if (req->kind == 3) {
+        if (!random_game_args_ok(req->n, req->m1, req->m2, succ_of(*req)) || req->k < 0 ||
+            !(req->mu > 0.0 && req->mu < 1.0)) {
+            set_last_error("server_submit: invalid random game");
+            return GS_EINVAL;
+        }
     } else {
-        set_last_error("server_submit: kind must be 1 (Isaacs) or 2 (game)");
+        set_last_error("server_submit: kind must be 1 (Isaacs), 2 (game) or 3 (random game)");
         return GS_EINVAL;
     }
     R->mem = estimate_bytes(*req) + (req->kind == 2 ? R->col.size() * 24 : 0);

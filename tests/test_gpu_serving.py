@@ -184,3 +184,63 @@ def test_invalid_requests(gs):
         assert info["status"] == gs.GS_EINVAL
         with pytest.raises(gs.GameSolveError):
             srv.result(t)
+
+
+def test_small_games_batched(gs):
+    """Small games (below the grid-wide threshold) that wait together with the
+    same kind and action counts are solved as one batch: they share t_start,
+    and each result equals the same game solved alone (the batch runs the
+    one-block-per-game kernel each would run alone) and the oracle's."""
+    drawn = [(n, 900 + k) for k, n in enumerate((200, 350, 800, 1200, 2000, 3000, 640, 999))]
+    tables = [(n, synth.random_game(n, 1300 + k)) for k, n in enumerate((260, 500, 1800))]
+    with gs.GameServer(slots=1, precision="mixed") as srv:
+        t_big = srv.submit_isaacs(1023, 0, 4)     # holds the only slot while the rest queue
+        t_drawn = [srv.submit_random_game(n, 4, 4, seed, 0.99) for n, seed in drawn]
+        t_tab = [srv.submit_game(n, 4, 4, *tab) for n, tab in tables]
+        i_drawn = [srv.wait(t) for t in t_drawn]
+        i_tab = [srv.wait(t) for t in t_tab]
+        o_drawn = [srv.result(t) for t in t_drawn]
+        o_tab = [srv.result(t) for t in t_tab]
+        assert srv.wait(t_big)["status"] == gs.GS_OK
+        srv.result(t_big)
+    assert len({i["t_start"] for i in i_drawn}) == 1
+    assert len({i["t_start"] for i in i_tab}) == 1
+    for k, ((n, seed), info, (v, a, b)) in enumerate(zip(drawn, i_drawn, o_drawn)):
+        assert info["status"] == gs.GS_OK and info["stats"]["converged"] == 1, k
+        assert info["stats"]["outer"] >= 1 and info["n"] == n
+        with gs.GameSolver(precision="mixed") as s:
+            s.set_random_game(n, 4, 4, seed, 0.99)
+            st = s.solve()
+            a0, b0 = s.get_policy()
+            assert np.array_equal(v, s.get_value()), k
+            assert np.array_equal(a, a0) and np.array_equal(b, b0), k
+            assert info["stats"]["outer"] == st["outer"] and info["stats"]["systems"] == st["systems"]
+        if k < 3:
+            rp, col, prob, rew, mu = synth.random_game(n, seed)
+            check_against_oracle(v, a, b, oracle.policy_iteration(
+                game_from_csr(n, 4, 4, rp, col, prob, rew, mu)), ("drawn", k))
+    for k, ((n, tab), info, (v, a, b)) in enumerate(zip(tables, i_tab, o_tab)):
+        assert info["status"] == gs.GS_OK, k
+        v0, a0, b0 = alone(gs, ("game", n, tab))
+        assert np.array_equal(v, v0) and np.array_equal(a, a0) and np.array_equal(b, b0), k
+        check_against_oracle(v, a, b, oracle_result(("game", n, tab)), ("table", k))
+
+
+def test_bad_table_in_a_batch_fails_alone(gs):
+    """A rejected table among batched games fails only its own request."""
+    good = [synth.random_game(n, 1400 + n) for n in (300, 400)]
+    bad = list(synth.random_game(350, 1500))
+    bad[2] = bad[2].copy()
+    bad[2][5] = 1.5                                   # a probability above one
+    with gs.GameServer(slots=1, precision="mixed") as srv:
+        t_big = srv.submit_isaacs(1023, 0, 5)
+        tickets = [srv.submit_game(300, 4, 4, *good[0]), srv.submit_game(350, 4, 4, *bad),
+                   srv.submit_game(400, 4, 4, *good[1])]
+        infos = [srv.wait(t) for t in tickets]
+        srv.wait(t_big)
+        srv.result(t_big)
+        assert infos[1]["status"] == gs.GS_EINVAL
+        for t, info, (n, tab) in ((tickets[0], infos[0], (300, good[0])), (tickets[2], infos[2], (400, good[1]))):
+            assert info["status"] == gs.GS_OK
+            v, a, b = srv.result(t)
+            assert np.array_equal(v, alone(gs, ("game", n, tab))[0])
