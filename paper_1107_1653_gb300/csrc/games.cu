@@ -386,15 +386,21 @@ struct GridCtx {
 };
 
 // float64 residual rhs - (v - mu M v) -> C.r; returns |r|_inf, sets *vmax.
+// With jacobi0, also the correction's first Jacobi sweep from zero,
+// e = r / diag -> C.e (the V(1,1) cycle below starts from it).
 template <typename T, class Ctx>
-__device__ double check(const Game& G, const BatchOut& O, const double* v, Ctx& C, double* vmax) {
+__device__ double check(const Game& G, const BatchOut& O, const double* v, Ctx& C, double* vmax,
+                        bool jacobi0 = false) {
     // maxima on the bit patterns, conversions on the integer pipe
     unsigned long long rm = 0, vm = 0;
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
         const int64_t row = O.sel[G.x0 + i];
         const double r = O.rhs[G.x0 + i] - (v[i] - G.mu * row_sum(G, row, v));
-        if constexpr (sizeof(T) == 4) C.r[i] = f64_to_f32(r);
-        else C.r[i] = r;
+        T rt;
+        if constexpr (sizeof(T) == 4) rt = f64_to_f32(r);
+        else rt = r;
+        C.r[i] = rt;
+        if (jacobi0) C.e[i] = rt / diag_row<T>(G, O, i);
         const unsigned long long rb = bits_of(r) & 0x7fffffffffffffffull;
         const unsigned long long vb = bits_of(v[i]) & 0x7fffffffffffffffull;
         rm = rb > rm ? rb : rm;
@@ -460,6 +466,41 @@ __device__ bool cycle(const Game& G, const BatchOut& O, double* v, Ctx& C, T asu
     return C.sync();
 }
 
+// The same two-level cycle for one Jacobi sweep before and after the coarse
+// correction, in two passes over the rows (the first sweep e1 = r / diag came
+// with the residual check): A e1 gives the coarse correction c (e2 = e1 + c)
+// and, since A 1 is the leakage s of each row, A e2 = A e1 + c s without
+// another product; the post-sweep e = e2 + (r - A e2) / diag and v += e close
+// the cycle.  Same iteration as cycle() with nu1 = nu2 = 1.
+template <typename T, class Ctx>
+__device__ bool cycle11(const Game& G, const BatchOut& O, double* v, Ctx& C, T asum) {
+    double part = 0.0;
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
+        T Ae, d;
+        apply_row<T>(G, O, i, C.e, &Ae, &d);
+        const T q = C.r[i] - Ae;
+        if constexpr (sizeof(T) == 4) part += f32_to_f64(q);
+        else part += (double)q;
+        C.r[i] = q;   // r - A e1 (r itself is not needed again)
+        C.t[i] = d;
+    }
+    const double tot = C.sum(part);
+    if (C.failed()) return false;
+    const T c = asum != T(0) ? (T)(tot / (double)asum) : T(0);
+    float* v32 = O.v32 + G.x0;
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
+        const int64_t row = O.sel[G.x0 + i];
+        const T s = sizeof(T) == 4 ? (T)G.T.leak32[row] : (T)G.T.leak[row];
+        const T e = C.e[i] + c + (C.r[i] - c * s) / C.t[i];
+        double vi = v[i];
+        if constexpr (sizeof(T) == 4) vi += f32_to_f64(e);
+        else vi += e;
+        v[i] = vi;
+        v32[i] = f64_to_f32(vi);
+    }
+    return C.sync();
+}
+
 // Why a policy evaluation stopped.
 enum { kEvalExact = 0, kEvalInexact = 1, kEvalCapped = 2 };
 
@@ -472,7 +513,8 @@ __device__ int evaluate(const Game& G, const BatchOut& O, const BatchOpts& P, do
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) part += G.T.leak[O.sel[G.x0 + i]];
     const T asum = (T)C.sum(part);
     double vm;
-    double res = check<T>(G, O, v, C, &vm);
+    const bool v11 = P.nu1 == 1 && P.nu2 == 1;
+    double res = check<T>(G, O, v, C, &vm, v11);
     const double res0 = res;
     double prev = res;
     int slow = 0;
@@ -486,9 +528,10 @@ __device__ int evaluate(const Game& G, const BatchOut& O, const BatchOpts& P, do
             prev = fmin(prev, res);
         }
         if (cyc >= P.max_cycles) return kEvalCapped;
-        if (!cycle<T>(G, O, v, C, asum, P.nu1, P.nu2)) return kEvalExact;
+        if (!(v11 ? cycle11<T>(G, O, v, C, asum) : cycle<T>(G, O, v, C, asum, P.nu1, P.nu2)))
+            return kEvalExact;
         ++*cycles;
-        res = check<T>(G, O, v, C, &vm);
+        res = check<T>(G, O, v, C, &vm, v11);
     }
 }
 
