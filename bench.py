@@ -513,6 +513,21 @@ def run_profile(args):
     return 0
 
 
+def run_profile_game(args):
+    """One solve of a random game of n states (mixed precision) and nothing
+    else: a short command for ncu on the grid-wide game kernel."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1107_1653_gb300 as gs
+    n = args.profile_game
+    with gs.GameSolver(precision="mixed") as s:
+        s.set_random_game(n, 4, 4, 7 + n, 0.99)
+        st = s.solve()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_game": True, "n": n, **st}))
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -810,10 +825,14 @@ def main():
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--profile", action="store_true",
                     help="run one solve only (for ncu); prints the solve statistics")
+    ap.add_argument("--profile-game", type=int, default=0,
+                    help="one random-game solve of this many states (for ncu)")
     args = ap.parse_args()
     globals()["SIDE"] = args.side
     if args.profile:
         return run_profile(args)
+    if args.profile_game:
+        return run_profile_game(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -1201,9 +1201,12 @@ __global__ void k_coarse_game(GameTables T, int nc, int WA, const int* __restric
             atomicMax(wmax, m);
             continue;
         }
+        // an average of probabilities is at most one; the rounding of the
+        // members' weights 1/c can leave it an ulp above (all successors in
+        // one aggregate): clamped
         for (int q = 0; q < Wc; ++q) {
             ccol[row * Wc + q] = q < m ? keys[q] : I;
-            cprob[row * Wc + q] = q < m ? vals[q] : 0.0;
+            cprob[row * Wc + q] = q < m ? fmin(vals[q], 1.0) : 0.0;
         }
         crew[row] = rew;
     }

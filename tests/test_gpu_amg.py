@@ -154,6 +154,18 @@ def test_continuous_action_isaacs_matches_oracle(gs, side, prec):
     check(v, a, b, ref, TOL[prec])
 
 
+def test_continuous_action_isaacs_algebraic_famg(gs):
+    """Algebraic FAMGpi on the continuous-action example (63 x 63, mu = 1):
+    its aggregated coarse games average up to 16 x 81 rows whose successors
+    can all fall in one aggregate (a probability one ulp above 1 before the
+    clamp); it reaches the fixed point of flat AMGpi."""
+    tables = synth.iex1_tables(63, 16, 9)
+    v0, _, _, st0 = solve_tables(gs, tables, precision="mixed")
+    v1, _, _, st1 = solve_tables(gs, tables, precision="mixed", fmg=1)
+    assert st0["converged"] == 1 and st1["converged"] == 1
+    assert np.max(np.abs(v1 - v0)) <= 1e-9 * np.max(np.abs(v0))
+
+
 def test_continuous_action_isaacs_approaches_the_exact_solution(gs):
     """On finer grids (and a finer MIN grid) the GPU value approaches the
     paper's exact solution sin x1 sin x2 (Sec. 6.1)."""
