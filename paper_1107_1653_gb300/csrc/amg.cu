@@ -1337,16 +1337,22 @@ gs_status run_game_fmg(gs_solver* s, gs_solve_stats* stats) {
     GamePI R;
     s->level_stats.clear();
     std::vector<int> per;
+    bool handed = false;   // the level below left a finite iterate to interpolate
     for (int l = L - 1; l >= 0; --l) {
         const bool finest = l == 0;
-        if (l < L - 1) {
+        if (handed) {
             GameProblem& C = *lev[l + 1]->game;
             GameProblem& F = *lev[l]->game;
             k_fmg_game_interp<<<grid_for(F.n_total), 256, 0, st>>>(F.n_total, F.m1, aggs[l], C.v, C.alpha,
                                                                   C.beta, F.v, F.alpha, F.beta);
             GS_CHECK_LAUNCH();
         }
-        const GamePI r = amgpi_game(s, *lev[l], finest ? s->opt.eps : 0.0, l < L - 1);
+        const GamePI r = amgpi_game(s, *lev[l], finest ? s->opt.eps : 0.0, handed);
+        // a coarse game whose evaluation broke down (a policy pair without
+        // exit on an undiscounted coarse game gives a singular system: its
+        // iterate is not finite) hands nothing up: the next level starts
+        // from the default start
+        handed = std::isfinite(r.res);
         per.insert(per.end(), {(int)lev[l]->game->n_total, r.outer, r.systems});
         R.cycles += r.cycles;
         if (finest) {

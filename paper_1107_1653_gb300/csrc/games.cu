@@ -330,6 +330,45 @@ __device__ __forceinline__ T diag_row(const Game& G, const BatchOut& O, int64_t 
     return (sizeof(T) == 4 ? (T)G.T.leak32[row] : (T)G.T.leak[row]) + off;
 }
 
+// The same row operations on the slot-major copy of the selected rows (same
+// entries, same order: the same arithmetic).
+__device__ __forceinline__ double row_sum_c(const Compact& S, int64_t n, int64_t i, const double* v) {
+    double s0 = 0.0, s1 = 0.0;
+    int k = 0;
+    for (; k + 1 < S.K; k += 2) {
+        s0 = fma(S.p64[k * n + i], v[S.col[k * n + i]], s0);
+        s1 = fma(S.p64[(k + 1) * n + i], v[S.col[(k + 1) * n + i]], s1);
+    }
+    if (k < S.K) s0 = fma(S.p64[k * n + i], v[S.col[k * n + i]], s0);
+    return s0 + s1;
+}
+template <typename T>
+__device__ __forceinline__ void apply_row_c(const Game& G, const Compact& S, int64_t i, const T* e, T* Ae,
+                                            T* diag) {
+    const int64_t n = G.n;
+    const T ei = e[i];
+    const T mu = sizeof(T) == 4 ? (T)G.mu_f : (T)G.mu;
+    const T leak = sizeof(T) == 4 ? (T)S.leak32[i] : (T)S.leak64[i];
+    T acc = leak * ei, off = 0;
+    for (int k = 0; k < S.K; ++k) {
+        const int32_t c = S.col[k * n + i];
+        const T p = sizeof(T) == 4 ? (T)S.p32[k * n + i] : (T)S.p64[k * n + i];
+        acc += mu * p * (ei - e[c]);
+        if (c != i) off += mu * p;
+    }
+    *Ae = acc;
+    *diag = leak + off;
+}
+template <typename T>
+__device__ __forceinline__ T diag_row_c(const Game& G, const Compact& S, int64_t i) {
+    const int64_t n = G.n;
+    const T mu = sizeof(T) == 4 ? (T)G.mu_f : (T)G.mu;
+    T off = 0;
+    for (int k = 0; k < S.K; ++k)
+        if (S.col[k * n + i] != i) off += mu * (sizeof(T) == 4 ? (T)S.p32[k * n + i] : (T)S.p64[k * n + i]);
+    return (sizeof(T) == 4 ? (T)S.leak32[i] : (T)S.leak64[i]) + off;
+}
+
 // Execution context of one game's policy iteration: which threads share the
 // work, how they synchronise, and where the correction vectors live.  The
 // block context runs a game inside one thread block (vectors in shared
@@ -341,6 +380,7 @@ struct BlockCtx {
     T *r, *e, *t;      // correction right-hand side, correction, Jacobi work vector
     double* red_d;
     int* red_i;
+    Compact cp{};      // not used: the rows are read in place
     __device__ size_t begin() const { return threadIdx.x; }
     __device__ size_t stride() const { return blockDim.x; }
     __device__ bool sync() { __syncthreads(); return true; }
@@ -356,6 +396,7 @@ struct GridCtx {
     T *r, *e, *t;
     double* part;      // [2][gridDim.x] per-block partials (alternating)
     GridBarrier* bar;
+    Compact cp;        // slot-major selected rows (cp.col null: rows read in place)
     double* red_d;
     int flip;
     bool bad;
@@ -393,14 +434,15 @@ __device__ double check(const Game& G, const BatchOut& O, const double* v, Ctx& 
                         bool jacobi0 = false) {
     // maxima on the bit patterns, conversions on the integer pipe
     unsigned long long rm = 0, vm = 0;
+    const bool cpt = C.cp.col != nullptr;
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
-        const int64_t row = O.sel[G.x0 + i];
-        const double r = O.rhs[G.x0 + i] - (v[i] - G.mu * row_sum(G, row, v));
+        const double Mv = cpt ? row_sum_c(C.cp, G.n, i, v) : row_sum(G, O.sel[G.x0 + i], v);
+        const double r = O.rhs[G.x0 + i] - (v[i] - G.mu * Mv);
         T rt;
         if constexpr (sizeof(T) == 4) rt = f64_to_f32(r);
         else rt = r;
         C.r[i] = rt;
-        if (jacobi0) C.e[i] = rt / diag_row<T>(G, O, i);
+        if (jacobi0) C.e[i] = rt / (cpt ? diag_row_c<T>(G, C.cp, i) : diag_row<T>(G, O, i));
         const unsigned long long rb = bits_of(r) & 0x7fffffffffffffffull;
         const unsigned long long vb = bits_of(v[i]) & 0x7fffffffffffffffull;
         rm = rb > rm ? rb : rm;
@@ -474,10 +516,12 @@ __device__ bool cycle(const Game& G, const BatchOut& O, double* v, Ctx& C, T asu
 // the cycle.  Same iteration as cycle() with nu1 = nu2 = 1.
 template <typename T, class Ctx>
 __device__ bool cycle11(const Game& G, const BatchOut& O, double* v, Ctx& C, T asum) {
+    const bool cpt = C.cp.col != nullptr;
     double part = 0.0;
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
         T Ae, d;
-        apply_row<T>(G, O, i, C.e, &Ae, &d);
+        if (cpt) apply_row_c<T>(G, C.cp, i, C.e, &Ae, &d);
+        else apply_row<T>(G, O, i, C.e, &Ae, &d);
         const T q = C.r[i] - Ae;
         if constexpr (sizeof(T) == 4) part += f32_to_f64(q);
         else part += (double)q;
@@ -489,8 +533,13 @@ __device__ bool cycle11(const Game& G, const BatchOut& O, double* v, Ctx& C, T a
     const T c = asum != T(0) ? (T)(tot / (double)asum) : T(0);
     float* v32 = O.v32 + G.x0;
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
-        const int64_t row = O.sel[G.x0 + i];
-        const T s = sizeof(T) == 4 ? (T)G.T.leak32[row] : (T)G.T.leak[row];
+        T s;
+        if (cpt) {
+            s = sizeof(T) == 4 ? (T)C.cp.leak32[i] : (T)C.cp.leak64[i];
+        } else {
+            const int64_t row = O.sel[G.x0 + i];
+            s = sizeof(T) == 4 ? (T)G.T.leak32[row] : (T)G.T.leak[row];
+        }
         const T e = C.e[i] + c + (C.r[i] - c * s) / C.t[i];
         double vi = v[i];
         if constexpr (sizeof(T) == 4) vi += f32_to_f64(e);
@@ -509,11 +558,26 @@ enum { kEvalExact = 0, kEvalInexact = 1, kEvalCapped = 2 };
 template <typename T, class Ctx>
 __device__ int evaluate(const Game& G, const BatchOut& O, const BatchOpts& P, double* v, Ctx& C,
                         double rel_tol, int* cycles) {
-    double part = 0.0;
-    for (int64_t i = C.begin(); i < G.n; i += C.stride()) part += G.T.leak[O.sel[G.x0 + i]];
-    const T asum = (T)C.sum(part);
-    double vm;
     const bool v11 = P.nu1 == 1 && P.nu2 == 1;
+    if (!v11) C.cp.col = nullptr;   // the general cycle reads the rows in place
+    double part = 0.0;
+    for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
+        const int64_t row = O.sel[G.x0 + i];
+        part += G.T.leak[row];
+        if (C.cp.col) {   // the selected rows, slot-major
+            const Compact& S = C.cp;
+            const int64_t k0 = row * S.K;
+            for (int k = 0; k < S.K; ++k) {
+                S.col[k * G.n + i] = G.T.col[k0 + k];
+                S.p64[k * G.n + i] = G.T.prob[k0 + k];
+                S.p32[k * G.n + i] = prob_at<float>(G.T, k0 + k);
+            }
+            S.leak64[i] = G.T.leak[row];
+            S.leak32[i] = G.T.leak32[row];
+        }
+    }
+    const T asum = (T)C.sum(part);   // (its barrier also publishes the gathered rows)
+    double vm;
     double res = check<T>(G, O, v, C, &vm, v11);
     const double res0 = res;
     double prev = res;
@@ -665,6 +729,7 @@ __global__ void __launch_bounds__(kThreads) k_game_pi_grid(const __grid_constant
     C.t = (T*)W.t;
     C.part = W.part;
     C.bar = W.bar;
+    C.cp = W.cp;
     C.red_d = red_d;
     C.flip = 0;
     C.bad = false;

@@ -63,11 +63,25 @@ struct BatchArgs {
     const int* order;       // queue position -> game, `count` entries (one-block kernel)
 };
 
+// The selected rows of a game's policy-fixed system gathered slot-major
+// (entry k of state i at [k * n + i]) at the start of each evaluation, so that
+// the cycles read them coalesced and without the selection's indirection.
+// Only for rows of one length K (col null: not used).
+struct Compact {
+    int32_t* col;
+    float* p32;          // the relaxation's copy (float32, or bfloat16 widened)
+    double* p64;
+    float* leak32;
+    double* leak64;
+    int K;
+};
+
 // Work vectors of the grid-wide single-game kernel (global memory).
 struct GridWork {
     void *r, *e, *t;     // n elements each (float32 or float64)
     double* part;        // 2 x (blocks) per-block partials
     GridBarrier* bar;    // zeroed before the launch
+    Compact cp;          // the selected rows, slot-major (cp.col null: rows read in place)
 };
 
 // Action counts: MAX at most kGameMaxM1, MIN at most kGameMaxM2 (policies are

@@ -148,6 +148,16 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
         GS_CUDA(cudaMemcpy(&rp1, row_ptr + 1, sizeof(int64_t), cudaMemcpyDefault));
         G->k_uniform = rp1 > 0 ? rp1 : 0;
         T = G->tables();
+        // the grid-wide kernel gathers each evaluation's rows slot-major
+        if (G->grid && G->k_uniform > 0 && G->k_uniform <= 64) {
+            const size_t m = (size_t)n_total * G->k_uniform;
+            G->cp.col = ar.alloc<int32_t>(m);
+            G->cp.p32 = ar.alloc<float>(m);
+            G->cp.p64 = ar.alloc<double>(m);
+            G->cp.leak32 = ar.alloc<float>(n_total);
+            G->cp.leak64 = ar.alloc<double>(n_total);
+            G->cp.K = (int)G->k_uniform;
+        }
     }
     launch_game_prepare(T, count, G->st_off, rows, G->mu, G->leak, G->leak32,
                         G->prob_bf16 ? nullptr : G->prob32,
@@ -243,7 +253,7 @@ gs_status run_games(gs_solver* s, gs_solve_stats* stats) {
     if (G.grid) GS_CUDA(cudaMemsetAsync(G.bar, 0, sizeof(GridBarrier), st));
     GS_CUDA(cudaEventRecord(e0, st));
     if (G.grid) {
-        GridWork W{G.wr, G.we, G.wt, G.part, G.bar};
+        GridWork W{G.wr, G.we, G.wt, G.part, G.bar, G.cp};
         const int blocks = std::min(game_grid_blocks(G.n_total, s->opt.grid_blocks), 152 * 64);
         launch_game_pi_grid(B, W, blocks, mixed, st);
     } else {

@@ -58,7 +58,9 @@ size_t estimate_bytes(const gs_request& r) {
         return n * 220 + (64 << 10);
     }
     const size_t rows = (size_t)r.n * r.m1 * r.m2;
-    const size_t base = rows * 32 + (size_t)r.n * 60 + (64 << 10);
+    // per row: leakage, reward, policy copies; per state: vectors and the
+    // grid kernel's slot-major copy of the selected rows (8 entries)
+    const size_t base = rows * 32 + (size_t)r.n * 200 + (64 << 10);
     return r.kind == 3 ? base + 2 * rows * (8 + 12 * (size_t)succ_of(r)) : base;
 }
 

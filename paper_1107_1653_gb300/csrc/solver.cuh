@@ -88,6 +88,7 @@ struct GameProblem {
     bool grid = false;                     // one large game on the whole grid
     double *wr = nullptr, *we = nullptr, *wt = nullptr, *part = nullptr;
     GridBarrier* bar = nullptr;
+    Compact cp{};                          // grid: the selected rows slot-major (rows of one length)
     std::vector<int> stats_h;
     std::vector<double> res_h;
     // algebraic multigrid path (options.game_solver = 1): the current
