@@ -332,25 +332,32 @@ __device__ __forceinline__ T diag_row(const Game& G, const BatchOut& O, int64_t 
 
 // The same row operations on the slot-major copy of the selected rows (same
 // entries, same order: the same arithmetic).
+// (KC > 0: rows of exactly KC entries, known at compile time, so that a
+// row's loads are issued together; KC = 0: S.K at run time.)
+template <int KC>
 __device__ __forceinline__ double row_sum_c(const Compact& S, int64_t n, int64_t i, const double* v) {
+    const int K = KC > 0 ? KC : S.K;
     double s0 = 0.0, s1 = 0.0;
     int k = 0;
-    for (; k + 1 < S.K; k += 2) {
+#pragma unroll
+    for (; k + 1 < K; k += 2) {
         s0 = fma(S.p64[k * n + i], v[S.col[k * n + i]], s0);
         s1 = fma(S.p64[(k + 1) * n + i], v[S.col[(k + 1) * n + i]], s1);
     }
-    if (k < S.K) s0 = fma(S.p64[k * n + i], v[S.col[k * n + i]], s0);
+    if (k < K) s0 = fma(S.p64[k * n + i], v[S.col[k * n + i]], s0);
     return s0 + s1;
 }
-template <typename T>
+template <typename T, int KC>
 __device__ __forceinline__ void apply_row_c(const Game& G, const Compact& S, int64_t i, const T* e, T* Ae,
                                             T* diag) {
+    const int K = KC > 0 ? KC : S.K;
     const int64_t n = G.n;
     const T ei = e[i];
     const T mu = sizeof(T) == 4 ? (T)G.mu_f : (T)G.mu;
     const T leak = sizeof(T) == 4 ? (T)S.leak32[i] : (T)S.leak64[i];
     T acc = leak * ei, off = 0;
-    for (int k = 0; k < S.K; ++k) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
         const int32_t c = S.col[k * n + i];
         const T p = sizeof(T) == 4 ? (T)S.p32[k * n + i] : (T)S.p64[k * n + i];
         acc += mu * p * (ei - e[c]);
@@ -359,12 +366,14 @@ __device__ __forceinline__ void apply_row_c(const Game& G, const Compact& S, int
     *Ae = acc;
     *diag = leak + off;
 }
-template <typename T>
+template <typename T, int KC>
 __device__ __forceinline__ T diag_row_c(const Game& G, const Compact& S, int64_t i) {
+    const int K = KC > 0 ? KC : S.K;
     const int64_t n = G.n;
     const T mu = sizeof(T) == 4 ? (T)G.mu_f : (T)G.mu;
     T off = 0;
-    for (int k = 0; k < S.K; ++k)
+#pragma unroll
+    for (int k = 0; k < K; ++k)
         if (S.col[k * n + i] != i) off += mu * (sizeof(T) == 4 ? (T)S.p32[k * n + i] : (T)S.p64[k * n + i]);
     return (sizeof(T) == 4 ? (T)S.leak32[i] : (T)S.leak64[i]) + off;
 }
@@ -434,15 +443,20 @@ __device__ double check(const Game& G, const BatchOut& O, const double* v, Ctx& 
                         bool jacobi0 = false) {
     // maxima on the bit patterns, conversions on the integer pipe
     unsigned long long rm = 0, vm = 0;
-    const bool cpt = C.cp.col != nullptr;
+    const int cpt = C.cp.col == nullptr ? 0 : C.cp.K == 8 ? 2 : 1;   // 2: rows of 8 entries
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
-        const double Mv = cpt ? row_sum_c(C.cp, G.n, i, v) : row_sum(G, O.sel[G.x0 + i], v);
+        const double Mv = cpt == 2   ? row_sum_c<8>(C.cp, G.n, i, v)
+                          : cpt == 1 ? row_sum_c<0>(C.cp, G.n, i, v)
+                                     : row_sum(G, O.sel[G.x0 + i], v);
         const double r = O.rhs[G.x0 + i] - (v[i] - G.mu * Mv);
         T rt;
         if constexpr (sizeof(T) == 4) rt = f64_to_f32(r);
         else rt = r;
         C.r[i] = rt;
-        if (jacobi0) C.e[i] = rt / (cpt ? diag_row_c<T>(G, C.cp, i) : diag_row<T>(G, O, i));
+        if (jacobi0)
+            C.e[i] = rt / (cpt == 2   ? diag_row_c<T, 8>(G, C.cp, i)
+                           : cpt == 1 ? diag_row_c<T, 0>(G, C.cp, i)
+                                      : diag_row<T>(G, O, i));
         const unsigned long long rb = bits_of(r) & 0x7fffffffffffffffull;
         const unsigned long long vb = bits_of(v[i]) & 0x7fffffffffffffffull;
         rm = rb > rm ? rb : rm;
@@ -516,11 +530,12 @@ __device__ bool cycle(const Game& G, const BatchOut& O, double* v, Ctx& C, T asu
 // the cycle.  Same iteration as cycle() with nu1 = nu2 = 1.
 template <typename T, class Ctx>
 __device__ bool cycle11(const Game& G, const BatchOut& O, double* v, Ctx& C, T asum) {
-    const bool cpt = C.cp.col != nullptr;
+    const int cpt = C.cp.col == nullptr ? 0 : C.cp.K == 8 ? 2 : 1;   // 2: rows of 8 entries
     double part = 0.0;
     for (int64_t i = C.begin(); i < G.n; i += C.stride()) {
         T Ae, d;
-        if (cpt) apply_row_c<T>(G, C.cp, i, C.e, &Ae, &d);
+        if (cpt == 2) apply_row_c<T, 8>(G, C.cp, i, C.e, &Ae, &d);
+        else if (cpt == 1) apply_row_c<T, 0>(G, C.cp, i, C.e, &Ae, &d);
         else apply_row<T>(G, O, i, C.e, &Ae, &d);
         const T q = C.r[i] - Ae;
         if constexpr (sizeof(T) == 4) part += f32_to_f64(q);
