@@ -729,6 +729,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_games_pi(const __grid_constant
         C.t = C.e + B.max_n;
         C.red_d = red_d;
         C.red_i = red_i;
+        if (B.cp.col) {   // this game's part of the slot-major rows
+            const int64_t x0 = B.st_off[g], K = B.cp.K;
+            C.cp = Compact{B.cp.col + x0 * K, B.cp.p32 + x0 * K, B.cp.p64 + x0 * K, B.cp.leak32 + x0,
+                           B.cp.leak64 + x0, B.cp.K};
+        }
         solve_game<T>(B, g, C);
     }
 }

@@ -51,6 +51,19 @@ struct BatchOpts {
     double eps, lin_tol, pi_rtol;
 };
 
+// The selected rows of a game's policy-fixed system gathered slot-major
+// (entry k of state i at [k * n + i], n the game's states) at the start of
+// each evaluation, so that the cycles read them coalesced and without the
+// selection's indirection.  Only for rows of one length K (col null: not used).
+struct Compact {
+    int32_t* col;
+    float* p32;          // the relaxation's copy (float32, or bfloat16 widened)
+    double* p64;
+    float* leak32;
+    double* leak64;
+    int K;
+};
+
 struct BatchArgs {
     GameTables T;
     BatchOut out;
@@ -61,19 +74,8 @@ struct BatchArgs {
     const double* mu;       // per game
     int* queue;             // work counter (zeroed before the launch)
     const int* order;       // queue position -> game, `count` entries (one-block kernel)
-};
-
-// The selected rows of a game's policy-fixed system gathered slot-major
-// (entry k of state i at [k * n + i]) at the start of each evaluation, so that
-// the cycles read them coalesced and without the selection's indirection.
-// Only for rows of one length K (col null: not used).
-struct Compact {
-    int32_t* col;
-    float* p32;          // the relaxation's copy (float32, or bfloat16 widened)
-    double* p64;
-    float* leak32;
-    double* leak64;
-    int K;
+    Compact cp;             // one-block kernel: slot-major rows of all games, game g's at
+                            // state offset st_off[g] (cp.col null: rows read in place)
 };
 
 // Work vectors of the grid-wide single-game kernel (global memory).

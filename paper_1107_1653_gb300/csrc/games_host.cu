@@ -148,8 +148,8 @@ std::unique_ptr<Problem> build_game_problem(gs_solver* s, int count, int m1, int
         GS_CUDA(cudaMemcpy(&rp1, row_ptr + 1, sizeof(int64_t), cudaMemcpyDefault));
         G->k_uniform = rp1 > 0 ? rp1 : 0;
         T = G->tables();
-        // the grid-wide kernel gathers each evaluation's rows slot-major
-        if (G->grid && G->k_uniform > 0 && G->k_uniform <= 64) {
+        // each evaluation of the two-level path gathers its rows slot-major
+        if (G->k_uniform > 0 && G->k_uniform <= 64 && s->opt.game_solver == 0) {
             const size_t m = (size_t)n_total * G->k_uniform;
             G->cp.col = ar.alloc<int32_t>(m);
             G->cp.p32 = ar.alloc<float>(m);
@@ -244,6 +244,7 @@ gs_status run_games(gs_solver* s, gs_solve_stats* stats) {
     B.mu = G.mu;
     B.queue = G.queue;
     B.order = G.order;
+    B.cp = G.cp;
     const int shape = G.grid ? 0 : tuned_shape(s, G, B, mixed);
     G.shape = shape;
     cudaEvent_t e0, e1;
