@@ -105,8 +105,9 @@ typedef struct {
     int32_t cycle_kernel;  /* Isaacs grids' V-cycles: 0 (default) tiled where they apply (each
                               thread block runs a whole smoothing leg of a tile of a level in
                               shared memory, with a halo recomputed by its neighbours: about
-                              two grid-wide barriers per level and cycle; the finest level
-                              keeps one phase per colour); 1 one grid-wide phase per
+                              two grid-wide barriers per level and cycle; the finest level,
+                              and coarse levels of side above 511 (255 in float64), keep one
+                              phase per colour); 1 one grid-wide phase per
                               relaxation colour.  Same arithmetic per point.  W-cycles always
                               take the latter. */
     int32_t game_solver;   /* policy evaluation of a single finite game (gamesolve_set_game):

@@ -80,8 +80,11 @@ size_t tail_smem_bytes(const SolveArgs& a);
 // needs (the tail's and the largest tile's, whichever is more).
 constexpr int kTiledSmemMax = 110 * 1024;
 // Largest coarse level side the tiled kernel tiles: a 1023 x 1023 coarse level
-// (the 2047 x 2047 grid's first) measured faster one phase per colour.
+// (the 2047 x 2047 grid's first) measured faster one phase per colour; in
+// float64 (tiles of at most 8 x 8 next-level points: shared memory) already a
+// 511 x 511 one (1023^2 float64 solve 19.8 -> 17.7 ms).
 constexpr int kTiledMaxSide = 511;
+constexpr int kTiledMaxSideF64 = 255;
 size_t tiled_smem_bytes(const SolveArgs& a);
 
 // Tile sides of a tiled launch for `workers` tile-taking thread blocks.

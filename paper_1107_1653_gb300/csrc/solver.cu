@@ -373,7 +373,8 @@ int linear_solve(gs_solver* s, IsaacsGrid& g, Counters& cnt, double rel_tol, boo
         set_tile_sides(a, std::max(1, blocks - 1));
     }
     a.tile_from = 1;
-    while (a.tile_from < a.tail && a.L[a.tile_from].side > kTiledMaxSide) ++a.tile_from;
+    const int tile_max = a.mixed ? kTiledMaxSide : kTiledMaxSideF64;
+    while (a.tile_from < a.tail && a.L[a.tile_from].side > tile_max) ++a.tile_from;
     // levels from smem_from on are staged in block 0's shared memory, as many as fit
     a.smem_from = std::max(a.tail, 1);
     while (a.smem_from < a.nlev && tail_smem_bytes(a) > (size_t)kTailSmemMax)
