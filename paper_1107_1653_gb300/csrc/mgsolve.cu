@@ -1519,7 +1519,6 @@ size_t tiled_smem_bytes(const SolveArgs& a) {
     auto side = [](int tc, int sc, int sf, int H) {
         return (size_t)std::min(sf, 2 * std::min(tc, sc) + 1 + 2 * H);
     };
-    auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
     size_t need = tail_smem_bytes(a);
     for (int l = std::max(1, a.tile_from); l < a.tail; ++l) {
         const LevelArgs& L = a.L[l];
