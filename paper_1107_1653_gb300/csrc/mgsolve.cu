@@ -173,7 +173,12 @@ __device__ void relax_coarse(const LevelArgs& L, int c, bool zero, size_t start,
 // u_{l+1} = 0.  With `fuse` the coarse level's first relaxation colour (its
 // C points, relaxed from the zero start) is done here too: such a point's
 // Gauss-Seidel value is f / diag, from data this item already has.
-template <typename T, typename W, class Op>
+// skip1 (the finest level after at least one pre-smoothing sweep): the
+// red-black sweep ends with colour 1, whose points' residuals that update has
+// just made zero (up to rounding), so only the colour-0 points' residuals
+// (the C point and the cell corners of each coarse point's stencil) are
+// formed; the edge points' are taken as zero.
+template <typename T, typename W, bool skip1, class Op>
 __device__ void restrict_with(const Op& op, const LevelArgs& L, const LevelArgs& C, bool fuse,
                               size_t start, size_t stride) {
     const int sc = L.sc;
@@ -193,6 +198,7 @@ __device__ void restrict_with(const Op& op, const LevelArgs& L, const LevelArgs&
         for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
             for (int di = -1; di <= 1; ++di) {
+                if (skip1 && ((di + dj) & 1)) continue;
                 acc += (T)restrict_weight(P, sc, I, J, di, dj) * op.resid(f, u, 2 * I + 1 + di, 2 * J + 1 + dj);
             }
         fc[t] = acc;
@@ -236,8 +242,9 @@ __device__ void relax_level(const SolveArgs& a, const LevelArgs& L, int l, int c
 template <typename T, typename W>
 __device__ void restrict_level(const SolveArgs& a, const LevelArgs& L, const LevelArgs& C, int l,
                                bool fuse, size_t start, size_t stride) {
-    if (l == 0) restrict_with<T, W>(L0Op<T>{a.K, a.code, L.side}, L, C, fuse, start, stride);
-    else restrict_with<T, W>(L9Op<T, W>{(const W*)L.A, L.n, L.side}, L, C, fuse, start, stride);
+    if (l == 0 && a.nu1 > 0) restrict_with<T, W, true>(L0Op<T>{a.K, a.code, L.side}, L, C, fuse, start, stride);
+    else if (l == 0) restrict_with<T, W, false>(L0Op<T>{a.K, a.code, L.side}, L, C, fuse, start, stride);
+    else restrict_with<T, W, false>(L9Op<T, W>{(const W*)L.A, L.n, L.side}, L, C, fuse, start, stride);
 }
 
 // Relaxation sweeps on level l before and after its coarse-grid correction
