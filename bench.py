@@ -100,7 +100,7 @@ def mg_cycle_bytes(n: int, prec: str, launches: int, cycles: int, sweeps: int = 
 # DRAM bytes per cycle-kernel launch from the committed capture of the current
 # kernel (profiles/k_mg_cycles_tiled_isaacs1023_mixed.md): read + write, with
 # ncu's cache flush before the launch.  Keyed by (side, precision).
-PROFILED_TRAFFIC = {(1023, "mixed"): 46.41e6 + 2.09e6}
+PROFILED_TRAFFIC = {(1023, "mixed"): 46.23e6 + 2.01e6}
 
 
 def load_peaks():
