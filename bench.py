@@ -657,6 +657,8 @@ def run_ours(args):
     # the precision workload: 2047^2, seed 3, every precision, against the oracle
     if not args.no_2047 and SIDE == 1023 and world == 1:
         line["side_2047"] = run_2047(args, stream, peak, peak_kind)
+    if world == 1 and SIDE == 1023 and not args.no_obstacle:
+        line["obstacle_1023"] = run_obstacle_1023(args, stream)
 
     # end to end through the C-ABI with host buffers
     if not args.no_e2e:
@@ -748,6 +750,47 @@ def run_2047(args, stream, peak, peak_kind):
     return out
 
 
+def run_obstacle_1023(args, stream):
+    """The obstacle configuration: 1023 x 1023 obstacle Isaacs game, seed 2,
+    flat AMGpi against FAMGpi from 31 x 31 (eps_l = 0.01 h_l^2, eps = 0 on the
+    finest level), FP64 and mixed, each timed (L2 flushed between solves), and
+    every result's error against the stored FP64 oracle run (sampled states)."""
+    import torch
+    import paper_1107_1653_gb300 as gs
+    samples = load_samples("isaacs1023_obstacle_seed2_samples.txt")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for prec in ("fp64", "mixed"):
+        for fmg in (0, 1):
+            s = gs.GameSolver(precision=prec, fmg=fmg, fmg_side=31, fmg_c=0.01, stream=stream,
+                              **ISAACS_CYCLE)
+            s.set_isaacs_grid(SIDE, 1, SEED)
+            s.solve()
+            ts, st = [], None
+            for _ in range(2 if not fmg else 3):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = s.solve()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            v = s.get_value()
+            s.close()
+            ms = statistics.mean(ts)
+            out["%s_%s" % (prec, "famg" if fmg else "flat")] = {
+                "ms_per_solve": ms, "solves_per_s": 1000.0 / ms, "outer": st["outer"],
+                "systems": st["systems"], "cycles": st["cycles"],
+                "err_vs_oracle_sampled": err_vs_samples(v, samples)}
+    out["config"] = {"side": SIDE, "variant": "obstacle", "seed": SEED, "cycle": cycle_label(ISAACS_CYCLE),
+                     "famg": "from 31 x 31, eps_l = 0.01 h_l^2, eps = 0 on the finest level",
+                     "l2": "flushed between solves (256 MiB write)",
+                     "oracle": "isaacs1023_obstacle_seed2_samples.txt (1,026 states)"}
+    return out
+
+
 def run_line(args):
     """The two-sided stopping game on a line (Sec. 6.3) at 2049 points: FAMGpi
     (eps_l = 1e-2 h_l^2, eps = 1e-10, as the paper's table) timed over the
@@ -814,6 +857,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-2047", action="store_true",
                     help="skip the 2047^2 precision configuration's block")
+    ap.add_argument("--no-obstacle", action="store_true",
+                    help="skip the 1023^2 obstacle block (flat AMGpi against FAMGpi)")
     ap.add_argument("--side", type=int, default=SIDE)
     ap.add_argument("--workload", default="isaacs", choices=["isaacs", "batch", "serving", "line"],
                     help="isaacs: the metric's 1023^2 solve (default); batch: 4096 random "
