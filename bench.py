@@ -425,13 +425,12 @@ def run_batch(args):
     return 0
 
 
-def run_serving(args):
+def serving_line(args):
     """C5: Poisson stream of requests, 70% Isaacs grids (sides 63..1023) and
     30% random games (n ~ U{1e3..1e6}), mixed precision, arrival rate 80% of
-    the closed-loop capacity; p50/p99 latency and solves/s."""
+    the closed-loop capacity; p50/p99 latency and solves/s (as a dict)."""
     import numpy as np
     import torch
-    torch.cuda.set_device(0)
     import paper_1107_1653_gb300 as gs
     rng = np.random.default_rng(5)
     # every game request is a fresh random game n ~ U{1e3..1e6} given by its
@@ -495,7 +494,13 @@ def run_serving(args):
         "p99_ms_games": float(np.percentile(lat_g, 99) * 1e3) if len(lat_g) else None,
         "completed": ok, "makespan_s": makespan,
     }
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_serving(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(serving_line(args)), flush=True)
     return 0
 
 
@@ -659,6 +664,14 @@ def run_ours(args):
         line["side_2047"] = run_2047(args, stream, peak, peak_kind)
     if world == 1 and SIDE == 1023 and not args.no_obstacle:
         line["obstacle_1023"] = run_obstacle_1023(args, stream)
+    # the batching and serving rows' workloads, compact
+    if world == 1 and SIDE == 1023 and not args.no_workloads:
+        line["batch_4096"] = batch_block(stream)
+        sv = serving_line(args)
+        line["serving"] = {k: sv[k] for k in ("value", "unit", "p50_ms", "p99_ms", "p50_ms_isaacs",
+                                              "p99_ms_isaacs", "p50_ms_games", "p99_ms_games",
+                                              "completed", "makespan_s")}
+        line["serving"]["config"] = sv["config"]
 
     # end to end through the C-ABI with host buffers
     if not args.no_e2e:
@@ -748,6 +761,62 @@ def run_2047(args, stream, peak, peak_kind):
                      "l2": "flushed between solves (256 MiB write)",
                      "oracle": "isaacs2047_plain_seed3_samples.txt (1,026 states)"}
     return out
+
+
+def batch_block(stream, count=4096, seed=4, warmup=2, steps=3):
+    """The 4096-game batch (C4) with its tables drawn on the device
+    (gamesolve_random_game, game g from the stream seed XOR g, as
+    synth.random_game_batch draws them on the host): games/s over a few
+    solves (L2 flushed between them), iteration counts, convergence."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1107_1653_gb300 as gs
+    sizes = synth.batch_game_sizes(count, seed)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    R, K = 16, 8
+    rows = int(off[-1]) * R
+    dev = torch.device("cuda", torch.cuda.current_device())
+    col = torch.empty(rows * K, dtype=torch.int32, device=dev)
+    prob = torch.empty(rows * K, dtype=torch.float64, device=dev)
+    rew = torch.empty(rows, dtype=torch.float64, device=dev)
+    scratch = torch.empty(int(sizes.max()) * R + 1, dtype=torch.int64, device=dev)
+    for g in range(count):
+        r0 = int(off[g]) * R
+        code = gs.lib.gamesolve_random_game(int(sizes[g]), 4, 4, K, synth.batch_game_seed(seed, g),
+                                            scratch.data_ptr(), col[r0 * K:].data_ptr(),
+                                            prob[r0 * K:].data_ptr(), rew[r0:].data_ptr(), stream.cuda_stream)
+        if code != gs.GS_OK:
+            raise RuntimeError("gamesolve_random_game failed")
+    rp = torch.arange(rows + 1, dtype=torch.int64, device=dev) * K   # rows of 8 entries
+    mu = np.full(count, 0.99)
+    s = gs.GameSolver(precision="mixed", stream=stream)
+    s.set_game_batch(off, 4, 4, rp, col, prob, rew, mu)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        s.solve()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    gst, gres = s.batch_stats()
+    s.close()
+    sec = statistics.mean(times)
+    return {"games_per_s": count / sec, "ms_per_batch": sec * 1e3, "states_per_s": float(off[-1]) / sec,
+            "warmup": warmup, "steps": steps,
+            "config": {"games": count, "states": int(off[-1]), "seed": seed, "precision": "mixed",
+                       "tables": "drawn on the device (gamesolve_random_game), resident before timing",
+                       "l2": "flushed between solves (256 MiB write)"},
+            "outer_max": int(gst[:, 0].max()), "systems": int(gst[:, 1].sum()),
+            "cycles": int(gst[:, 2].sum()), "converged": int(gst[:, 3].min()),
+            "res_max": float(gres.max())}
 
 
 def run_obstacle_1023(args, stream):
@@ -859,6 +928,8 @@ def main():
                     help="skip the 2047^2 precision configuration's block")
     ap.add_argument("--no-obstacle", action="store_true",
                     help="skip the 1023^2 obstacle block (flat AMGpi against FAMGpi)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the compact 4096-game batch and serving-stream blocks")
     ap.add_argument("--side", type=int, default=SIDE)
     ap.add_argument("--workload", default="isaacs", choices=["isaacs", "batch", "serving", "line"],
                     help="isaacs: the metric's 1023^2 solve (default); batch: 4096 random "
