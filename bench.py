@@ -672,6 +672,10 @@ def run_ours(args):
                                               "p99_ms_isaacs", "p50_ms_games", "p99_ms_games",
                                               "completed", "makespan_s")}
         line["serving"]["config"] = sv["config"]
+        _, lo = line_results(args)
+        line["stopping_line_2049"] = {"famgpi": lo["famgpi"], "amgpi_flat": lo["amgpi"],
+                                      "paper_e_inf": 1.16e-7, "paper_e_l2": 7.40e-8}
+        line["continuous_actions_127"] = iex1_block(stream)
 
     # end to end through the C-ABI with host buffers
     if not args.no_e2e:
@@ -819,6 +823,39 @@ def batch_block(stream, count=4096, seed=4, warmup=2, steps=3):
             "res_max": float(gres.max())}
 
 
+def iex1_block(stream, side=127, ka=32, kb=13):
+    """The Isaacs example with continuous action sets (Sec. 6.1), its action
+    sets discretised (ka directions on MAX's unit circle, a kb x kb grid of
+    MIN's b), lambda = 0: flat AMGpi on the tables path with algebraic
+    multigrid, timed once after a warm-up solve, and the error against the
+    exact solution sin x1 sin x2."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1107_1653_gb300 as gs
+    n, m1, m2, rp, col, prob, rew, mu = synth.iex1_tables(side, ka, kb)
+    with gs.GameSolver(precision="mixed", game_solver=1, stream=stream) as s:
+        s.set_game(n, m1, m2, rp, col, prob, rew, mu)
+        s.solve()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = s.solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v = s.get_value()
+    h = 1.0 / (side + 1)
+    idx = np.arange(n)
+    x1, x2 = (idx % side + 1) * h, (idx // side + 1) * h
+    e = v - np.sin(x1) * np.sin(x2)
+    return {"ms_per_solve": e0.elapsed_time(e1), "outer": st["outer"], "systems": st["systems"],
+            "cycles": st["cycles"], "e_inf": float(np.max(np.abs(e))),
+            "e_l2": float(np.sqrt(np.mean(e * e))),
+            "config": {"side": side, "max_actions": m1, "min_actions": m2, "rows": int(len(rew)),
+                       "precision": "mixed", "game_solver": "algebraic multigrid"}}
+
+
 def run_obstacle_1023(args, stream):
     """The obstacle configuration: 1023 x 1023 obstacle Isaacs game, seed 2,
     flat AMGpi against FAMGpi from 31 x 31 (eps_l = 0.01 h_l^2, eps = 0 on the
@@ -860,7 +897,7 @@ def run_obstacle_1023(args, stream):
     return out
 
 
-def run_line(args):
+def line_results(args):
     """The two-sided stopping game on a line (Sec. 6.3) at 2049 points: FAMGpi
     (eps_l = 1e-2 h_l^2, eps = 1e-10, as the paper's table) timed over the
     steps, flat AMGpi once; the discretisation errors against the exact
@@ -868,7 +905,6 @@ def run_line(args):
     import numpy as np
     import torch
     import synth
-    torch.cuda.set_device(0)
     import paper_1107_1653_gb300 as gs
     points = 2049
     c, p1, p2, vl, vr = synth.stopping_line(points)
@@ -902,6 +938,13 @@ def run_line(args):
                      "cycles": st["cycles"], "fmg_levels": st["fmg_levels"],
                      "e_inf": float(np.max(np.abs(e))), "e_l2": float(np.sqrt(np.mean(e * e))),
                      "res_inf": st["res_inf"]}
+    return points, out
+
+
+def run_line(args):
+    import torch
+    torch.cuda.set_device(0)
+    points, out = line_results(args)
     line = {"metric": "two-sided stopping game (Sec. 6.3) solves/s at 2049 points, FAMGpi",
             "value": 1000.0 / out["famgpi"]["ms"], "unit": "solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["famgpi"]["ms"],
