@@ -676,6 +676,7 @@ def run_ours(args):
         line["stopping_line_2049"] = {"famgpi": lo["famgpi"], "amgpi_flat": lo["amgpi"],
                                       "paper_e_inf": 1.16e-7, "paper_e_l2": 7.40e-8}
         line["continuous_actions_127"] = iex1_block(stream)
+        line["tables_famg_line_513"] = tables_famg_block(stream)
 
     # end to end through the C-ABI with host buffers
     if not args.no_e2e:
@@ -854,6 +855,34 @@ def iex1_block(stream, side=127, ka=32, kb=13):
             "e_l2": float(np.sqrt(np.mean(e * e))),
             "config": {"side": side, "max_actions": m1, "min_actions": m2, "rows": int(len(rew)),
                        "precision": "mixed", "game_solver": "algebraic multigrid"}}
+
+
+def tables_famg_block(stream, points=513):
+    """Full multilevel policy iteration for a game given only by its tables
+    (algebraic FAMGpi: coarse games by aggregation) against flat AMGpi, both
+    on the algebraic-multigrid path, FP64: the Sec. 6.3 game at `points`
+    points given as CSR tables; time, MAX iterations on the finest level."""
+    import torch
+    import synth
+    import paper_1107_1653_gb300 as gs
+    n, m1, m2, rp, col, prob, rew, mu = synth.two_stop_tables(points)
+    out = {}
+    for name, fmg in (("famgpi", 1), ("amgpi_flat", 0)):
+        with gs.GameSolver(precision="fp64", game_solver=1, fmg=fmg, max_outer=100000,
+                           max_inner=100000, stream=stream) as s:
+            s.set_game(n, m1, m2, rp, col, prob, rew, mu)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = s.solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        out[name] = {"ms": e0.elapsed_time(e1), "outer_finest": st["outer"], "systems_finest": st["systems"],
+                     "cycles": st["cycles"], "fmg_levels": st["fmg_levels"], "converged": st["converged"]}
+    out["config"] = {"game": "Sec. 6.3 two-sided stopping game as CSR tables", "points": points,
+                     "precision": "fp64", "game_solver": "algebraic multigrid"}
+    return out
 
 
 def run_obstacle_1023(args, stream):
