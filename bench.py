@@ -895,6 +895,29 @@ def run_obstacle_1023(args, stream):
     samples = load_samples("isaacs1023_obstacle_seed2_samples.txt")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     out = {}
+    # the plain grid under FAMGpi (its flat solve is the headline), c = 0.1
+    plain = load_samples("isaacs1023_plain_seed2_samples.txt")
+    for prec in ("fp64", "mixed"):
+        s = gs.GameSolver(precision=prec, fmg=1, fmg_side=31, fmg_c=0.1, stream=stream, **ISAACS_CYCLE)
+        s.set_isaacs_grid(SIDE, 0, SEED)
+        s.solve()
+        ts, st = [], None
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = s.solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        v = s.get_value()
+        s.close()
+        ms = statistics.mean(ts)
+        out["plain_%s_famg" % prec] = {"ms_per_solve": ms, "solves_per_s": 1000.0 / ms, "outer": st["outer"],
+                                       "systems": st["systems"], "cycles": st["cycles"],
+                                       "err_vs_oracle_sampled": err_vs_samples(v, plain)}
     for prec in ("fp64", "mixed"):
         for fmg in (0, 1):
             s = gs.GameSolver(precision=prec, fmg=fmg, fmg_side=31, fmg_c=0.01, stream=stream,
@@ -919,10 +942,11 @@ def run_obstacle_1023(args, stream):
                 "ms_per_solve": ms, "solves_per_s": 1000.0 / ms, "outer": st["outer"],
                 "systems": st["systems"], "cycles": st["cycles"],
                 "err_vs_oracle_sampled": err_vs_samples(v, samples)}
-    out["config"] = {"side": SIDE, "variant": "obstacle", "seed": SEED, "cycle": cycle_label(ISAACS_CYCLE),
-                     "famg": "from 31 x 31, eps_l = 0.01 h_l^2, eps = 0 on the finest level",
+    out["config"] = {"side": SIDE, "variant": "obstacle (plain_* entries: the plain grid)", "seed": SEED,
+                     "cycle": cycle_label(ISAACS_CYCLE),
+                     "famg": "from 31 x 31, eps_l = c h_l^2 (c = 0.01 obstacle, 0.1 plain), eps = 0 on the finest level",
                      "l2": "flushed between solves (256 MiB write)",
-                     "oracle": "isaacs1023_obstacle_seed2_samples.txt (1,026 states)"}
+                     "oracle": "isaacs1023_obstacle_seed2_samples.txt and isaacs1023_plain_seed2_samples.txt (1,026 states each)"}
     return out
 
 
