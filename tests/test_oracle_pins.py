@@ -508,3 +508,48 @@ def test_iex1_converges_to_the_exact_solution():
         u = exact_value((idx % side + 1) * h, (idx // side + 1) * h)
         errs.append(np.max(np.abs(res.v - u)))
     assert errs[0] > errs[1] > errs[2] and errs[2] < 3e-4, errs
+
+
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_random_game_recipe(k):
+    """synth.random_game follows its documented counter-based recipe, which
+    the device generator (gamesolve_random_game) restates: row rho's
+    successors are the ranks picked by draws rho*17 + t (t < k), stepped past
+    the earlier picks; its probabilities the normalised -log1p(-u) of draws
+    rho*17 + 8 + t (pairwise sum for k = 8, left to right otherwise, the last
+    one set to one minus the others); its reward 2u - 1 of draw rho*17 + 16.
+    Recomputed here row by row in plain Python from synth.uniform01."""
+    import math
+    n, seed, m1, m2 = 37, 1234567, 2, 3
+    rp, col, prob, rew, _ = synth.random_game(n, seed, m1=m1, m2=m2, k=k)
+    assert np.array_equal(rp, np.arange(n * m1 * m2 + 1) * k)
+    for rho in range(n * m1 * m2):
+        base = rho * 17
+        u = [float(x) for x in synth.uniform01(seed, np.arange(base, base + 17, dtype=np.uint64))]
+        picks, taken = [], []
+        for t in range(k):
+            idx = min(int(u[t] * (n - t)), n - t - 1)
+            for p in sorted(taken):
+                if idx >= p:
+                    idx += 1
+            picks.append(idx)
+            taken.append(idx)
+        e = [-math.log1p(-u[8 + t]) for t in range(k)]
+        if k == 8:
+            tot = ((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7]))
+        else:
+            tot = 0.0
+            for x in e:
+                tot += x
+        p = [x / tot for x in e]
+        if k > 1:
+            head = 0.0
+            for x in p[:-1]:
+                head += x
+            p[-1] = max(1.0 - head, 0.0)
+        else:
+            p = [1.0]
+        order = sorted(range(k), key=lambda t: picks[t])
+        assert list(col[rho * k:(rho + 1) * k]) == [picks[t] for t in order]
+        assert np.allclose(prob[rho * k:(rho + 1) * k], [p[t] for t in order], rtol=0, atol=4e-16)
+        assert rew[rho] == u[16] * 2.0 - 1.0
