@@ -1034,7 +1034,7 @@ def main():
     ap.add_argument("--games", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--burst", type=int, default=64)
-    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--slots", type=int, default=2)
     ap.add_argument("--profile", action="store_true",
                     help="run one solve only (for ncu); prints the solve statistics")
     ap.add_argument("--profile-game", type=int, default=0,
