@@ -454,7 +454,11 @@ typedef struct {
 } gs_ticket_info;
 
 /* Starts `slots` worker threads on the current device, each creating a solver
- * with `opt` (NULL = defaults) on its own stream.  mem_budget: device bytes the
+ * with `opt` (NULL = defaults) on its own stream.  Unless opt->grid_blocks is
+ * set, a slot's grid-wide launches are capped at 2 x (SMs) / slots blocks; on
+ * a mixed stream of Isaacs grids and large games 2 slots served the most
+ * requests per second (whole-GPU launches, one request's host steps hidden
+ * behind the other's kernels).  mem_budget: device bytes the
  * requests in flight may hold together (0 = half the free memory); a request
  * larger than the budget runs when nothing else is in flight.
  * Errors: GS_EINVAL (slots outside [1, 64] or bad options), GS_ECUDA. */
