@@ -324,7 +324,7 @@ class GameSolver:
 class GameServer:
     """Owns one gs_server (continuous batching of solve requests)."""
 
-    def __init__(self, slots=4, mem_budget=0, **opts):
+    def __init__(self, slots=2, mem_budget=0, **opts):
         self.opts = default_options(**opts)
         h = _P()
         _check(lib.gamesolve_server_create(ctypes.byref(h), ctypes.byref(self.opts), slots,
