@@ -481,15 +481,43 @@ __global__ void k_transpose_sort(int nc, int WR, const int* __restrict__ cnt, in
 // fine points of R's row ascending, then A's slots, then P's slots.  count
 // pass (write == false): distinct columns only; fill pass: the row in ELL
 // form with the diagonal first and the rest in order of first appearance.
-__global__ void k_rap(int nc, const AmgLevelArgs F, int Wc, bool write, int* __restrict__ wmax,
-                      int* __restrict__ overflow, int* __restrict__ ccol, double* __restrict__ c64,
-                      float* __restrict__ c32) {
+// Threads per block of the Galerkin product and the size of each thread's
+// hash table over its coarse row's columns (a power of two above the row cap).
+constexpr int kRapThreads = 16;
+constexpr int kRapHash = 128;
+static_assert(kRapHash > kAmgRowCap, "hash table must exceed the row cap");
+
+__global__ void __launch_bounds__(kRapThreads) k_rap(int nc, const AmgLevelArgs F, int Wc, bool write,
+                                                     int* __restrict__ wmax, int* __restrict__ overflow,
+                                                     int* __restrict__ ccol, double* __restrict__ c64,
+                                                     float* __restrict__ c32) {
+    // each thread's row lives in shared memory: its columns in order of first
+    // appearance (keys, vals) and a hash table column -> position, so that
+    // adding a product costs one probe instead of a scan of the row (the sums
+    // are formed in the same order as by a scan: the same values)
+    __shared__ int s_keys[kRapThreads][kAmgRowCap];
+    __shared__ double s_vals[kRapThreads][kAmgRowCap];
+    __shared__ int s_hk[kRapThreads][kRapHash];            // column + 1, 0 = empty
+    __shared__ unsigned char s_hq[kRapThreads][kRapHash];  // its position in keys/vals
+    int* keys = s_keys[threadIdx.x];
+    double* vals = s_vals[threadIdx.x];
+    int* hk = s_hk[threadIdx.x];
+    unsigned char* hq = s_hq[threadIdx.x];
+    auto slot = [&](int J) {
+        unsigned h = ((unsigned)J * 2654435761u) >> (32 - 7);
+        while (hk[h] != 0 && hk[h] != J + 1) h = (h + 1) & (kRapHash - 1);
+        return h;
+    };
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
-        int keys[kAmgRowCap];
-        double vals[kAmgRowCap];
+        for (int h = 0; h < kRapHash; ++h) hk[h] = 0;
         int m = 1;
         keys[0] = I;
         vals[0] = 0.0;
+        {
+            const unsigned h = slot(I);
+            hk[h] = I + 1;
+            hq[h] = 0;
+        }
         bool over = false;
         for (int r = 0; r < F.WR; ++r) {
             const int i = F.rcol[(size_t)I * F.WR + r];
@@ -503,13 +531,20 @@ __global__ void k_rap(int nc, const AmgLevelArgs F, int Wc, bool write, int* __r
                     const int J = F.pcol[(size_t)k * F.WP + p];
                     if (J < 0) break;
                     const double add = wa * F.p64[(size_t)k * F.WP + p];
-                    int q = 0;
-                    while (q < m && keys[q] != J) ++q;
-                    if (q == m) {
-                        if (m == kAmgRowCap) { over = true; continue; }
-                        keys[m] = J;
-                        vals[m] = 0.0;
-                        ++m;
+                    const unsigned h = slot(J);
+                    int q;
+                    if (hk[h] == 0) {
+                        if (m == kAmgRowCap) {
+                            over = true;
+                            continue;
+                        }
+                        q = m++;
+                        keys[q] = J;
+                        vals[q] = 0.0;
+                        hk[h] = J + 1;
+                        hq[h] = (unsigned char)q;
+                    } else {
+                        q = hq[h];
                     }
                     vals[q] += add;
                 }
@@ -1489,7 +1524,8 @@ void AmgHierarchy::build(const GameTables& T, const int64_t* sel, double mu, int
         // Galerkin coarse operator: count pass, then fill
         const AmgLevelArgs FA = args_of(F);
         GS_CUDA(cudaMemsetAsync(scal, 0, sizeof(int) * 8, st));
-        k_rap<<<grid(nc), 128, 0, st>>>(nc, FA, 0, false, scal, scal + 1, nullptr, nullptr, nullptr);
+        const unsigned rap_blocks = (unsigned)std::max(1, std::min((nc + kRapThreads - 1) / kRapThreads, 152 * 64));
+        k_rap<<<rap_blocks, kRapThreads, 0, st>>>(nc, FA, 0, false, scal, scal + 1, nullptr, nullptr, nullptr);
         GS_CHECK_LAUNCH();
         read_scal();
         if (hs[1]) break;   // a Galerkin row too wide: relax this level as the coarsest
@@ -1499,7 +1535,7 @@ void AmgHierarchy::build(const GameTables& T, const int64_t* sel, double mu, int
         C.col = ar->alloc<int>((size_t)nc * C.W);
         C.a64 = ar->alloc<double>((size_t)nc * C.W);
         C.a32 = ar->alloc<float>((size_t)nc * C.W);
-        k_rap<<<grid(nc), 128, 0, st>>>(nc, FA, C.W, true, scal, scal + 1, C.col, C.a64, C.a32);
+        k_rap<<<rap_blocks, kRapThreads, 0, st>>>(nc, FA, C.W, true, scal, scal + 1, C.col, C.a64, C.a32);
         GS_CHECK_LAUNCH();
         lv.push_back(C);
     }
