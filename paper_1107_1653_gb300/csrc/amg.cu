@@ -219,6 +219,20 @@ __global__ void k_colour_mark(int n, int W, const int* __restrict__ col, const i
 
 // Round k: local maxima take colour k; counts per (colour, C/F) class and the
 // points left uncoloured.
+// The points of each smoother class (C or F, colour k) counted, then listed
+// (class order: C colours, then F colours; order within a class is free: its
+// points are mutually uncoupled).
+__global__ void k_class_count(int n, int ncolour, const int16_t* __restrict__ colour,
+                              const int8_t* __restrict__ cf, int* __restrict__ cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&cnt[(cf[i] == 1 ? 0 : ncolour) + colour[i]], 1);
+}
+__global__ void k_class_scatter(int n, int ncolour, const int16_t* __restrict__ colour,
+                                const int8_t* __restrict__ cf, int* __restrict__ cursor, int* __restrict__ ord) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        ord[atomicAdd(&cursor[(cf[i] == 1 ? 0 : ncolour) + colour[i]], 1)] = i;
+}
+
 __global__ void k_colour_select(int n, int k, int16_t* __restrict__ colour, int* __restrict__ notmax,
                                 const int8_t* __restrict__ cf, int* __restrict__ cls, int* __restrict__ left) {
     int lc = 0, nC = 0, nF = 0;
@@ -683,30 +697,99 @@ __device__ void amg_relax(const AmgLevelArgs& L, const T* u, T* t, const T* f, i
 }
 
 // Gauss-Seidel on the points of colour k in the C (which = 1) or F (which =
-// 0) set, in place: they are mutually uncoupled.
+// 0) set, in place: they are mutually uncoupled.  The class's points are read
+// from its list (thread index gt of gs).
 template <typename T>
 __device__ void amg_gs(const AmgLevelArgs& L, T* u, const T* f, int k, int which, size_t gt, size_t gs) {
-    for (size_t i = gt; i < (size_t)L.n; i += gs) {
-        if (L.colour[i] != k || (L.cf[i] == 1) != (which == 1)) continue;
+    const int key = (which == 1 ? 0 : L.ncolour) + k;
+    const size_t b = (size_t)L.kofs[key], e = (size_t)L.kofs[key + 1];
+    for (size_t x = b + gt; x < e; x += gs) {
+        const int i = L.ord[x];
         T Au, d;
-        amg_row<T>(L, (int)i, u, &Au, &d);
+        amg_row<T>(L, i, u, &Au, &d);
         u[i] += (f[i] - Au) / d;
     }
 }
 
 // One C/F Gauss-Seidel sweep, colour by colour (C points first when c_first).
-template <typename T>
-__device__ bool amg_sweep(const AmgLevelArgs& L, T* u, const T* f, bool c_first, const GridSync& G,
-                          size_t gt, size_t gs) {
+// Who runs a phase and how it ends: the whole grid with a grid barrier, or
+// thread block 0 alone with a block barrier (small levels).
+// gx numbers the threads block-minor (thread t of block b is t * blocks + b),
+// so that a short list is spread over all the blocks, not packed into the
+// first few.
+struct GridPh {
+    const GridSync* G;
+    size_t gt, gs, gx;
+    __device__ bool sync() const { return G->sync(); }
+};
+struct BlockPh {
+    size_t gt, gs, gx;
+    __device__ bool sync() const {
+        __syncthreads();
+        return true;
+    }
+};
+
+template <typename T, class Ph>
+__device__ bool amg_sweep(const AmgLevelArgs& L, T* u, const T* f, bool c_first, const Ph& ph) {
     for (int half = 0; half < 2; ++half) {
         const int which = (half == 0) == c_first ? 1 : 0;
         for (int k = 0; k < L.ncolour; ++k) {
             const unsigned long long m = which ? L.cmaskC[k >> 6] : L.cmaskF[k >> 6];
             if (!(m >> (k & 63) & 1ull)) continue;   // no point of this set has colour k
-            amg_gs<T>(L, u, f, k, which, gt, gs);
-            if (!G.sync()) return false;
+            amg_gs<T>(L, u, f, k, which, ph.gx, ph.gs);
+            if (!ph.sync()) return false;
         }
     }
+    return true;
+}
+
+// Down leg of level l: C/F relaxation, residual, restriction f_{l+1} = R r_l,
+// u_{l+1} = 0.
+template <typename T, class Ph>
+__device__ bool amg_down(const AmgSolveArgs& a, int l, T* const* u, T* const* t, const Ph& ph) {
+    const AmgLevelArgs& L = a.L[l];
+    const T* f = (const T*)L.f;
+    for (int s = 0; s < a.nu1; ++s)
+        if (!amg_sweep<T>(L, u[l], f, true, ph)) return false;
+    for (size_t i = ph.gt; i < (size_t)L.n; i += ph.gs) {
+        T Au, d;
+        amg_row<T>(L, (int)i, u[l], &Au, &d);
+        t[l][i] = f[i] - Au;
+    }
+    if (!ph.sync()) return false;
+    const AmgLevelArgs& C = a.L[l + 1];
+    T* fc = (T*)C.f;
+    for (size_t I = ph.gt; I < (size_t)C.n; I += ph.gs) {
+        T acc = 0;
+        for (int r = 0; r < L.WR; ++r) {
+            const int i = L.rcol[I * L.WR + r];
+            if (i < 0) break;
+            acc += rw<T>(L, I * L.WR + r) * t[l][i];
+        }
+        fc[I] = acc;
+        u[l + 1][I] = T(0);
+    }
+    return ph.sync();
+}
+
+// Up leg of level l: u_l += P u_{l+1}, then F/C relaxation.
+template <typename T, class Ph>
+__device__ bool amg_up(const AmgSolveArgs& a, int l, T* const* u, const Ph& ph) {
+    const AmgLevelArgs& L = a.L[l];
+    const T* f = (const T*)L.f;
+    for (size_t i = ph.gt; i < (size_t)L.n; i += ph.gs) {
+        T acc = 0;
+        for (int p = 0; p < L.WP; ++p) {
+            const int J = L.pcol[i * L.WP + p];
+            if (J < 0) break;
+            acc += pw<T>(L, i * L.WP + p) * u[l + 1][J];
+        }
+        u[l][i] += acc;
+    }
+    if (!ph.sync()) return false;
+    for (int s = 0; s < a.nu2; ++s)
+        if (!amg_sweep<T>(L, u[l], f, false, ph)) return false;
     return true;
 }
 
@@ -744,6 +827,39 @@ __device__ void amg_check(const AmgSolveArgs& a, int slot, T* f0, T* u0, size_t 
 
 // V-cycles on the correction of a.v, with the float64 stopping test between
 // cycles (same rules as the Isaacs grids' kernel).
+// The coarsest level: its inverse applied by the thread block that has
+// `inverse_block` set (block 0), or (coarsening stopped early) Jacobi sweeps
+// over the phase's threads.
+template <typename T, class Ph>
+__device__ bool amg_coarsest(const AmgSolveArgs& a, T** u, T** t, double* fs, const Ph& ph, bool inverse_block) {
+    const int Lc = a.nlev - 1;
+    const AmgLevelArgs& C = a.L[Lc];
+    if (a.coarse_sweeps > 0) {
+        for (size_t i = ph.gt; i < (size_t)C.n; i += ph.gs) u[Lc][i] = T(0);
+        if (!ph.sync()) return false;
+        for (int k = 0; k < a.coarse_sweeps; ++k) {
+            amg_relax<T>(C, u[Lc], t[Lc], (const T*)C.f, 2, ph.gt, ph.gs);
+            T* sw = u[Lc];
+            u[Lc] = t[Lc];
+            t[Lc] = sw;
+            if (!ph.sync()) return false;
+        }
+        return true;
+    }
+    if (inverse_block) {
+        const T* f = (const T*)C.f;
+        for (int k = threadIdx.x; k < C.n; k += blockDim.x) fs[k] = (double)f[k];
+        __syncthreads();
+        for (int r = threadIdx.x; r < C.n; r += blockDim.x) {
+            double acc = 0.0;
+            for (int k = 0; k < C.n; ++k) acc += a.inv[(size_t)r * C.n + k] * fs[k];
+            u[Lc][r] = (T)acc;
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kAmgThreads) k_amg_cycles(const __grid_constant__ AmgSolveArgs a) {
     __shared__ double fs[kAmgCoarsest];
@@ -790,72 +906,26 @@ __global__ void __launch_bounds__(kAmgThreads) k_amg_cycles(const __grid_constan
             a.out->rmax[slot ^ 1] = 0ull;
             a.out->vmax[slot ^ 1] = 0ull;
         }
-        // down: C/F relaxation, residual, restriction f_{l+1} = R r_l, u_{l+1} = 0
-        for (int l = 0; l < Lc; ++l) {
-            const AmgLevelArgs& L = a.L[l];
-            const T* f = (const T*)L.f;
-            for (int s = 0; s < a.nu1; ++s)
-                if (!amg_sweep<T>(L, u[l], f, true, G, gt, gs)) return;
-            for (size_t i = gt; i < (size_t)L.n; i += gs) {
-                T Au, d;
-                amg_row<T>(L, (int)i, u[l], &Au, &d);
-                t[l][i] = f[i] - Au;
+        // down legs of the grid-wide levels, then the small levels (a.tail
+        // and below) by thread block 0 alone, then the up legs
+        const GridPh gp{&G, gt, gs, (size_t)threadIdx.x * gridDim.x + blockIdx.x};
+        const int tl = a.tail < Lc ? a.tail : Lc;
+        for (int l = 0; l < tl; ++l)
+            if (!amg_down<T>(a, l, u, t, gp)) return;
+        if (a.tail <= Lc) {
+            if (blockIdx.x == 0) {
+                const BlockPh bp{threadIdx.x, blockDim.x, threadIdx.x};
+                for (int l = a.tail; l < Lc; ++l) amg_down<T>(a, l, u, t, bp);
+                amg_coarsest<T>(a, u, t, fs, bp, true);
+                for (int l = Lc - 1; l >= a.tail; --l) amg_up<T>(a, l, u, bp);
             }
             if (!G.sync()) return;
-            const AmgLevelArgs& C = a.L[l + 1];
-            T* fc = (T*)C.f;
-            for (size_t I = gt; I < (size_t)C.n; I += gs) {
-                T acc = 0;
-                for (int r = 0; r < L.WR; ++r) {
-                    const int i = L.rcol[I * L.WR + r];
-                    if (i < 0) break;
-                    acc += rw<T>(L, I * L.WR + r) * t[l][i];
-                }
-                fc[I] = acc;
-                u[l + 1][I] = T(0);
-            }
+        } else {
+            if (!amg_coarsest<T>(a, u, t, fs, gp, blockIdx.x == 0)) return;
             if (!G.sync()) return;
         }
-        // coarsest: its inverse by block 0, or (coarsening stopped early)
-        // Jacobi sweeps over the whole grid
-        if (a.coarse_sweeps > 0) {
-            const AmgLevelArgs& C = a.L[Lc];
-            for (size_t i = gt; i < (size_t)C.n; i += gs) u[Lc][i] = T(0);
-            if (!G.sync()) return;
-            for (int k = 0; k < a.coarse_sweeps; ++k) {
-                amg_relax<T>(C, u[Lc], t[Lc], (const T*)C.f, 2, gt, gs);
-                T* sw = u[Lc]; u[Lc] = t[Lc]; t[Lc] = sw;
-                if (!G.sync()) return;
-            }
-        } else if (blockIdx.x == 0) {
-            const AmgLevelArgs& C = a.L[Lc];
-            const T* f = (const T*)C.f;
-            for (int k = threadIdx.x; k < C.n; k += blockDim.x) fs[k] = (double)f[k];
-            __syncthreads();
-            for (int r = threadIdx.x; r < C.n; r += blockDim.x) {
-                double acc = 0.0;
-                for (int k = 0; k < C.n; ++k) acc += a.inv[(size_t)r * C.n + k] * fs[k];
-                u[Lc][r] = (T)acc;
-            }
-        }
-        if (!G.sync()) return;
-        // up: u_l += P u_{l+1}, then F/C relaxation
-        for (int l = Lc - 1; l >= 0; --l) {
-            const AmgLevelArgs& L = a.L[l];
-            const T* f = (const T*)L.f;
-            for (size_t i = gt; i < (size_t)L.n; i += gs) {
-                T acc = 0;
-                for (int p = 0; p < L.WP; ++p) {
-                    const int J = L.pcol[i * L.WP + p];
-                    if (J < 0) break;
-                    acc += pw<T>(L, i * L.WP + p) * u[l + 1][J];
-                }
-                u[l][i] += acc;
-            }
-            if (!G.sync()) return;
-            for (int s = 0; s < a.nu2; ++s)
-                if (!amg_sweep<T>(L, u[l], f, false, G, gt, gs)) return;
-        }
+        for (int l = tl - 1; l >= 0; --l)
+            if (!amg_up<T>(a, l, u, gp)) return;
         // v += e and the next residual check
         for (size_t i = gt; i < (size_t)a.L[0].n; i += gs) a.v[i] += (double)u[0][i];
         if (!G.sync()) return;
@@ -1587,10 +1657,29 @@ void AmgHierarchy::colour_level(AmgLevelMem& F, int* flag, int* scal, int* hs, R
         if (hs[5]) F.cmaskC[k >> 6] |= 1ull << (k & 63);
         if (hs[6]) F.cmaskF[k >> 6] |= 1ull << (k & 63);
         F.ncolour = k + 1;
-        if (hs[2] == 0) return;
+        if (hs[2] == 0) break;
     }
-    set_last_error("AMG: more than %d colours needed for the smoother", kAmgMaxColours);
-    throw Error{GS_EINVAL};
+    if (hs[2] != 0) {
+        set_last_error("AMG: more than %d colours needed for the smoother", kAmgMaxColours);
+        throw Error{GS_EINVAL};
+    }
+    // the points listed by class, so that a colour phase visits only its own
+    const int nk = 2 * F.ncolour;
+    int* cnt = ar->alloc<int>(nk);
+    GS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * nk, st));
+    k_class_count<<<g, 256, 0, st>>>(nf, F.ncolour, F.colour, F.cf, cnt);
+    GS_CHECK_LAUNCH();
+    std::vector<int> hc(nk), ofs(nk + 1, 0);
+    GS_CUDA(cudaMemcpyAsync(hc.data(), cnt, sizeof(int) * nk, cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < nk; ++k) ofs[k + 1] = ofs[k] + hc[k];
+    F.kofs = ar->alloc<int>(nk + 1);
+    F.ord = ar->alloc<int>(std::max(1, nf));
+    GS_CUDA(cudaMemcpyAsync(F.kofs, ofs.data(), sizeof(int) * (nk + 1), cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(cnt, ofs.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+    k_class_scatter<<<g, 256, 0, st>>>(nf, F.ncolour, F.colour, F.cf, cnt, F.ord);
+    GS_CHECK_LAUNCH();
+    GS_CUDA(cudaStreamSynchronize(st));   // the host offsets' buffer is released on return
 }
 
 AmgLevelArgs AmgHierarchy::args_of(const AmgLevelMem& m) {
@@ -1610,6 +1699,8 @@ AmgLevelArgs AmgHierarchy::args_of(const AmgLevelMem& m) {
     A.r32 = m.r32;
     A.cf = m.cf;
     A.colour = m.colour;
+    A.ord = m.ord;
+    A.kofs = m.kofs;
     A.ncolour = m.ncolour;
     A.cmaskC[0] = m.cmaskC[0];
     A.cmaskC[1] = m.cmaskC[1];
@@ -1637,6 +1728,12 @@ int AmgHierarchy::solve(double* v, const double* rhs, const gs_options& opt, dou
     a.v = v;
     a.inv = inv;
     a.coarse_sweeps = coarse_sweeps;
+    // the small levels' phases are short: one block with block barriers beats
+    // the grid barrier there (needs the coarsest inverse: the Jacobi sweeps
+    // swap their vectors per thread)
+    a.tail = a.nlev;
+    if (coarse_sweeps == 0)
+        while (a.tail > 0 && lv[a.tail - 1].n <= kAmgTailN) --a.tail;
     a.bar = bar_state;
     a.out = dout;
     for (int l = 0; l < a.nlev; ++l) a.L[l] = args_of(lv[l]);
@@ -1651,6 +1748,7 @@ int AmgHierarchy::solve(double* v, const double* rhs, const gs_options& opt, dou
     const int ps = std::max(1, per_sm[mixed ? 0 : 1]);
     int nb = (int)std::min<size_t>((size_t)ps * sms, ((size_t)lv[0].n + kAmgThreads - 1) / kAmgThreads);
     if (opt.grid_blocks > 0) nb = std::min(nb, opt.grid_blocks);
+    if (a.tail == 0) nb = 1;   // the whole hierarchy is small
     nb = std::max(1, nb);
     GS_CUDA(cudaMemsetAsync(bar_state, 0, sizeof(GridBarrier), st));
     GS_CUDA(cudaMemsetAsync(dout, 0, sizeof(AmgOut), st));

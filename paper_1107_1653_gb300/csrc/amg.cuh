@@ -18,6 +18,8 @@ constexpr int kAmgInvSmem = 64;         // inverted in shared memory up to this 
 constexpr int kAmgRowCap = 96;          // entries of a coarse row the set-up accumulates
 constexpr int kAmgCoarseSweeps = 30;    // Jacobi sweeps on a coarsest level too large to invert
 constexpr int kAmgMaxColours = 128;     // colours of the Gauss-Seidel smoother's colouring
+constexpr int kAmgTailN = 2048;         // levels this small run in one thread block, with
+                                        // block barriers instead of grid barriers
 
 // One level of the hierarchy, rows in ELL form (slot 0 holds the diagonal;
 // unused slots have column -1 and value 0).
@@ -37,6 +39,8 @@ struct AmgLevelArgs {
     const float* r32;
     const int8_t* cf;       // 1 C point, 2 F point (this level's splitting)
     const int16_t* colour;  // colour of each point (smoother)
+    const int* ord;         // the points ordered by class: C points by colour, then F points
+    const int* kofs;        // class k (C: colour k, F: ncolour + colour k) is ord[kofs[k], kofs[k+1])
     int ncolour;
     unsigned long long cmaskC[2], cmaskF[2];   // colours that hold C (F) points
     void* u;                // V-cycle unknown (float32 in the mixed path, else float64)
@@ -58,6 +62,8 @@ struct AmgSolveArgs {
     double* v;              // fine iterate (float64)
     const double* inv;      // inverse of the coarsest operator (n_L <= kAmgCoarsest)
     int coarse_sweeps;      // > 0: the coarsest level is relaxed this many times instead
+    int tail;               // levels tail .. nlev - 1 are cycled by thread block 0 alone
+                            // (nlev: none)
     GridBarrier* bar;
     AmgOut* out;
     AmgLevelArgs L[kAmgMaxLevels];
@@ -77,6 +83,8 @@ struct AmgLevelMem {
     float* r32 = nullptr;
     int8_t* cf = nullptr;
     int16_t* colour = nullptr;
+    int* ord = nullptr;
+    int* kofs = nullptr;
     int ncolour = 0;
     unsigned long long cmaskC[2] = {0, 0}, cmaskF[2] = {0, 0};
     void *u = nullptr, *f = nullptr, *t = nullptr;
