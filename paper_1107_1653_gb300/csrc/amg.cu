@@ -1698,7 +1698,6 @@ AmgLevelArgs AmgHierarchy::args_of(const AmgLevelMem& m) {
     A.r64 = m.r64;
     A.r32 = m.r32;
     A.cf = m.cf;
-    A.colour = m.colour;
     A.ord = m.ord;
     A.kofs = m.kofs;
     A.ncolour = m.ncolour;

@@ -38,7 +38,6 @@ struct AmgLevelArgs {
     const double* r64;
     const float* r32;
     const int8_t* cf;       // 1 C point, 2 F point (this level's splitting)
-    const int16_t* colour;  // colour of each point (smoother)
     const int* ord;         // the points ordered by class: C points by colour, then F points
     const int* kofs;        // class k (C: colour k, F: ncolour + colour k) is ord[kofs[k], kofs[k+1])
     int ncolour;
