@@ -905,13 +905,6 @@ __device__ __forceinline__ void for_sublattice(const Valid& r, int px, int py, F
     }
 }
 
-// Points with (i + j) = c (mod 2) of the rectangle (the fine level's colours).
-template <class F>
-__device__ __forceinline__ void for_redblack(const Valid& r, int c, F&& f) {
-    for_sublattice(r, c, 0, f);
-    for_sublattice(r, c ^ 1, 1, f);
-}
-
 template <class F>
 __device__ __forceinline__ void for_rect(int x0, int x1, int y0, int y1, F&& f) {
     const int nx = x1 - x0, ny = y1 - y0;
@@ -1044,17 +1037,6 @@ __device__ void tile_restrict(const Tile& t, const T* r, int rw, const LevelArgs
         fc[x] = acc;
         if (zero_uc) uc[x] = T(0);
     });
-}
-
-// Diagonal of a staged 9-point row, as L9Op::diag forms it.
-template <typename T>
-__device__ __forceinline__ T diag9(const T* A, int wh, int q) {
-    T d = A[q];
-    if constexpr (sizeof(T) == 4) {
-#pragma unroll
-        for (int k = 1; k < 9; ++k) d -= A[k * wh + q];
-    }
-    return d;
 }
 
 // Down leg of a coarse level l (1 <= l < tail): pre-smoothing (the first

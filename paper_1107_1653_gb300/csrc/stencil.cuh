@@ -69,20 +69,9 @@ struct Src5 {
     }
 };
 
-// Row sum of an implicit fine row (the leakage 1 - mu sum_y p(y)), float64.
-__device__ __forceinline__ double l0_rowsum(const IsaacsConsts* K, int c, int i, int j, int side) {
-    if (c == kStopCode) return 1.0;
-    const double* am = K->am[c];
-    double s = K->kappa;
-    if (i == 0) s -= am[1];
-    if (i + 1 == side) s -= am[2];
-    if (j == 0) s -= am[3];
-    if (j + 1 == side) s -= am[4];
-    return s;
-}
-
-// The same row sum in float32 for the float32 path: kappa plus the mass of
-// the couplings dropped at the boundary (all terms non-negative).
+// Row sum of an implicit fine row (the leakage 1 - mu sum_y p(y)) in float32
+// for the float32 path: kappa plus the mass of the couplings dropped at the
+// boundary (all terms non-negative).
 __device__ __forceinline__ float l0_rowsum_f(const IsaacsConsts* K, int c, int i, int j, int side) {
     if (c == kStopCode) return 1.0f;
     const float* am = K->amf[c];
